@@ -1,0 +1,74 @@
+"""Small hand-built systems for tests (inputs only)."""
+
+import json
+import os
+
+import numpy as np
+
+from paper_1108_4214_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def make_system(types, bonds, pos_sigma, box, rules, params=None, n_replicas=1, offsets=None, boxes=None):
+    """A System with explicit beads; pos_sigma in sigma (wrapped into the box
+    when snapshots are taken)."""
+    types = np.asarray(types, np.int32)
+    N = len(types)
+    offs = np.array(offsets if offsets is not None else [0, N], np.int64)
+    R = len(offs) - 1
+    bq = np.array(boxes if boxes is not None else [int(round(box * W.QSCALE))] * R, np.int64)
+    return W.System(
+        name="hand", bead_offset=offs, box_q=bq, types=types,
+        bonds=np.asarray(bonds, np.int32).reshape(-1, 4), rules=rules,
+        pos0=np.asarray(pos_sigma, np.float64).reshape(N, 3), seed=11, sigma_perturb=0.0,
+        form_scale=np.ones(R), break_scale=np.ones(R), rng_stream=np.arange(R, dtype=np.uint32),
+        params=dict(W.default_params(11), **(params or {})),
+    )
+
+
+def qpos(system, pos_sigma):
+    """Quantize explicit positions (sigma) for a system."""
+    x = np.asarray(pos_sigma, np.float64).reshape(-1, 3)
+    return W.quantize(x, system.box_q, system._rep_of_bead())
+
+
+def mask_of(spec):
+    if spec == "*":
+        return W.ALL_BEADS
+    return W.bit(*spec)
+
+
+def bond_mask_of(spec):
+    if spec == "*":
+        return W.ALL_BONDS
+    return W.bit(*spec)
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def golden_rules(entries):
+    out = []
+    for e in entries:
+        if e["kind"] == "createangle":
+            out.append(dict(kind="createangle", type=e["type"], beads=tuple(mask_of(b) for b in e["beads"]),
+                            bonds=tuple(bond_mask_of(b) for b in e["bonds"])))
+        elif e["kind"] == "createdihedral":
+            out.append(dict(kind="createdihedral", type=e["type"], beads=tuple(mask_of(b) for b in e["beads"]),
+                            bonds=tuple(bond_mask_of(b) for b in e["bonds"])))
+        else:
+            raise ValueError(e["kind"])
+    return out
+
+
+def ladder_1bead_positions(sep=0.5, spacing=0.5):
+    """The 4-mer ladder of the golden fixture: strand 1 along x at y=0, strand 2
+    (antiparallel) at y=sep; rung k holds beads k and 7-k."""
+    p = np.zeros((8, 3))
+    for k in range(4):
+        p[k] = (5.0 + spacing * k, 5.0, 5.0)
+        p[7 - k] = (5.0 + spacing * k, 5.0 + sep, 5.0)
+    return p

@@ -1,0 +1,163 @@
+"""Pins of the oracle's FP64 bonded forces: closed forms, finite differences of
+the energy, Newton's third law, invariances and the virial's strain
+derivative."""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1108_4214_gb300 import workloads as W
+
+from helpers import make_system
+
+
+def rot(rng):
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def test_closed_forms():
+    E, F = O.bond_half([1.3, 0, 0], 100.0, 1.0)
+    assert E == pytest.approx(0.5 * 100 * 0.09) and F == pytest.approx([-2 * 100 * 0.3, 0, 0])
+    E, Fa, Fc = O.angle([1, 0, 0], [-2, 0, 0], 2.0)  # straight: theta = 180 deg
+    assert E == pytest.approx(0.0, abs=1e-15) and np.allclose(Fa, 0) and np.allclose(Fc, 0)
+    E, Fa, Fc = O.angle([1, 0, 0], [0, 3, 0], 2.0)  # right angle
+    assert E == pytest.approx(2.0)
+    # Fa = -K d cos / d ra = -K rc / (|ra||rc|) at 90 deg
+    assert Fa == pytest.approx([0, -2.0 / 1.0, 0]) and Fc == pytest.approx([-2.0 / 3.0, 0, 0])
+    # planar trans (A and D on opposite sides): phi = 180 deg, E = K (1 - d); cis: E = K (1 + d)
+    trans = O.dihedral([0, -1, 0], [1, 0, 0], [0, -1, 0], 1.0, 1.0)
+    cis = O.dihedral([0, -1, 0], [1, 0, 0], [0, 1, 0], 1.0, 1.0)
+    assert trans[0] == pytest.approx(0.0, abs=1e-15) and cis[0] == pytest.approx(2.0)
+    assert O.dihedral([0, -1, 0], [1, 0, 0], [0, 1, 0], 1.0, -1.0)[0] == pytest.approx(0.0, abs=1e-15)
+    # perpendicular planes: cos phi = 0, E = K
+    assert O.dihedral([0, -1, 0], [1, 0, 0], [0, 0, 1], 1.5, 1.0)[0] == pytest.approx(1.5)
+
+
+def _fd(fun, x, h=1e-6):
+    g = np.zeros_like(x)
+    for i in range(x.size):
+        xp, xm = x.copy(), x.copy()
+        xp.flat[i] += h
+        xm.flat[i] -= h
+        g.flat[i] = (fun(xp) - fun(xm)) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_finite_differences_and_newton3(seed):
+    rng = np.random.default_rng(seed)
+    # bond
+    r = rng.normal(size=3)
+    E, F = O.bond_half(r, 37.0, 0.8)
+    g = _fd(lambda x: 2 * O.bond_half(x, 37.0, 0.8)[0], r)  # half energy per end
+    assert np.allclose(F, -g, rtol=1e-7, atol=1e-7)
+    # angle as a function of the three positions
+    P = rng.normal(size=(3, 3))
+
+    def Eang(x):
+        x = x.reshape(3, 3)
+        return O.angle(x[0] - x[1], x[2] - x[1], 1.7)[0]
+    E, Fa, Fc = O.angle(P[0] - P[1], P[2] - P[1], 1.7)
+    g = _fd(Eang, P.ravel()).reshape(3, 3)
+    Fb = -(Fa + Fc)
+    assert np.allclose(np.stack([Fa, Fb, Fc]), -g, rtol=1e-6, atol=1e-7)
+    # dihedral
+    Q = rng.normal(size=(4, 3))
+
+    def Edih(x):
+        x = x.reshape(4, 3)
+        return O.dihedral(x[1] - x[0], x[2] - x[1], x[3] - x[2], 0.9, -1.0)[0]
+    E, Fs = O.dihedral(Q[1] - Q[0], Q[2] - Q[1], Q[3] - Q[2], 0.9, -1.0)
+    g = _fd(Edih, Q.ravel()).reshape(4, 3)
+    assert np.allclose(np.stack(Fs), -g, rtol=1e-6, atol=1e-7)
+    assert np.allclose(np.sum(Fs, axis=0), 0, atol=1e-12)
+    # rotation invariance of the energies, covariance of the forces
+    M = rot(rng)
+    E2, Fs2 = O.dihedral(M @ (Q[1] - Q[0]), M @ (Q[2] - Q[1]), M @ (Q[3] - Q[2]), 0.9, -1.0)
+    assert E2 == pytest.approx(E, rel=1e-12)
+    assert np.allclose(np.stack(Fs2), np.stack(Fs) @ M.T, atol=1e-10)
+
+
+def _molecule(seed, box=40.0):
+    """A random branched molecule of 12 beads in a large box, with angle and
+    dihedral rules that type every path."""
+    rng = np.random.default_rng(seed)
+    n = 12
+    parent = [-1] + [int(rng.integers(0, k)) for k in range(1, n)]
+    deg = np.zeros(n, int)
+    bonds = []
+    for k in range(1, n):
+        p = parent[k]
+        if deg[p] >= 3:
+            p = k - 1
+        deg[p] += 1
+        deg[k] += 1
+        t = int(rng.integers(1, 3))
+        bonds.append([p, k, t, t])
+    pos = np.zeros((n, 3))
+    for k in range(1, n):
+        pos[k] = pos[[b[0] for b in bonds if b[1] == k][0]] + rng.normal(size=3) * 0.6
+    pos += box / 2
+    rules = [
+        dict(kind="createangle", type=1, beads=(W.ALL_BEADS,) * 3, bonds=(W.ALL_BONDS, W.ALL_BONDS)),
+        dict(kind="createdihedral", type=1, beads=(W.ALL_BEADS,) * 4, bonds=(W.bit(1), W.ALL_BONDS, W.ALL_BONDS)),
+        dict(kind="createdihedral", type=2, beads=(W.ALL_BEADS,) * 4, bonds=(W.ALL_BONDS,) * 3),
+    ]
+    s = make_system(rng.integers(0, 5, n), bonds, pos, box, rules)
+    s.forcefield = dict(bond_k=np.full(16, 30.0), bond_r0=np.full(16, 0.7), angle_k=np.full(16, 1.3),
+                        dihedral_k=np.full(16, 0.8), dihedral_d=np.array([1, 1, -1] + [1] * 13, np.int32))
+    return s, pos
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_system_forces_are_minus_energy_gradient(seed):
+    s, pos = _molecule(seed)
+    o = O.Oracle(s)
+    _, a, d = o.topology()
+    assert len(a) > 5 and len(d) > 3
+    q = s.snapshot()
+    f, ev = o.forces(q)
+    h = 64  # quanta
+    for i in range(0, s.n_beads, 3):
+        for c in range(3):
+            qp, qm = q.copy(), q.copy()
+            qp[i, c] += h
+            qm[i, c] -= h
+            g = (o.forces(qp)[1][0, 0] - o.forces(qm)[1][0, 0]) / (2 * h / W.QSCALE)
+            assert f[i, c] == pytest.approx(-g, rel=1e-5, abs=1e-5)
+    assert np.allclose(f.sum(axis=0), 0, atol=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_virial_is_minus_strain_derivative(seed):
+    # under x_a -> x_a + eps x_b about the molecule's centre, dE/deps = -W_ba
+    s, pos = _molecule(seed)
+    o = O.Oracle(s)
+    ctr = pos.mean(axis=0)
+    comp = {(0, 0): 1, (1, 1): 2, (2, 2): 3, (0, 1): 4, (0, 2): 5, (1, 2): 6}
+    _, ev = o.forces(s.snapshot())
+    W6 = ev[0]
+    Wm = np.zeros((3, 3))
+    for (a_, b_), k in comp.items():
+        Wm[a_, b_] = Wm[b_, a_] = W6[k]
+    eps = 1e-2  # quantization noise in dE/deps is ~ 2^-21 / eps relative
+    for a_ in range(3):
+        for b_ in range(3):
+            def energy(e):
+                x = pos - ctr
+                x2 = x.copy()
+                x2[:, a_] += e * x[:, b_]
+                from helpers import qpos
+                return o.forces(qpos(s, x2 + ctr))[1][0, 0]
+            dE = (energy(eps) - energy(-eps)) / (2 * eps)
+            assert dE == pytest.approx(-Wm[b_, a_], rel=2e-3, abs=1e-3 * np.abs(Wm).max())
+
+
+def test_translation_invariance_through_the_box():
+    s, pos = _molecule(1)
+    o = O.Oracle(s)
+    f0, e0 = o.forces(s.snapshot())
+    from helpers import qpos
+    f1, e1 = o.forces(qpos(s, pos + np.array([19.75, -33.125, 5.5])))  # wraps through the boundary
+    assert np.allclose(f0, f1, atol=1e-6) and np.allclose(e0, e1, rtol=1e-9, atol=1e-6)
