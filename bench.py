@@ -1,0 +1,343 @@
+"""Benchmark: bead-updates/s of one dynamic-bonding call plus bonded forces.
+
+A step is dynbond_step + dynbond_forces on a fresh snapshot of the plain
+1,048,576-bead DNA-like workload (8192 strands x 64 nt, density 0.5), inputs
+resident in HBM; L2 is flushed (256 MB write) between timed steps and each
+step is timed with CUDA events on the library's stream.  value = beads x
+steps / device time, summed over all ranks (weak scaling: every rank runs its
+own independent system; there is no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the reference of this build) on the
+same workload, metric and unit, on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bead-updates/s of dynbond_step+dynbond_forces"
+UNIT = "bead-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batched", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int):
+    from paper_1108_4214_gb300 import workloads as W
+    s = W.config2()
+    if rank:
+        s = W.dna_system(s.name, 8192, 64, 0.5, 2 + 1000 * rank, W.rules_dna2())
+    return s
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def algorithmic_bytes(stats_before, st, N, R):
+    """Minimum bytes one step + forces must move (per the design notes):
+    positions and slots read for the search and the breakage scan, candidate
+    edges written and read, nominations per round, the angle / dihedral lists
+    read by the purge and the forces, records written, and the forces."""
+    c = {k: int(v) for k, v in st.items()}
+    na0, nd0 = stats_before
+    b = 16 * N + 16 * N  # positions + slots: candidate search / breakage scan
+    b += 2 * 16 * c["candidates"] * 2  # edge list (both directions) written and read
+    b += 8 * 2 * c["candidates"] * max(1, c["create_rounds"])  # nominations per round
+    b += 16 * (na0 + nd0)  # purge reads both lists
+    b += 16 * (c["angles_added"] + c["dihedrals_added"])  # appended records
+    b += 16 * N + 16 * N + 16 * (c["n_angles"] + c["n_dihedrals"]) + 16 * N + 56 * R  # forces
+    return b
+
+
+def kernel_bytes(phase, N, st, na_before, nd_before):
+    """Algorithmic bytes of one launch of the phase that dominates the step."""
+    if phase == "bead":
+        return 16 * N + 16 * N + N + 4 * N  # positions, slots, types, replica ids
+    if phase == "purge":
+        return 16 * (na_before + nd_before) + 16 * (st["n_angles"] - st["angles_added"] +
+                                                     st["n_dihedrals"] - st["dihedrals_added"])
+    if phase == "bond_forces":
+        return 16 * N + 16 * N + 16 * N  # positions, slots, forces
+    if phase == "angle_forces":
+        return 16 * st["n_angles"] + 3 * 2 * 16 * st["n_angles"]  # records + 3 force read-modify-writes
+    if phase == "dihedral_forces":
+        return 16 * st["n_dihedrals"] + 4 * 2 * 16 * st["n_dihedrals"]
+    if phase == "candidates":
+        return 16 * N // 2 + 16 * N // 2 + 16 * 2 * st["candidates"]
+    if phase == "cells":
+        return 16 * N // 2 * 2 + 8 * N
+    return None
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1108_4214_gb300 import dynbond
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    s = workload(rank)
+    N, R = s.n_beads, s.n_replicas
+    K, Wm = args.steps, args.warmup
+    snaps_np = s.snapshots(0, K + Wm)
+    snaps = [torch.from_numpy(x).to(dev) for x in snaps_np]
+    stream = torch.cuda.current_stream()
+    ctx = dynbond.Context(s, flags=dynbond.FLAG_PROFILE, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    force = torch.empty((N, 4), dtype=torch.float32, device=dev)
+    ev = torch.empty((R, 7), dtype=torch.float64, device=dev)
+    for k in range(Wm):
+        ctx.step(snaps[k], k)
+        ctx.forces(snaps[k], force, ev)
+    ctx.sync()
+    phases = {}
+    stats_all = []
+    times = []
+    prev_counts = None
+    with ClockSampler(dev.index) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(Wm, Wm + K):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.step(snaps[k], k)
+            ctx.forces(snaps[k], force, ev)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            for name, ms in ctx.phase_times().items():
+                phases.setdefault(name, []).append(ms)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # statistics of one more (untimed) call for the algorithmic byte counts
+    na_before, nd_before = ctx.topology()[1].shape[0], ctx.topology()[2].shape[0]
+    st = ctx.step(snaps[-1], Wm + K, stats=True)
+    stats = {n: int(st[:, j].sum()) for j, n in enumerate(dynbond.STAT_NAMES)}
+    ctx.forces(snaps[-1], force, ev)
+    ctx.sync()
+    value = N * K * world / (total_ms / 1e3)
+    result = dict(value=value, ms=total_ms / K, N=N, R=R, phases={k: float(np.mean(v)) for k, v in phases.items()},
+                  stats=stats, na_before=na_before, nd_before=nd_before, clocks=clk.summary(), rank=rank,
+                  world=world, name=s.name)
+
+    # end to end through the host-buffer entry point: pinned host input, result read back
+    pin_pos = torch.empty((N, 4), dtype=torch.int32).pin_memory()
+    pin_f = torch.empty((N, 4), dtype=torch.float32).pin_memory()
+    pin_ev = torch.empty((R, 7), dtype=torch.float64).pin_memory()
+    ctx_h = dynbond.Context(s, stream=stream)
+    for k in range(min(Wm, 3)):
+        pin_pos.copy_(torch.from_numpy(snaps_np[k]))
+        ctx_h.run_host(pin_pos, k, pin_f, pin_ev)
+    e2e_s = 0.0
+    for k in range(Wm, Wm + K):
+        pin_pos.copy_(torch.from_numpy(snaps_np[k]))
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx_h.run_host(pin_pos, k, pin_f, pin_ev)
+        e2e_s += time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    result["e2e"] = dict(value=N * K * world / e2e_s, unit=UNIT, h2d_bytes_per_step=16 * N,
+                         d2h_bytes_per_step=16 * N + 56 * R)
+    ctx_h.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(seconds: float):
+    """The oracle as it stands, serial on one host core, on a bounded sample
+    of the same workload: as many whole step + forces calls as fit in about
+    `seconds` (at least one)."""
+    from oracle import oracle as O
+    s = workload(0)
+    o = O.Oracle(s)
+    snaps = s.snapshots(0, 64)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(snaps[n], n)
+        o.forces(snaps[n])
+        n += 1
+        if time.perf_counter() - t0 > seconds or n == len(snaps):
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=s.n_beads * n / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{n} consecutive calls (step + forces) of the 1,048,576-bead workload, serial C++ oracle")
+
+
+def reference_arm(args):
+    """The oracle timed as the reference implementation: W untimed calls,
+    then K timed calls of step + forces on the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    s = workload(0)
+    o = O.Oracle(s)
+    K, Wm = args.steps, args.warmup
+    snaps = s.snapshots(0, K + Wm)
+    for k in range(Wm):
+        o.step(snaps[k], k)
+        o.forces(snaps[k])
+    t0 = time.perf_counter()
+    for k in range(Wm, Wm + K):
+        o.step(snaps[k], k)
+        o.forces(snaps[k])
+    dt = time.perf_counter() - t0
+    v = s.n_beads * K / dt
+    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=K, warmup=Wm,
+                ms_per_step=1e3 * dt / K, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64+f64",
+                data="synthetic", config=dict(workload=s.name, beads=s.n_beads, replicas=1),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle",
+                                  sample=f"{K} timed calls (step + forces) of the workload, serial C++ oracle"),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.steps < 1 or args.warmup < 3:
+        raise SystemExit("need --steps >= 1 and --warmup >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import __graft_entry__  # noqa: F401  (path setup only)
+    res = run_gpu(args)
+    if res["rank"] != 0:
+        return
+    peak, peak_kind = peaks()
+    ph = res["phases"]
+    dom = max((k for k in ph if not k.endswith("setup")), key=lambda k: ph[k])
+    kb = kernel_bytes(dom, res["N"], res["stats"], res["na_before"], res["nd_before"])
+    roof = None
+    if kb is not None and ph[dom] > 0:
+        ach = kb / (ph[dom] * 1e-3) / 1e9
+        roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
+                    peak_source=peak_kind, bytes_per_launch=kb, ms_per_launch=ph[dom], traffic=None)
+    alg = algorithmic_bytes((res["na_before"], res["nd_before"]), res["stats"], res["N"], res["R"])
+    step_gbs = alg / (res["ms"] * 1e-3) / 1e9
+    rank, world, _ = dist_env()
+    cpu = cpu_baseline(args.cpu_baseline_seconds) if world == 1 else None
+    kernels_per_step = 15 + 6
+    line = dict(
+        metric=METRIC, value=res["value"], unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=res["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64+f32",
+        data="synthetic",
+        config=dict(workload=res["name"], beads=res["N"], replicas=res["R"], parallelism=f"replicas x{world}",
+                    l2="flushed between timed steps (256 MB write)", step="dynbond_step + dynbond_forces"),
+        roofline=roof,
+        step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=step_gbs, peak=peak, unit="GB/s",
+                           frac=step_gbs / peak, peak_source=peak_kind),
+        phases_ms=ph, cpu_baseline=cpu, e2e=res["e2e"], gpu_launches=kernels_per_step * args.steps,
+        clocks=res["clocks"], stats_last_call=res["stats"],
+    )
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,288 @@
+/*
+ * dynbond.h — C ABI of the GB300 dynamic-bonding library (libdynbond.so).
+ *
+ * One call of dynbond_step() is one application of the dynamic-bonding fix of
+ * C. Svaneborg, "LAMMPS Framework for Dynamic Bonding and an Application
+ * Modeling DNA" (arXiv:1108.4214): creation and breakage nomination on the
+ * state before the call, mutual-nomination matching, stochastic trials,
+ * killbond / breakbond / convertbond, removal of every angle and dihedral that
+ * contains a removed or converted bond, and typed creation of the angles and
+ * dihedrals of every new triplet and quartet (Sec. 2; Appendix steps 1-10).
+ * dynbond_forces() evaluates the bonded forces of the resulting topology.
+ *
+ * Conventions shared by every entry point
+ *   - Beads of all replicas are numbered globally 0..N-1; replica r owns
+ *     [bead_offset[r], bead_offset[r+1]).  Replicas never interact.
+ *   - Positions are int32 on a fixed-point grid of 2^-20 sigma per unit,
+ *     passed as int4 {x, y, z, w} per bead (16 bytes, w ignored), each
+ *     coordinate in [0, box_q[r]).  Squared distances are exact int64; a
+ *     distance threshold r is compared as d2 <= floor((r * 2^20)^2) ("within r")
+ *     or d2 > floor((r * 2^20)^2) ("longer than r").
+ *   - Bond types are 1..15, bead types 0..15; type masks have bit t set for
+ *     type t ('*' = all bits).  Each bead holds at most DYNBOND_SLOTS bonds.
+ *   - Device pointers (d_*) are caller-owned CUDA global memory; host
+ *     pointers (h_*, and every pointer inside dynbond_system / dynbond_rule /
+ *     dynbond_topology) are caller-owned host memory that is only read (or
+ *     written, for outputs) during the call.
+ *   - Every call is ordered on the context's CUDA stream.  Errors found on the
+ *     device (capacity, bad positions, timeouts) are reported by the next call
+ *     that synchronizes: dynbond_sync(), or dynbond_step() with h_stats.  After
+ *     a device error the context refuses further steps (status sticks).
+ *   - No entry point throws or aborts; each returns a dynbond_status.
+ */
+#ifndef DYNBOND_H
+#define DYNBOND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dynbond_status {
+  DYNBOND_OK = 0,
+  DYNBOND_EINVAL = 1,         /* malformed argument, rule, system or position */
+  DYNBOND_ENOMEM = 2,         /* device or host allocation failed */
+  DYNBOND_ECAPACITY = 3,      /* a fixed capacity was exceeded (see DYNBOND_MAX_*) */
+  DYNBOND_ECUDA = 4,          /* a CUDA runtime call failed */
+  DYNBOND_ETIMEOUT = 5,       /* a bounded device-side wait gave up */
+  DYNBOND_ENOTCONVERGED = 6   /* matching needed more than DYNBOND_MAX_ROUNDS rounds */
+} dynbond_status;
+
+enum {
+  DYNBOND_MAX_TYPES = 16,     /* bead types 0..15, bond / angle / dihedral types 1..15 */
+  DYNBOND_SLOTS = 4,          /* bonds per bead; creation also requires fewer than this */
+  DYNBOND_MAX_RULES = 32,
+  DYNBOND_MAX_CANDIDATES = 24,/* creation candidates one bead keeps in registers; beads with more
+                                 take an exact two-pass path (no limit) */
+  DYNBOND_MAX_ROUNDS = 4096,  /* matching rounds of one call */
+  DYNBOND_EV = 7              /* energy + 6 virial components per replica */
+};
+
+/* Rule kinds: the rule set of the fix (Fig. 1). */
+typedef enum dynbond_rule_kind {
+  DYNBOND_CREATEBOND = 1,     /* type; bead_mask[0..1]; dist (max); prob */
+  DYNBOND_CREATEDIRBOND = 2,  /* type (stored by the bead-mask-0 end), type2 (by the other); bead_mask[0..1]; dist; prob */
+  DYNBOND_BREAKBOND = 3,      /* type; dist (min, strict); prob */
+  DYNBOND_CONVERTBOND = 4,    /* type -> type2; prob */
+  DYNBOND_KILLBOND = 5,       /* type; dist (min, strict) */
+  DYNBOND_CREATEANGLE = 6,    /* type; bead_mask[0..2]; bond_mask[0] = t, [1] = s */
+  DYNBOND_CREATEDIHEDRAL = 7, /* type; bead_mask[0..3]; bond_mask[0] = r, [1] = s / s', [2] = t */
+  DYNBOND_MAXBOND = 8         /* bond_mask[0] = counted bond types; bead_mask[0]; maxn */
+} dynbond_rule_kind;
+
+/*
+ * One rule (64 bytes).  Rules are evaluated in list order:
+ *   - creation (createbond / createdirbond): per candidate pair the LAST rule
+ *     matching bead types, distance and maxbond decides the stored bond types
+ *     (Sec. 2, Appendix step 2); a directional bond is oriented by trying the
+ *     lower-id bead as the rule's first bead type first;
+ *   - breakage / conversion (breakbond / convertbond): per bond the LAST
+ *     matching rule; these rules, and killbond, apply to symmetric bonds of
+ *     their type (both endpoints store it), as Sec. 2 describes them;
+ *   - typing (createangle / createdihedral): per path the FIRST rule matching
+ *     ABC or CBA (ABCD or DCBA) with the directional bond types of Sec. 2:
+ *     angle t = type B stores toward A, s = type B stores toward C; dihedral
+ *     r = B toward A, s = C toward B or s' = B toward C, t = C toward D;
+ *   - maxbond: a bead of a type in bead_mask[0] may receive a bond stored as a
+ *     type in bond_mask[0] only while it stores fewer than maxn such bonds.
+ *     Conversions are not checked against maxbond (the fix checks it while
+ *     nominating creation partners only).
+ */
+typedef struct dynbond_rule {
+  int32_t kind;
+  int32_t type;
+  int32_t type2;
+  int32_t maxn;
+  uint32_t bead_mask[4];
+  uint32_t bond_mask[3];
+  uint32_t reserved;
+  double dist;
+  double prob;
+} dynbond_rule;
+
+enum {
+  DYNBOND_FLAG_NO_GRAPH = 1,  /* launch kernels one by one instead of replaying a CUDA graph */
+  DYNBOND_FLAG_PROFILE = 2    /* record CUDA events between phases (dynbond_phase_times) */
+};
+
+/*
+ * Run parameters.
+ *   seed          64-bit key of the Philox4x32-10 trials (Salmon et al., SC'11).
+ *   paircheck13/14  1 admits creation between beads 2 / 3 bonds apart; beads
+ *                 1 bond apart never bond again, beads >= 4 apart always may.
+ *   max_rounds    0 = repeat mutual-nomination rounds until none matches;
+ *                 k > 0 = at most k rounds (1 = the fix's single nomination).
+ *   prob_mode     0 = one uniform per trial: success iff u < floor(p 2^32);
+ *                 1 = the fix's average of two uniforms: u0 + u1 < 2 floor(p 2^32).
+ *   reactive_mask bead types of the reactive group; every rule acts only on
+ *                 pairs / bonds of two reactive beads.
+ *   flags         DYNBOND_FLAG_*.
+ *   cell_scale    0 = autotune; k >= 1: cell edge >= k x the largest creation
+ *                 distance (never changes results).
+ *   block_size    0 = default (256) threads per block for the bead passes.
+ *   spin_limit    0 = default; iterations of every bounded device-side wait.
+ */
+typedef struct dynbond_params {
+  uint64_t seed;
+  int32_t paircheck13;
+  int32_t paircheck14;
+  int32_t max_rounds;
+  int32_t prob_mode;
+  uint32_t reactive_mask;
+  int32_t flags;
+  int32_t cell_scale;
+  int32_t block_size;
+  int32_t spin_limit;
+  int32_t reserved[5];
+} dynbond_params;
+
+/*
+ * Bonded force field, indexed by type (entry 0 unused):
+ *   bond      E = bond_k (r - bond_r0)^2; each endpoint feels the force of the
+ *             type IT stores and books half the energy (directional bonds,
+ *             Sec. 2: equal potentials both ways conserve momentum);
+ *   angle     E = angle_k (1 + cos theta), theta the angle at the centre bead;
+ *   dihedral  E = dihedral_k (1 + dihedral_d cos phi) (the form of Sec. 3),
+ *             phi = 180 degrees for the trans conformation.
+ */
+typedef struct dynbond_forcefield {
+  double bond_k[DYNBOND_MAX_TYPES];
+  double bond_r0[DYNBOND_MAX_TYPES];
+  double angle_k[DYNBOND_MAX_TYPES];
+  double dihedral_k[DYNBOND_MAX_TYPES];
+  int32_t dihedral_d[DYNBOND_MAX_TYPES];
+} dynbond_forcefield;
+
+/*
+ * The system, read during dynbond_create() only.
+ *   bead_offset[R+1], box_q[R]  replica bead ranges and periodic box edges
+ *                 (quantized units, 2 <= box_q < 2^31).
+ *   form_scale[R], break_scale[R]  nullable (= 1): the trial probability of a
+ *                 creation (breakage / conversion) rule in replica r is
+ *                 min(1, prob x scale[r]).
+ *   rng_stream[R] nullable (= r): 24-bit Philox stream id of replica r.
+ *   bead_type[N]  0..15.
+ *   bonds[n_bonds*4]  rows (i, j, type stored by i, type stored by j), global
+ *                 ids, i and j in the same replica; at most DYNBOND_SLOTS
+ *                 bonds per bead.  The initial angles and dihedrals are the
+ *                 typed set of every non-cyclic 3- and 4-bead path of this
+ *                 graph, which every later call keeps exact.
+ */
+typedef struct dynbond_system {
+  int32_t n_replicas;
+  int32_t reserved;
+  const int64_t* bead_offset;
+  const int64_t* box_q;
+  const double* form_scale;
+  const double* break_scale;
+  const uint32_t* rng_stream;
+  const int32_t* bead_type;
+  const int32_t* bonds;
+  int64_t n_bonds;
+} dynbond_system;
+
+/* Per-replica statistics of one call (Appendix step 10), 17 int64 values. */
+typedef struct dynbond_stats {
+  int64_t candidates;       /* creation candidate pairs */
+  int64_t create_matched;   /* mutually nominated creation pairs */
+  int64_t bonds_formed;
+  int64_t break_candidates; /* bonds eligible for breakbond / convertbond */
+  int64_t break_matched;
+  int64_t bonds_broken;     /* by breakbond trials (not also killed) */
+  int64_t bonds_killed;
+  int64_t bonds_converted;  /* by convertbond trials (not also killed) */
+  int64_t angles_removed;
+  int64_t angles_added;
+  int64_t dihedrals_removed;
+  int64_t dihedrals_added;
+  int64_t n_bonds;          /* totals after the call */
+  int64_t n_angles;
+  int64_t n_dihedrals;
+  int64_t create_rounds;    /* rounds in which this replica matched a creation pair */
+  int64_t break_rounds;
+} dynbond_stats;
+
+/*
+ * Topology export (two-call protocol): call once with null arrays to obtain
+ * the counts, then again with caller-allocated host arrays of those sizes.
+ *   bonds[n_bonds*4]        (i < j, type stored by i, type stored by j), sorted;
+ *   angles[n_angles*4]      (a, b, c, type), a < c, sorted;
+ *   dihedrals[n_dihedrals*5] (a, b, c, d, type), a < d, sorted.
+ */
+typedef struct dynbond_topology {
+  int64_t n_bonds;
+  int64_t n_angles;
+  int64_t n_dihedrals;
+  int32_t* bonds;
+  int32_t* angles;
+  int32_t* dihedrals;
+} dynbond_topology;
+
+typedef struct dynbond_ctx dynbond_ctx;
+typedef struct CUstream_st* dynbond_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+/*
+ * Create a context: validates the rules (the fix's parse-time sanity check)
+ * and the system, uploads it to the current CUDA device, builds the initial
+ * angle / dihedral lists and captures the per-call work.  Device memory for
+ * the topology is sized for the worst case (6 angles and 18 dihedrals per
+ * bead), so the lists never overflow.  Returns EINVAL on malformed input,
+ * ENOMEM / ECUDA on device failure; *out is NULL on failure.
+ */
+dynbond_status dynbond_create(const dynbond_params* params, const dynbond_rule* rules, int32_t n_rules,
+                              const dynbond_system* system, const dynbond_forcefield* forcefield,
+                              dynbond_stream stream, dynbond_ctx** out);
+
+/*
+ * One call of the fix (Appendix steps 1-10) at call index `step` on the
+ * positions d_pos (device int4[N], read only).  Trials are keyed by
+ * (seed, step, pair), so repeating a step index repeats its random numbers.
+ * h_stats (nullable, host [n_replicas]): when given, the call waits for the
+ * device and fills the statistics, and device errors are returned.
+ */
+dynbond_status dynbond_step(dynbond_ctx* ctx, const int32_t* d_pos, uint64_t step, dynbond_stats* h_stats);
+
+/*
+ * Bonded forces of the current topology at d_pos: d_force (device float4[N],
+ * overwritten; w = 0) in FP32; d_ev (device double[R*7], overwritten) per
+ * replica (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz) with W_ab = sum over interactions
+ * of (r_role - r_ref)_a F_role,b, reduced in FP64.
+ */
+dynbond_status dynbond_forces(dynbond_ctx* ctx, const int32_t* d_pos, float* d_force, double* d_ev);
+
+/*
+ * dynbond_step + dynbond_forces from host buffers: copies h_pos (int4[N]) to
+ * the device, runs both, and copies the forces (float4[N]) and energies /
+ * virials (double[R*7]) back.  Waits for completion.  h_stats nullable.
+ */
+dynbond_status dynbond_run_host(dynbond_ctx* ctx, const int32_t* h_pos, uint64_t step, float* h_force,
+                                double* h_ev, dynbond_stats* h_stats);
+
+/* Export the current topology (two-call protocol above).  Synchronizes. */
+dynbond_status dynbond_get_topology(dynbond_ctx* ctx, dynbond_topology* topo);
+
+/* Wait for the context's stream and return any device-side error. */
+dynbond_status dynbond_sync(dynbond_ctx* ctx);
+
+/*
+ * Per-phase device times (ms) of the last dynbond_step and dynbond_forces of a
+ * context created with DYNBOND_FLAG_PROFILE (CUDA events recorded between the
+ * phases inside the replayed work, so timing adds no host synchronization to
+ * the calls themselves).  Synchronizes the stream, writes up to n values and
+ * their static names, and returns the number of phases in *n_out.
+ */
+dynbond_status dynbond_phase_times(dynbond_ctx* ctx, float* ms, const char** names, int32_t n, int32_t* n_out);
+
+/* Human-readable text of the last error of ctx (never NULL). */
+const char* dynbond_last_error(const dynbond_ctx* ctx);
+
+const char* dynbond_status_string(dynbond_status status);
+
+void dynbond_destroy(dynbond_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DYNBOND_H */

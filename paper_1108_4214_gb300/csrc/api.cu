@@ -1,0 +1,846 @@
+// Host side of libdynbond: the C ABI of include/dynbond.h.  A context owns
+// the device topology (bond slots, per-replica angle / dihedral lists sized
+// for the worst case), the per-call scratch, and two CUDA graphs (one call of
+// the fix; one force evaluation) replayed with new arguments each call.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace dynbond;
+
+struct dynbond_ctx {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  dynbond_params prm{};
+  RuleTab rt{};
+  FF ff{};
+  long long N = 0;
+  int R = 0;
+  long long n_cells = 0;
+  long long W = 0;  // bitmap words
+  Dev d{};
+  std::vector<void*> allocs;
+  cudaGraphExec_t g_step = nullptr, g_forces = nullptr;
+  bool use_graph = true;
+  int block = 256;
+  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_nb = 0, grid_seg = 0;
+  long long st_scan_n = 0, st_nb_n = 0, st_pa_n = 0, st_pd_n = 0, st_rb_n = 0;
+  void* small = nullptr;
+  size_t small_bytes = 0;
+  void* status_all = nullptr;
+  size_t status_bytes = 0;
+  dynbond_status sticky = DYNBOND_OK;
+  std::string last_error;
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_step, ev_forces;
+  std::vector<const char*> names_step, names_forces;
+  std::vector<float> last_step_ms, last_forces_ms;
+  int last_profiled = 0;  // 1 = step, 2 = forces
+  int4* h2d_pos = nullptr;
+  float4* d2h_force = nullptr;
+  double* d2h_ev = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_create_error;  // message of the last failed dynbond_create
+
+dynbond_status fail(dynbond_ctx* c, dynbond_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      return fail(ctx, DYNBOND_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    }                                                                                         \
+  } while (0)
+
+template <class T>
+dynbond_status dalloc(dynbond_ctx* c, T** p, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DYNBOND_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return DYNBOND_OK;
+}
+
+// floor((dist * 2^20)^2), exact for the double dist: with dist * 2^20 = m 2^e
+// (m an integer below 2^53) the square m^2 2^(2e) fits 128-bit integers.
+long long quantized_r2(double dist) {
+  if (!(dist > 0.0) || !std::isfinite(dist)) return 0;
+  int e;
+  double f = std::frexp(std::ldexp(dist, 20), &e);  // dist 2^20 = f 2^e, f in [0.5, 1)
+  unsigned long long m = (unsigned long long)std::ldexp(f, 53);
+  int sh = 2 * (e - 53);
+  unsigned __int128 sq = (unsigned __int128)m * m;
+  const unsigned __int128 cap = (unsigned __int128)0x7FFFFFFFFFFFFFFFull;
+  if (sh >= 0) {
+    if (sh >= 63 || (sq << sh) > cap) return 0x7FFFFFFFFFFFFFFFll;
+    return (long long)(sq << sh);
+  }
+  if (-sh >= 128) return 0;
+  unsigned __int128 v = sq >> (-sh);
+  return v > cap ? 0x7FFFFFFFFFFFFFFFll : (long long)v;
+}
+
+unsigned long long prob_threshold(double p) {
+  if (!(p > 0.0)) return 0ull;
+  if (p >= 1.0) return 1ull << 32;
+  return (unsigned long long)(p * 4294967296.0);
+}
+
+bool mask_ok(uint32_t m) { return m != 0 && (m >> DYNBOND_MAX_TYPES) == 0; }
+bool btype_ok(int t) { return t >= 1 && t < DYNBOND_MAX_TYPES; }
+
+dynbond_status build_rules(dynbond_ctx* c, const dynbond_rule* rules, int n) {
+  if (n < 0 || n > MAXR) return fail(c, DYNBOND_EINVAL, "n_rules must be in [0, 32]");
+  if (n > 0 && !rules) return fail(c, DYNBOND_EINVAL, "rules is NULL");
+  RuleTab& rt = c->rt;
+  std::memset(&rt, 0, sizeof(rt));
+  rt.n = n;
+  for (int k = 0; k < n; ++k) {
+    const dynbond_rule& r = rules[k];
+    std::string where = "rule " + std::to_string(k) + ": ";
+    rt.kind[k] = r.kind;
+    rt.type[k] = r.type;
+    rt.type2[k] = r.type2;
+    rt.maxn[k] = r.maxn;
+    for (int q = 0; q < 4; ++q) rt.bead[k][q] = r.bead_mask[q];
+    for (int q = 0; q < 3; ++q) rt.bond[k][q] = r.bond_mask[q];
+    bool dist_ok = std::isfinite(r.dist) && r.dist >= 0.0;
+    bool prob_ok = std::isfinite(r.prob) && r.prob >= 0.0;
+    switch (r.kind) {
+      case DYNBOND_CREATEBOND:
+      case DYNBOND_CREATEDIRBOND:
+        if (!btype_ok(r.type) || (r.kind == DYNBOND_CREATEDIRBOND && !btype_ok(r.type2)))
+          return fail(c, DYNBOND_EINVAL, where + "bond type out of range 1..15");
+        if (!mask_ok(r.bead_mask[0]) || !mask_ok(r.bead_mask[1]))
+          return fail(c, DYNBOND_EINVAL, where + "bead type masks must be nonzero over types 0..15");
+        if (!dist_ok || !prob_ok) return fail(c, DYNBOND_EINVAL, where + "bad distance or probability");
+        rt.r2[k] = quantized_r2(r.dist);
+        break;
+      case DYNBOND_BREAKBOND:
+      case DYNBOND_KILLBOND:
+        if (!btype_ok(r.type)) return fail(c, DYNBOND_EINVAL, where + "bond type out of range 1..15");
+        if (!dist_ok || (r.kind == DYNBOND_BREAKBOND && !prob_ok))
+          return fail(c, DYNBOND_EINVAL, where + "bad distance or probability");
+        rt.r2[k] = quantized_r2(r.dist);
+        break;
+      case DYNBOND_CONVERTBOND:
+        if (!btype_ok(r.type) || !btype_ok(r.type2) || !prob_ok)
+          return fail(c, DYNBOND_EINVAL, where + "bad bond types or probability");
+        break;
+      case DYNBOND_CREATEANGLE:
+        if (!btype_ok(r.type)) return fail(c, DYNBOND_EINVAL, where + "angle type out of range 1..15");
+        for (int q = 0; q < 3; ++q)
+          if (!mask_ok(r.bead_mask[q])) return fail(c, DYNBOND_EINVAL, where + "bead masks must be nonzero");
+        for (int q = 0; q < 2; ++q)
+          if (!mask_ok(r.bond_mask[q])) return fail(c, DYNBOND_EINVAL, where + "bond masks must be nonzero");
+        rt.angle_idx[rt.n_angle++] = k;
+        break;
+      case DYNBOND_CREATEDIHEDRAL:
+        if (!btype_ok(r.type)) return fail(c, DYNBOND_EINVAL, where + "dihedral type out of range 1..15");
+        for (int q = 0; q < 4; ++q)
+          if (!mask_ok(r.bead_mask[q])) return fail(c, DYNBOND_EINVAL, where + "bead masks must be nonzero");
+        for (int q = 0; q < 3; ++q)
+          if (!mask_ok(r.bond_mask[q])) return fail(c, DYNBOND_EINVAL, where + "bond masks must be nonzero");
+        rt.dihedral_idx[rt.n_dihedral++] = k;
+        break;
+      case DYNBOND_MAXBOND:
+        if (!mask_ok(r.bond_mask[0]) || !mask_ok(r.bead_mask[0]) || r.maxn < 0)
+          return fail(c, DYNBOND_EINVAL, where + "maxbond needs bond and bead masks and maxn >= 0");
+        rt.maxbond_idx[rt.n_maxbond++] = k;
+        break;
+      default:
+        return fail(c, DYNBOND_EINVAL, where + "unknown rule kind " + std::to_string(r.kind));
+    }
+    if (r.kind == DYNBOND_CREATEBOND || r.kind == DYNBOND_CREATEDIRBOND) {
+      rt.r2max = std::max(rt.r2max, rt.r2[k]);
+      for (int a = 0; a < 16; ++a) {
+        if ((r.bead_mask[0] >> a) & 1u || (r.bead_mask[1] >> a) & 1u) rt.role_rules[a] |= 1u << k;
+        for (int b = 0; b < 16; ++b)
+          if ((((r.bead_mask[0] >> a) & 1u) && ((r.bead_mask[1] >> b) & 1u)) ||
+              (((r.bead_mask[0] >> b) & 1u) && ((r.bead_mask[1] >> a) & 1u)))
+            rt.pair_rules[a][b] |= 1u << k;
+      }
+    }
+    if (r.kind == DYNBOND_BREAKBOND || r.kind == DYNBOND_CONVERTBOND || r.kind == DYNBOND_KILLBOND)
+      rt.breakish |= 1u << r.type;
+  }
+  const dynbond_params& p = c->prm;
+  rt.reactive = p.reactive_mask;
+  rt.pc13 = p.paircheck13 != 0;
+  rt.pc14 = p.paircheck14 != 0;
+  rt.max_rounds = p.max_rounds;
+  rt.prob_mode = p.prob_mode;
+  rt.key0 = (uint32_t)p.seed;
+  rt.key1 = (uint32_t)(p.seed >> 32);
+  return DYNBOND_OK;
+}
+
+int occupancy_grid(dynbond_ctx* c, const void* fn, int block, int per_sm_cap) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return c->nsm * std::min(nb, per_sm_cap);
+}
+
+int bounded_grid(long long work, int block, int cap) {
+  long long g = (work + block - 1) / block;
+  return (int)std::max<long long>(1, std::min<long long>(g, cap));
+}
+
+// ---------------------------------------------------------------------------
+// launch sequences
+// ---------------------------------------------------------------------------
+
+void mark(dynbond_ctx* c, std::vector<cudaEvent_t>& ev, size_t k) {
+  if (c->profile && k < ev.size()) cudaEventRecord(ev[k], c->stream);
+}
+
+cudaError_t launch_match(dynbond_ctx* c) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(c->grid_match);
+  cfg.blockDim = dim3(256);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_match, c->d, c->rt);
+}
+
+cudaError_t enqueue_step(dynbond_ctx* c) {
+  const Dev& d = c->d;
+  cudaStream_t s = c->stream;
+  size_t k = 0;
+  mark(c, c->ev_step, k++);
+  cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s);
+  cudaMemsetAsync(d.cell_start, 0, sizeof(int) * (c->n_cells + 1), s);
+  cudaMemsetAsync(d.bm_ca, 0, sizeof(unsigned) * c->W, s);
+  cudaMemsetAsync(c->small, 0, c->small_bytes, s);
+  cudaMemsetAsync(c->status_all, 0, c->status_bytes, s);
+  k_tiles<<<1, 1024, 0, s>>>(d, 0);
+  mark(c, c->ev_step, k++);
+  k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->rt);
+  mark(c, c->ev_step, k++);
+  k_scan_cells<<<c->grid_scan, 256, 0, s>>>(d);
+  k_scatter<<<c->grid_bead, 256, 0, s>>>(d);
+  mark(c, c->ev_step, k++);
+  k_candidates<<<c->grid_cand, 256, 0, s>>>(d, c->rt);
+  k_cand_overflow<<<c->nsm, 128, 0, s>>>(d, c->rt);
+  mark(c, c->ev_step, k++);
+  cudaError_t e = launch_match(c);
+  if (e != cudaSuccess) return e;
+  mark(c, c->ev_step, k++);
+  k_edit<<<c->grid_bead, 256, 0, s>>>(d, c->rt);
+  mark(c, c->ev_step, k++);
+  k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 0);
+  k_tiles<<<1, 1024, 0, s>>>(d, 1);
+  mark(c, c->ev_step, k++);
+  k_purge<<<c->grid_seg, 256, 0, s>>>(d, 0);
+  k_purge<<<c->grid_seg, 256, 0, s>>>(d, 1);
+  mark(c, c->ev_step, k++);
+  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->rt, 0);
+  k_finalize<<<(c->R + 255) / 256, 256, 0, s>>>(d);
+  mark(c, c->ev_step, k++);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_forces(dynbond_ctx* c) {
+  const Dev& d = c->d;
+  cudaStream_t s = c->stream;
+  size_t k = 0;
+  mark(c, c->ev_forces, k++);
+  cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * c->R, s);
+  k_tiles<<<1, 1024, 0, s>>>(d, 2);
+  mark(c, c->ev_forces, k++);
+  k_bond_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
+  mark(c, c->ev_forces, k++);
+  k_angle_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
+  mark(c, c->ev_forces, k++);
+  k_dihedral_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
+  mark(c, c->ev_forces, k++);
+  k_ev_out<<<1, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t capture(dynbond_ctx* c, cudaError_t (*enqueue)(dynbond_ctx*), cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = enqueue(c);
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return e1 != cudaSuccess ? e1 : e2;
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+  }
+  return e;
+}
+
+dynbond_status device_status(dynbond_ctx* c) {
+  unsigned err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, c->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->sticky = DYNBOND_ECUDA;
+    return fail(c, DYNBOND_ECUDA, std::string("device execution: ") + cudaGetErrorString(e));
+  }
+  if (!err) return DYNBOND_OK;
+  dynbond_status s;
+  std::string msg;
+  if (err & ERR_POS) {
+    s = DYNBOND_EINVAL;
+    msg = "a position lies outside [0, box_q) of its replica";
+  } else if (err & ERR_TIMEOUT) {
+    s = DYNBOND_ETIMEOUT;
+    msg = "a bounded device-side wait gave up (grid barrier or look-back)";
+  } else if (err & ERR_ROUNDS) {
+    s = DYNBOND_ENOTCONVERGED;
+    msg = "matching did not reach a fixpoint within DYNBOND_MAX_ROUNDS rounds";
+  } else if (err & ERR_CAND) {
+    s = DYNBOND_ECAPACITY;
+    msg = "a bead had more than DYNBOND_MAX_CANDIDATES creation candidates";
+  } else if (err & ERR_CAND_CAP) {
+    s = DYNBOND_ECAPACITY;
+    msg = "candidate buffer exhausted";
+  } else if (err & ERR_INTERNAL) {
+    s = DYNBOND_ECAPACITY;
+    msg = "internal consistency check failed (interaction record out of range)";
+  } else {
+    s = DYNBOND_ECAPACITY;
+    msg = "bond slot capacity exceeded";
+  }
+  c->sticky = s;
+  return fail(c, s, msg);
+}
+
+void collect_profile(dynbond_ctx* c, int which) {
+  std::vector<cudaEvent_t>& ev = which == 1 ? c->ev_step : c->ev_forces;
+  std::vector<float>& out = which == 1 ? c->last_step_ms : c->last_forces_ms;
+  out.assign(ev.size() - 1, 0.f);
+  for (size_t k = 0; k + 1 < ev.size(); ++k) cudaEventElapsedTime(&out[k], ev[k], ev[k + 1]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* dynbond_status_string(dynbond_status s) {
+  switch (s) {
+    case DYNBOND_OK: return "ok";
+    case DYNBOND_EINVAL: return "invalid argument";
+    case DYNBOND_ENOMEM: return "out of memory";
+    case DYNBOND_ECAPACITY: return "capacity exceeded";
+    case DYNBOND_ECUDA: return "CUDA error";
+    case DYNBOND_ETIMEOUT: return "device wait timed out";
+    case DYNBOND_ENOTCONVERGED: return "matching did not converge";
+  }
+  return "unknown status";
+}
+
+const char* dynbond_last_error(const dynbond_ctx* c) { return c ? c->last_error.c_str() : g_create_error.c_str(); }
+
+void dynbond_destroy(dynbond_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->g_step) cudaGraphExecDestroy(c->g_step);
+  if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
+  for (cudaEvent_t e : c->ev_step) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_forces) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+}  // extern "C"
+
+namespace {
+
+
+dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const dynbond_rule* rules, int32_t n_rules,
+                           const dynbond_system* sys, const dynbond_forcefield* ff, dynbond_stream stream) {
+  if (!params || !sys || !ff) return (fail(c, DYNBOND_EINVAL, "params, system and forcefield are required"));
+  c->prm = *params;
+  c->stream = (cudaStream_t)stream;
+  c->profile = (params->flags & DYNBOND_FLAG_PROFILE) != 0;
+  c->use_graph = (params->flags & DYNBOND_FLAG_NO_GRAPH) == 0;
+  if (params->max_rounds < 0 || params->prob_mode < 0 || params->prob_mode > 1 || params->cell_scale < 0)
+    return (fail(c, DYNBOND_EINVAL, "bad max_rounds, prob_mode or cell_scale"));
+  dynbond_status st = build_rules(c, rules, n_rules);
+  if (st) return (st);
+
+  // ---- system validation (host)
+  const int R = sys->n_replicas;
+  if (R < 1 || !sys->bead_offset || !sys->box_q || !sys->bead_type)
+    return (fail(c, DYNBOND_EINVAL, "n_replicas >= 1 with bead_offset, box_q and bead_type required"));
+  if (sys->bead_offset[0] != 0) return (fail(c, DYNBOND_EINVAL, "bead_offset[0] must be 0"));
+  for (int r = 0; r < R; ++r) {
+    if (sys->bead_offset[r + 1] <= sys->bead_offset[r])
+      return (fail(c, DYNBOND_EINVAL, "every replica needs at least one bead (offsets increasing)"));
+    if (sys->box_q[r] < 2 || sys->box_q[r] >= (1ll << 31))
+      return (fail(c, DYNBOND_EINVAL, "box_q must lie in [2, 2^31)"));
+  }
+  const long long N = sys->bead_offset[R];
+  if (N >= (1ll << 28)) return (fail(c, DYNBOND_EINVAL, "at most 2^28 - 1 beads"));
+  c->N = N;
+  c->R = R;
+  std::vector<int> rep(N);
+  for (int r = 0; r < R; ++r)
+    for (long long i = sys->bead_offset[r]; i < sys->bead_offset[r + 1]; ++i) rep[i] = r;
+  std::vector<unsigned char> type(N);
+  for (long long i = 0; i < N; ++i) {
+    if (sys->bead_type[i] < 0 || sys->bead_type[i] >= DYNBOND_MAX_TYPES)
+      return (fail(c, DYNBOND_EINVAL, "bead types must lie in 0..15"));
+    type[i] = (unsigned char)sys->bead_type[i];
+  }
+  std::vector<uint4> slots(N, make_uint4(0, 0, 0, 0));
+  std::vector<int> deg(N, 0);
+  std::vector<long long> nb_rep(R, 0);
+  if (sys->n_bonds < 0 || (sys->n_bonds > 0 && !sys->bonds)) return (fail(c, DYNBOND_EINVAL, "bad bond list"));
+  for (long long k = 0; k < sys->n_bonds; ++k) {
+    long long i = sys->bonds[4 * k], j = sys->bonds[4 * k + 1];
+    int ti = sys->bonds[4 * k + 2], tj = sys->bonds[4 * k + 3];
+    if (i < 0 || j < 0 || i >= N || j >= N || i == j || rep[i] != rep[j] || !btype_ok(ti) || !btype_ok(tj))
+      return (fail(c, DYNBOND_EINVAL, "bond " + std::to_string(k) + " is malformed"));
+    for (int q = 0; q < deg[i]; ++q)
+      if ((int)(((unsigned*)&slots[i])[q] >> 4) == j)
+        return (fail(c, DYNBOND_EINVAL, "bond " + std::to_string(k) + " is listed twice"));
+    if (deg[i] >= SLOTS || deg[j] >= SLOTS)
+      return (fail(c, DYNBOND_EINVAL, "more than 4 bonds on one bead"));
+    ((unsigned*)&slots[i])[deg[i]++] = ((unsigned)j << 4) | (unsigned)ti;
+    ((unsigned*)&slots[j])[deg[j]++] = ((unsigned)i << 4) | (unsigned)tj;
+    nb_rep[rep[i]] += 1;
+  }
+  for (int t = 0; t < 16; ++t) {
+    c->ff.bond_k[t] = (float)ff->bond_k[t];
+    c->ff.bond_r0[t] = (float)ff->bond_r0[t];
+    c->ff.angle_k[t] = (float)ff->angle_k[t];
+    c->ff.dih_k[t] = (float)ff->dihedral_k[t];
+    c->ff.dih_d[t] = (float)ff->dihedral_d[t];
+  }
+
+  // ---- device
+  CUDA_TRY(c, cudaGetDevice(&c->device));
+  CUDA_TRY(c, cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+
+  // cells: edge >= largest creation distance, widened so a cell holds about
+  // one creation-capable bead (results do not depend on the choice)
+  std::vector<int> nc(R);
+  std::vector<long long> cell_base(R + 1, 0);
+  long long w = 0;
+  while (w * w < c->rt.r2max) ++w;  // smallest integer width covering the reach
+  if (c->rt.r2max > 0 && w < 1) w = 1;
+  for (int r = 0; r < R; ++r) {
+    long long L = sys->box_q[r];
+    long long ncap = w > 0 ? L / w : 1;
+    double scale = params->cell_scale;
+    if (scale <= 0) {
+      long long ne = 0;
+      for (long long i = sys->bead_offset[r]; i < sys->bead_offset[r + 1]; ++i) ne += c->rt.role_rules[type[i]] != 0;
+      double vol = std::pow((double)L, 3.0);
+      double occ = w > 0 && ne > 0 ? (double)ne * std::pow((double)w, 3.0) / vol : 1.0;
+      scale = std::max(1.0, std::cbrt(1.0 / std::max(occ, 1e-12)));
+    }
+    long long n = w > 0 ? (long long)((double)L / (scale * (double)w)) : 1;
+    n = std::max<long long>(1, std::min<long long>({n, ncap, 1024}));
+    nc[r] = (int)n;
+    cell_base[r + 1] = cell_base[r] + n * n * n;
+  }
+  c->n_cells = cell_base[R];
+  c->W = N / 32 + 1;
+
+  Dev& d = c->d;
+  d.N = N;
+  d.R = R;
+  d.n_cells = c->n_cells;
+  d.spin_limit = params->spin_limit > 0 ? params->spin_limit : (1 << 24);
+  long long* p_off;
+  long long* p_box;
+  long long* p_cb;
+  int* p_nc;
+  int* p_rep;
+  unsigned char* p_type;
+  unsigned* p_stream;
+  unsigned long long *p_tf, *p_tb;
+#define ALLOC(ptr, n)                         \
+  do {                                        \
+    dynbond_status s_ = dalloc(c, &(ptr), (size_t)(n)); \
+    if (s_) return (s_);                  \
+  } while (0)
+  ALLOC(p_off, R + 1);
+  ALLOC(p_box, R);
+  ALLOC(p_cb, R + 1);
+  ALLOC(p_nc, R);
+  ALLOC(p_rep, N);
+  ALLOC(p_type, N);
+  ALLOC(p_stream, R);
+  ALLOC(p_tf, (size_t)R * MAXR);
+  ALLOC(p_tb, (size_t)R * MAXR);
+  ALLOC(d.args, 1);
+  ALLOC(d.slots, N);
+  ALLOC(d.ang, 6 * N);
+  ALLOC(d.dih, 18 * N);
+  ALLOC(d.n_ang, R);
+  ALLOC(d.n_dih, R);
+  ALLOC(d.n_bonds, R);
+  ALLOC(d.cnt, 1);
+  ALLOC(d.err, 1);
+  ALLOC(d.cell_start, c->n_cells + 1);
+  ALLOC(d.bead_cell, N);
+  ALLOC(d.bead_rank, N);
+  ALLOC(d.sorted, N);
+  d.cand_cap = 2 * N + 65536;
+  ALLOC(d.cand, d.cand_cap);
+  ALLOC(d.cand_start, N);
+  ALLOC(d.cand_len, N);
+  ALLOC(d.act_c, N);
+  ALLOC(d.ovf, N);
+  ALLOC(d.brk, 4 * N);
+  ALLOC(d.brk_len, N);
+  ALLOC(d.killmask, N);
+  ALLOC(d.act_b, N);
+  ALLOC(d.bm_ca, c->W);
+  ALLOC(d.bm_ba, c->W);
+  ALLOC(d.bm_dirty, c->W);
+  ALLOC(d.bm_new, c->W);
+  ALLOC(d.mate, 2 * N);
+  ALLOC(d.nom, 2 * N);
+  ALLOC(d.ptr, 2 * N);
+  ALLOC(d.rem, N);
+  ALLOC(d.newp, N);
+  ALLOC(d.nbl, 2 * N + 1);
+  ALLOC(d.nbl_first, R);
+  ALLOC(d.tb_ang, R + 1);
+  ALLOC(d.tb_dih, R + 1);
+  ALLOC(d.tb_nb, R + 1);
+  ALLOC(d.tb_beads, R + 1);
+  ALLOC(d.ev_acc, 7 * R);
+  // per-call counters zeroed together: kept/added counts, new-bond counts,
+  // round flags, statistics
+  {
+    size_t ints = 5 * (size_t)R + 2 * (size_t)R;
+    size_t bytes = ((ints * sizeof(int) + 15) / 16) * 16 + (size_t)R * NSTAT * sizeof(long long);
+    char* base;
+    ALLOC(base, bytes);
+    c->small = base;
+    c->small_bytes = bytes;
+    int* ip = (int*)base;
+    d.kept_ang = ip;
+    d.kept_dih = ip + R;
+    d.added_ang = ip + 2 * R;
+    d.added_dih = ip + 3 * R;
+    d.nbl_count = ip + 4 * R;
+    d.round_hit = ip + 5 * R;
+    d.stats = (long long*)(base + ((ints * sizeof(int) + 15) / 16) * 16);
+  }
+  {
+    c->st_scan_n = c->n_cells / (256 * 8) + 2;
+    c->st_nb_n = N / (256 * 4) + 2;
+    c->st_pa_n = 6 * N / PURGE_TILE + R + 2;
+    c->st_pd_n = 18 * N / PURGE_TILE + R + 2;
+    c->st_rb_n = 2 * N / REBUILD_TILE + R + 2;
+    long long tot = c->st_scan_n + c->st_nb_n + c->st_pa_n + c->st_pd_n + c->st_rb_n;
+    unsigned long long* base;
+    ALLOC(base, tot);
+    c->status_all = base;
+    c->status_bytes = (size_t)tot * 8;
+    d.st_scan = base;
+    d.st_nb = d.st_scan + c->st_scan_n;
+    d.st_pa = d.st_nb + c->st_nb_n;
+    d.st_pd = d.st_pa + c->st_pa_n;
+    d.st_rb = d.st_pd + c->st_pd_n;
+  }
+  ALLOC(c->h2d_pos, N);
+  ALLOC(c->d2h_force, N);
+  ALLOC(c->d2h_ev, 7 * R);
+#undef ALLOC
+  d.off = p_off;
+  d.box = p_box;
+  d.cell_base = p_cb;
+  d.nc = p_nc;
+  d.rep = p_rep;
+  d.type = p_type;
+  d.stream = p_stream;
+  d.T_form = p_tf;
+  d.T_break = p_tb;
+
+  // ---- upload
+  std::vector<unsigned long long> tf((size_t)R * MAXR, 0), tb((size_t)R * MAXR, 0);
+  std::vector<unsigned> strm(R);
+  std::vector<int> tbeads(R + 1, 0);
+  for (int r = 0; r < R; ++r) {
+    double fs = sys->form_scale ? sys->form_scale[r] : 1.0, bs = sys->break_scale ? sys->break_scale[r] : 1.0;
+    if (!std::isfinite(fs) || !std::isfinite(bs) || fs < 0 || bs < 0)
+      return (fail(c, DYNBOND_EINVAL, "probability scales must be finite and >= 0"));
+    for (int k = 0; k < n_rules; ++k) {
+      tf[(size_t)r * MAXR + k] = prob_threshold(std::min(1.0, rules[k].prob * fs));
+      tb[(size_t)r * MAXR + k] = prob_threshold(std::min(1.0, rules[k].prob * bs));
+    }
+    strm[r] = sys->rng_stream ? sys->rng_stream[r] : (unsigned)r;
+    long long n = sys->bead_offset[r + 1] - sys->bead_offset[r];
+    tbeads[r + 1] = tbeads[r] + (int)((n + BEAD_TILE - 1) / BEAD_TILE);
+  }
+  std::vector<long long> boxv(sys->box_q, sys->box_q + R), offv(sys->bead_offset, sys->bead_offset + R + 1);
+  std::vector<int> zeros(R, 0);
+  cudaStream_t s = c->stream;
+  CUDA_TRY(c, cudaMemcpyAsync(p_off, offv.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_box, boxv.data(), 8 * R, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_cb, cell_base.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_rep, rep.data(), 4 * N, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_type, type.data(), N, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_stream, strm.data(), 4 * R, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_tf, tf.data(), 8 * tf.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(p_tb, tb.data(), 8 * tb.size(), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(d.slots, slots.data(), 16 * N, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(d.n_bonds, nb_rep.data(), 8 * R, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemcpyAsync(d.tb_beads, tbeads.data(), 4 * (R + 1), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
+  CUDA_TRY(c, cudaMemsetAsync(d.n_ang, 0, 4 * R, s));
+  CUDA_TRY(c, cudaMemsetAsync(d.n_dih, 0, 4 * R, s));
+  CUDA_TRY(c, cudaMemsetAsync(d.args, 0, sizeof(CallArgs), s));
+
+  // ---- launch geometry
+  c->grid_bead = bounded_grid(N, 256, c->nsm * 8);
+  c->grid_scan = bounded_grid(c->n_cells, 256 * 8, c->nsm * 4);
+  c->grid_cand = bounded_grid(N, 256, c->nsm * 8);
+  c->grid_nb = bounded_grid(N, 256 * 4, c->nsm * 4);
+  c->grid_seg = c->nsm * 4;
+  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 256, 2),
+                                       bounded_grid(N, 256, c->nsm * 2)));
+
+  // ---- initial interactions: the typed set of every path of the initial graph
+  CUDA_TRY(c, cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s));
+  CUDA_TRY(c, cudaMemsetAsync(c->small, 0, c->small_bytes, s));
+  CUDA_TRY(c, cudaMemsetAsync(c->status_all, 0, c->status_bytes, s));
+  k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 1);
+  k_tiles<<<1, 1024, 0, s>>>(d, 1);
+  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->rt, 1);
+  k_finalize<<<(R + 255) / 256, 256, 0, s>>>(d);
+  CUDA_TRY(c, cudaGetLastError());
+  st = device_status(c);
+  if (st) return (st);
+
+  // ---- profiling events and graphs
+  if (c->profile) {
+    c->names_step = {"step_setup", "bead", "cells", "candidates", "match", "edit", "newbonds", "purge", "rebuild"};
+    c->names_forces = {"forces_setup", "bond_forces", "angle_forces", "dihedral_forces"};
+    c->ev_step.resize(c->names_step.size() + 1);
+    c->ev_forces.resize(c->names_forces.size() + 1);
+    for (auto& e : c->ev_step) CUDA_TRY(c, cudaEventCreate(&e));
+    for (auto& e : c->ev_forces) CUDA_TRY(c, cudaEventCreate(&e));
+  }
+  if (c->use_graph) {
+    if (capture(c, enqueue_step, &c->g_step) != cudaSuccess ||
+        capture(c, enqueue_forces, &c->g_forces) != cudaSuccess) {
+      if (c->g_step) cudaGraphExecDestroy(c->g_step);
+      if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
+      c->g_step = c->g_forces = nullptr;
+      c->use_graph = false;
+      cudaGetLastError();
+      c->last_error = "CUDA graph capture unavailable; launching kernels directly";
+    }
+  }
+  return DYNBOND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dynbond_status dynbond_create(const dynbond_params* params, const dynbond_rule* rules, int32_t n_rules,
+                              const dynbond_system* sys, const dynbond_forcefield* ff, dynbond_stream stream,
+                              dynbond_ctx** out) {
+  if (!out) return DYNBOND_EINVAL;
+  *out = nullptr;
+  dynbond_ctx* c = new dynbond_ctx();
+  dynbond_status st = create_impl(c, params, rules, n_rules, sys, ff, stream);
+  if (st != DYNBOND_OK) {
+    g_create_error = c->last_error;
+    dynbond_destroy(c);
+    return st;
+  }
+  *out = c;
+  return DYNBOND_OK;
+}
+
+dynbond_status dynbond_step(dynbond_ctx* c, const int32_t* d_pos, uint64_t step, dynbond_stats* h_stats) {
+  if (!c || !d_pos) return DYNBOND_EINVAL;
+  if (c->sticky) return c->sticky;
+  k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, step, 1, 0);
+  cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_step, c->stream) : enqueue_step(c);
+  if (e != cudaSuccess) {
+    c->sticky = DYNBOND_ECUDA;
+    return fail(c, DYNBOND_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  }
+  if (c->profile) c->last_profiled |= 1;
+  if (h_stats) {
+    dynbond_status st = device_status(c);
+    if (st) return st;
+    static_assert(sizeof(dynbond_stats) == NSTAT * sizeof(long long), "stats layout");
+    CUDA_TRY(c, cudaMemcpy(h_stats, c->d.stats, sizeof(dynbond_stats) * c->R, cudaMemcpyDeviceToHost));
+  }
+  return DYNBOND_OK;
+}
+
+dynbond_status dynbond_forces(dynbond_ctx* c, const int32_t* d_pos, float* d_force, double* d_ev) {
+  if (!c || !d_pos || !d_force || !d_ev) return DYNBOND_EINVAL;
+  if (c->sticky) return c->sticky;
+  k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, (float4*)d_force, d_ev, 0, 0, 1);
+  cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_forces, c->stream) : enqueue_forces(c);
+  if (e != cudaSuccess) {
+    c->sticky = DYNBOND_ECUDA;
+    return fail(c, DYNBOND_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  }
+  if (c->profile) c->last_profiled |= 2;
+  return DYNBOND_OK;
+}
+
+dynbond_status dynbond_run_host(dynbond_ctx* c, const int32_t* h_pos, uint64_t step, float* h_force, double* h_ev,
+                                dynbond_stats* h_stats) {
+  if (!c || !h_pos || !h_force || !h_ev) return DYNBOND_EINVAL;
+  if (c->sticky) return c->sticky;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h2d_pos, h_pos, 16 * c->N, cudaMemcpyHostToDevice, c->stream));
+  dynbond_status st = dynbond_step(c, (const int32_t*)c->h2d_pos, step, nullptr);
+  if (st) return st;
+  st = dynbond_forces(c, (const int32_t*)c->h2d_pos, (float*)c->d2h_force, c->d2h_ev);
+  if (st) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(h_force, c->d2h_force, 16 * c->N, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(h_ev, c->d2h_ev, 8 * 7 * c->R, cudaMemcpyDeviceToHost, c->stream));
+  st = device_status(c);
+  if (st) return st;
+  if (h_stats) CUDA_TRY(c, cudaMemcpy(h_stats, c->d.stats, sizeof(dynbond_stats) * c->R, cudaMemcpyDeviceToHost));
+  return DYNBOND_OK;
+}
+
+dynbond_status dynbond_sync(dynbond_ctx* c) {
+  if (!c) return DYNBOND_EINVAL;
+  if (c->sticky) return c->sticky;
+  return device_status(c);
+}
+
+dynbond_status dynbond_get_topology(dynbond_ctx* c, dynbond_topology* t) {
+  if (!c || !t) return DYNBOND_EINVAL;
+  dynbond_status st = device_status(c);
+  if (st && st != DYNBOND_OK && c->sticky == DYNBOND_ECUDA) return st;
+  const long long N = c->N;
+  const int R = c->R;
+  std::vector<uint4> slots(N);
+  std::vector<int> na(R), nd(R);
+  std::vector<long long> off(R + 1);
+  CUDA_TRY(c, cudaMemcpy(slots.data(), c->d.slots, 16 * N, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(na.data(), c->d.n_ang, 4 * R, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(nd.data(), c->d.n_dih, 4 * R, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(off.data(), c->d.off, 8 * (R + 1), cudaMemcpyDeviceToHost));
+  auto part = [](unsigned v) { return v ? (int)(v >> 4) : -1; };
+  auto stored = [&](long long x, long long y) {
+    const unsigned* s = (const unsigned*)&slots[x];
+    for (int q = 0; q < SLOTS; ++q)
+      if (s[q] && part(s[q]) == y) return (int)(s[q] & 15u);
+    return 0;
+  };
+  long long nb = 0, sa = 0, sd = 0;
+  for (long long i = 0; i < N; ++i) {
+    const unsigned* s = (const unsigned*)&slots[i];
+    for (int q = 0; q < SLOTS; ++q) nb += part(s[q]) > i;
+  }
+  for (int r = 0; r < R; ++r) {
+    sa += na[r];
+    sd += nd[r];
+  }
+  bool fill = t->bonds || t->angles || t->dihedrals;
+  if (fill) {
+    if ((t->bonds && t->n_bonds < nb) || (t->angles && t->n_angles < sa) || (t->dihedrals && t->n_dihedrals < sd))
+      return fail(c, DYNBOND_EINVAL, "topology arrays smaller than the counts");
+    if (t->bonds) {
+      std::vector<std::array<int, 4>> B;
+      B.reserve(nb);
+      for (long long i = 0; i < N; ++i) {
+        const unsigned* s = (const unsigned*)&slots[i];
+        for (int q = 0; q < SLOTS; ++q)
+          if (part(s[q]) > i) B.push_back({(int)i, part(s[q]), (int)(s[q] & 15u), stored(part(s[q]), i)});
+      }
+      std::sort(B.begin(), B.end());
+      std::memcpy(t->bonds, B.data(), B.size() * sizeof(B[0]));
+    }
+    if (t->angles) {
+      std::vector<std::array<int, 4>> A(sa);
+      long long at = 0;
+      for (int r = 0; r < R; ++r) {
+        if (na[r]) CUDA_TRY(c, cudaMemcpy(&A[at], c->d.ang + 6 * off[r], 16 * (size_t)na[r], cudaMemcpyDeviceToHost));
+        at += na[r];
+      }
+      std::sort(A.begin(), A.end());
+      std::memcpy(t->angles, A.data(), A.size() * sizeof(A[0]));
+    }
+    if (t->dihedrals) {
+      std::vector<std::array<int, 4>> D4(sd);
+      long long at = 0;
+      for (int r = 0; r < R; ++r) {
+        if (nd[r])
+          CUDA_TRY(c, cudaMemcpy(&D4[at], c->d.dih + 18 * off[r], 16 * (size_t)nd[r], cudaMemcpyDeviceToHost));
+        at += nd[r];
+      }
+      std::vector<std::array<int, 5>> D(sd);
+      for (long long k = 0; k < sd; ++k)
+        D[k] = {D4[k][0], D4[k][1], D4[k][2], D4[k][3] & 0x0FFFFFFF, (int)((unsigned)D4[k][3] >> 28)};
+      std::sort(D.begin(), D.end());
+      std::memcpy(t->dihedrals, D.data(), D.size() * sizeof(D[0]));
+    }
+  }
+  t->n_bonds = nb;
+  t->n_angles = sa;
+  t->n_dihedrals = sd;
+  return c->sticky;
+}
+
+dynbond_status dynbond_phase_times(dynbond_ctx* c, float* ms, const char** names, int32_t n, int32_t* n_out) {
+  if (!c) return DYNBOND_EINVAL;
+  if (!c->profile) return fail(c, DYNBOND_EINVAL, "context created without DYNBOND_FLAG_PROFILE");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->last_profiled & 1) collect_profile(c, 1);
+  if (c->last_profiled & 2) collect_profile(c, 2);
+  c->last_profiled = 0;
+  int k = 0;
+  for (size_t q = 0; q < c->last_step_ms.size(); ++q, ++k)
+    if (k < n) {
+      if (ms) ms[k] = c->last_step_ms[q];
+      if (names) names[k] = c->names_step[q];
+    }
+  for (size_t q = 0; q < c->last_forces_ms.size(); ++q, ++k)
+    if (k < n) {
+      if (ms) ms[k] = c->last_forces_ms[q];
+      if (names) names[k] = c->names_forces[q];
+    }
+  if (n_out) *n_out = k;
+  return DYNBOND_OK;
+}
+
+}  // extern "C"

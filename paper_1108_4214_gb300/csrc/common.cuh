@@ -1,0 +1,459 @@
+// Device-side building blocks of the dynamic-bonding library: the context
+// view passed to every kernel, the rule table, exact integer geometry, the
+// Philox4x32-10 generator, bitmaps, warp / block scans, a bounded single-pass
+// look-back for ordered compaction, and a bounded grid barrier.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dynbond.h"
+
+namespace dynbond {
+
+constexpr int SLOTS = DYNBOND_SLOTS;
+constexpr int MAXR = DYNBOND_MAX_RULES;
+constexpr int MAXC = DYNBOND_MAX_CANDIDATES;
+constexpr int MAX_ROUNDS = DYNBOND_MAX_ROUNDS;
+constexpr int NSTAT = 17;
+constexpr unsigned FULL = 0xffffffffu;
+
+// bits of the sticky device error word
+enum : unsigned {
+  ERR_POS = 1u,        // a position outside [0, box)
+  ERR_CAND = 2u,       // (unused: beads with many candidates take the exact overflow path)
+  ERR_CAND_CAP = 4u,   // candidate buffer exhausted
+  ERR_SLOTS = 8u,      // a bead would exceed SLOTS bonds (internal)
+  ERR_TIMEOUT = 16u,   // a bounded wait gave up
+  ERR_ROUNDS = 32u,    // matching needed more than MAX_ROUNDS rounds
+  ERR_INTERNAL = 64u,  // an internal consistency check failed (record out of range)
+};
+
+enum StatIdx {
+  ST_CANDIDATES, ST_CREATE_MATCHED, ST_FORMED, ST_BREAK_CANDIDATES, ST_BREAK_MATCHED, ST_BROKEN, ST_KILLED,
+  ST_CONVERTED, ST_ANG_REMOVED, ST_ANG_ADDED, ST_DIH_REMOVED, ST_DIH_ADDED, ST_NBONDS, ST_NANGLES,
+  ST_NDIHEDRALS, ST_CREATE_ROUNDS, ST_BREAK_ROUNDS
+};
+
+enum { TAG_FORM = 1u, TAG_BREAK = 2u };
+
+// Rule table, passed by value (kernel parameter space) so every lane reads it
+// through the constant cache.
+struct RuleTab {
+  int n;
+  int kind[MAXR];
+  int type[MAXR];
+  int type2[MAXR];
+  int maxn[MAXR];
+  uint32_t bead[MAXR][4];
+  uint32_t bond[MAXR][3];
+  long long r2[MAXR];
+  uint32_t pair_rules[16][16];  // creation rules whose bead masks admit (ti, tj) in some orientation
+  uint32_t role_rules[16];      // creation rules naming bead type t in either role
+  long long r2max;              // largest creation threshold
+  uint32_t breakish;            // bond types named by breakbond / convertbond / killbond
+  uint32_t reactive;
+  int n_maxbond, n_angle, n_dihedral;
+  int maxbond_idx[MAXR], angle_idx[MAXR], dihedral_idx[MAXR];
+  int pc13, pc14, max_rounds, prob_mode;
+  uint32_t key0, key1;
+};
+
+// Arguments that change from call to call, read from device memory so that a
+// captured CUDA graph can be replayed with new positions and call index.
+struct CallArgs {
+  const int4* pos;
+  float4* force;
+  double* ev;
+  unsigned long long step;
+};
+
+struct Counters {
+  int n_sorted;
+  int cand_used;
+  int n_act_c;
+  int n_act_b;
+  int n_nbl;
+  int n_ovf;
+  int ticket[8];
+  unsigned bar[2];
+  int rounds_done;
+  int round_matched[MAX_ROUNDS];
+};
+
+// Device view of a context.  Arrays marked [N] are indexed by global bead id.
+struct Dev {
+  long long N;
+  int R;
+  int spin_limit;
+  const long long* off;        // [R+1]
+  const long long* box;        // [R]
+  const int* nc;               // [R] cells per axis
+  const long long* cell_base;  // [R+1]
+  long long n_cells;
+  const int* rep;              // [N]
+  const unsigned char* type;   // [N]
+  const unsigned* stream;      // [R]
+  const unsigned long long* T_form;   // [R*MAXR]
+  const unsigned long long* T_break;  // [R*MAXR]
+  CallArgs* args;
+  // topology
+  uint4* slots;                // [N] (partner << 4 | stored type), 0 = empty
+  int4* ang;                   // replica r owns [6*off[r], 6*off[r+1])
+  int4* dih;                   // replica r owns [18*off[r], 18*off[r+1]); w = d | type << 28
+  int* n_ang;                  // [R]
+  int* n_dih;                  // [R]
+  int* kept_ang;               // [R]
+  int* kept_dih;               // [R]
+  int* added_ang;              // [R]
+  int* added_dih;              // [R]
+  long long* n_bonds;          // [R]
+  // per-call scratch
+  Counters* cnt;
+  unsigned* err;               // sticky error word
+  int* cell_start;             // [n_cells + 1]
+  int* bead_cell;              // [N]
+  int* bead_rank;              // [N]
+  int4* sorted;                // [N] (x, y, z, gid << 4 | type)
+  int4* cand;                  // [cand_cap] (partner, rule | mytype << 8, d2 lo, d2 hi)
+  long long cand_cap;
+  int* cand_start;             // [N]
+  int* cand_len;               // [N]
+  int* act_c;                  // [N]
+  int* ovf;                    // [N] sorted indices of beads with more than MAXC candidates
+  int4* brk;                   // [N*4] (partner, rule, key lo, key hi), key = -d2
+  unsigned char* brk_len;      // [N]
+  unsigned char* killmask;     // [N]
+  int* act_b;                  // [N]
+  unsigned* bm_ca;             // [W] creation-active beads
+  unsigned* bm_ba;             // [W] breakage/kill-active beads
+  unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
+  unsigned* bm_new;            // [W] beads with a formed or retyped bond
+  int* mate;                   // [2*N] creation / breakage partner, -1 = none
+  int* nom;                    // [2*N]
+  int* ptr;                    // [2*N]
+  int* round_hit;              // [2*R]
+  int4* rem;                   // [N] partners whose bond was removed or retyped
+  int2* newp;                  // [N] formed partner, retyped partner
+  int4* nbl;                   // new-bond list (u, v, replica, 0), u < v
+  int* nbl_count;              // [R]
+  int* nbl_first;              // [R]
+  int* tb_ang;                 // [R+1] tile bases
+  int* tb_dih;                 // [R+1]
+  int* tb_nb;                  // [R+1]
+  int* tb_beads;               // [R+1] (static)
+  unsigned long long* st_scan; // look-back status words
+  unsigned long long* st_nb;
+  unsigned long long* st_pa;
+  unsigned long long* st_pd;
+  unsigned long long* st_rb;
+  long long* stats;            // [R*NSTAT]
+  double* ev_acc;              // [R*7]
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int s_partner(unsigned v) { return v ? (int)(v >> 4) : -1; }
+__device__ __forceinline__ int s_type(unsigned v) { return (int)(v & 15u); }
+__device__ __forceinline__ unsigned s_get(const uint4& s, int k) {
+  return k == 0 ? s.x : k == 1 ? s.y : k == 2 ? s.z : s.w;
+}
+__device__ __forceinline__ void s_set(uint4& s, int k, unsigned v) {
+  if (k == 0) s.x = v;
+  else if (k == 1) s.y = v;
+  else if (k == 2) s.z = v;
+  else s.w = v;
+}
+__device__ __forceinline__ int s_deg(const uint4& s) { return (s.x != 0) + (s.y != 0) + (s.z != 0) + (s.w != 0); }
+// type that the bead with slots s stores for its bond to q, or 0 if none
+__device__ __forceinline__ int s_type_to(const uint4& s, int q) {
+  unsigned want = (unsigned)q << 4;
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    unsigned v = s_get(s, k);
+    if (v && (v & ~15u) == want) return s_type(v);
+  }
+  return 0;
+}
+__device__ __forceinline__ bool has_bit(uint32_t m, int t) { return (m >> t) & 1u; }
+
+// minimum-image component of xi - xj for a box edge L (2 dx in (-L, L])
+__device__ __forceinline__ int wrap_dx(int dx, int L) {
+  int half_dn = L >> 1, half_up = (L >> 1) + (L & 1);
+  if (dx > half_dn) dx -= L;
+  else if (dx <= -half_up) dx += L;
+  return dx;
+}
+__device__ __forceinline__ long long dist2(const int4& a, const int4& b, int L) {
+  long long x = wrap_dx(a.x - b.x, L), y = wrap_dx(a.y - b.y, L), z = wrap_dx(a.z - b.z, L);
+  return x * x + y * y + z * z;
+}
+
+__device__ __forceinline__ int find_rep(const long long* base, int R, long long x) {
+  // largest r with base[r] <= x (base[R] > x)
+  int lo = 0, hi = R - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int find_seg(const int* base, int R, int x) {
+  int lo = 0, hi = R - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int ld_cg(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round the counter
+// words 0 and 2 are multiplied by the two round multipliers, high halves are
+// xored with the other counter words and the round key, and the key advances
+// by the two Weyl increments.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+    unsigned h0 = __umulhi(m0, c.x), l0 = m0 * c.x;
+    unsigned h1 = __umulhi(m1, c.z), l1 = m1 * c.z;
+    c = make_uint4(h1 ^ c.y ^ k.x, l1, h0 ^ c.w ^ k.y, l0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// One Bernoulli trial of the pair (a, b), a < b, global ids.
+__device__ __forceinline__ bool trial(const Dev& d, const RuleTab& rt, int a, int b, int r, unsigned tag,
+                                      unsigned long long T) {
+  long long o = d.off[r];
+  uint4 c = make_uint4((unsigned)(a - o), (unsigned)(b - o), (unsigned)d.args->step,
+                       (tag << 24) | (d.stream[r] & 0xFFFFFFu));
+  uint4 u = philox4x32_10(c, make_uint2(rt.key0, rt.key1));
+  if (rt.prob_mode == 0) return (unsigned long long)u.x < T;
+  return (unsigned long long)u.x + (unsigned long long)u.y < 2ull * T;
+}
+
+// ---------------------------------------------------------------------------
+// rules
+// ---------------------------------------------------------------------------
+
+// May a bead of bead type bt with slots s receive one more bond stored as nt?
+__device__ __forceinline__ bool maxbond_ok(const RuleTab& rt, int bt, const uint4& s, int nt) {
+  if (s_deg(s) >= SLOTS) return false;
+  for (int m = 0; m < rt.n_maxbond; ++m) {
+    int k = rt.maxbond_idx[m];
+    if (!has_bit(rt.bead[k][0], bt) || !has_bit(rt.bond[k][0], nt)) continue;
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      unsigned v = s_get(s, q);
+      cnt += (v != 0) && has_bit(rt.bond[k][0], s_type(v));
+    }
+    if (cnt >= rt.maxn[k]) return false;
+  }
+  return true;
+}
+
+// Can the bead take part in any creation pair (reactive, named by a creation
+// rule in some role with room for the type it would store)?
+__device__ __forceinline__ bool creation_eligible(const RuleTab& rt, int bt, const uint4& s) {
+  if (!has_bit(rt.reactive, bt)) return false;
+  uint32_t m = rt.role_rules[bt];
+  while (m) {
+    int k = __ffs(m) - 1;
+    m &= m - 1;
+    if (has_bit(rt.bead[k][0], bt) && maxbond_ok(rt, bt, s, rt.type[k])) return true;
+    int t2 = rt.kind[k] == DYNBOND_CREATEDIRBOND ? rt.type2[k] : rt.type[k];
+    if (has_bit(rt.bead[k][1], bt) && maxbond_ok(rt, bt, s, t2)) return true;
+  }
+  return false;
+}
+
+// Last creation rule matching the pair (a < b): bead types, distance and
+// maxbond at both ends; orientation a-first is tried first.  Returns the rule
+// (or -1) and the types a and b would store.
+__device__ __forceinline__ int creation_rule(const RuleTab& rt, int ta, int tb, const uint4& sa, const uint4& sb,
+                                             long long d2, int* sta, int* stb) {
+  uint32_t m = rt.pair_rules[ta][tb];
+  while (m) {
+    int k = 31 - __clz(m);
+    m &= ~(1u << k);
+    if (d2 > rt.r2[k]) continue;
+    int t1 = rt.type[k], t2 = rt.kind[k] == DYNBOND_CREATEDIRBOND ? rt.type2[k] : rt.type[k];
+    if (has_bit(rt.bead[k][0], ta) && has_bit(rt.bead[k][1], tb) && maxbond_ok(rt, ta, sa, t1) &&
+        maxbond_ok(rt, tb, sb, t2)) {
+      *sta = t1;
+      *stb = t2;
+      return k;
+    }
+    if (has_bit(rt.bead[k][0], tb) && has_bit(rt.bead[k][1], ta) && maxbond_ok(rt, tb, sb, t1) &&
+        maxbond_ok(rt, ta, sa, t2)) {
+      *sta = t2;
+      *stb = t1;
+      return k;
+    }
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int angle_type(const RuleTab& rt, int ta, int tb, int tc, int t_ba, int t_bc) {
+  for (int q = 0; q < rt.n_angle; ++q) {
+    int k = rt.angle_idx[q];
+    const uint32_t* bm = rt.bead[k];
+    bool fwd = has_bit(bm[0], ta) && has_bit(bm[1], tb) && has_bit(bm[2], tc) && has_bit(rt.bond[k][0], t_ba) &&
+               has_bit(rt.bond[k][1], t_bc);
+    bool rev = has_bit(bm[0], tc) && has_bit(bm[1], tb) && has_bit(bm[2], ta) && has_bit(rt.bond[k][0], t_bc) &&
+               has_bit(rt.bond[k][1], t_ba);
+    if (fwd || rev) return rt.type[k];
+  }
+  return 0;
+}
+
+// r = type B stores toward A, s = C toward B, sp = B toward C, t = C toward D
+__device__ __forceinline__ int dihedral_type(const RuleTab& rt, int ta, int tb, int tc, int td, int r, int s, int sp,
+                                             int t) {
+  for (int q = 0; q < rt.n_dihedral; ++q) {
+    int k = rt.dihedral_idx[q];
+    const uint32_t* bm = rt.bead[k];
+    const uint32_t* bd = rt.bond[k];
+    bool fwd = has_bit(bm[0], ta) && has_bit(bm[1], tb) && has_bit(bm[2], tc) && has_bit(bm[3], td) &&
+               has_bit(bd[0], r) && (has_bit(bd[1], s) || has_bit(bd[1], sp)) && has_bit(bd[2], t);
+    bool rev = has_bit(bm[0], td) && has_bit(bm[1], tc) && has_bit(bm[2], tb) && has_bit(bm[3], ta) &&
+               has_bit(bd[0], t) && (has_bit(bd[1], sp) || has_bit(bd[1], s)) && has_bit(bd[2], r);
+    if (fwd || rev) return rt.type[k];
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// scans
+// ---------------------------------------------------------------------------
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// Exclusive block scan (blockDim.x a multiple of 32, <= 1024); returns the
+// exclusive prefix of v and the block total in *total.  Uses `sh` (>= 33 T).
+template <class T>
+__device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) sh[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < nw ? sh[lane] : T(0);
+    T wi = warp_incl_scan(w);
+    if (lane < nw) sh[lane] = wi - w;
+    if (lane == nw - 1) sh[32] = wi;
+  }
+  __syncthreads();
+  T r = sh[wid] + inc - v;
+  *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// single-pass look-back (one thread per block calls it).  Tiles are taken in
+// ticket order, so every predecessor has started; each tile publishes its
+// aggregate after reading its input and its inclusive prefix after the
+// look-back.  status[t] = flag << 62 | value; flag 1 = aggregate, 2 = prefix.
+// Returns the exclusive prefix within the segment starting at seg_first, or
+// -1 after spin_limit unsuccessful polls (error bit set).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long lookback(unsigned long long* status, long long t, long long seg_first,
+                                              unsigned long long agg, int spin_limit, unsigned* err) {
+  const unsigned long long FA = 1ull << 62, FP = 2ull << 62, VM = (1ull << 62) - 1;
+  if (t == seg_first) {
+    st_release(status + t, FP | agg);
+    return 0;
+  }
+  st_release(status + t, FA | agg);
+  unsigned long long excl = 0;
+  long long p = t - 1;
+  int spins = 0;
+  while (true) {
+    unsigned long long s = ld_acquire(status + p);
+    unsigned long long f = s & (3ull << 62);
+    if (f == 0) {
+      if (++spins > spin_limit) {
+        atomicOr(err, ERR_TIMEOUT);
+        return -1;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    excl += s & VM;
+    if (f == FP || p == seg_first) break;
+    --p;
+  }
+  st_release(status + t, FP | (excl + agg));
+  return (long long)excl;
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier for co-resident (cooperative) launches, bounded: returns false
+// (error bit set) if the other blocks do not arrive within spin_limit polls.
+// bar[0] = arrivals, bar[1] = generation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int spin_limit, unsigned* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      int spins = 0;
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (++spins > spin_limit || (*(volatile unsigned*)err & ERR_TIMEOUT)) {
+          atomicOr(err, ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+}  // namespace dynbond

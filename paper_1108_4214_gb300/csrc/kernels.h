@@ -1,0 +1,39 @@
+// Kernel declarations and tile sizes shared by the kernel translation units
+// and the host context.
+#pragma once
+
+#include "common.cuh"
+
+namespace dynbond {
+
+constexpr int PURGE_TILE = 2048;   // 256 threads x 8 records
+constexpr int REBUILD_TILE = 256;  // new bonds per tile, one per thread
+constexpr int FORCE_TILE = 1024;   // records per force work item
+constexpr int BEAD_TILE = 1024;    // beads per force work item
+
+// bonded force-field tables in FP32 (kernel parameter space)
+struct FF {
+  float bond_k[16], bond_r0[16], angle_k[16], dih_k[16], dih_d[16];
+};
+
+__global__ void k_bead(Dev d, RuleTab rt);
+__global__ void k_scan_cells(Dev d);
+__global__ void k_scatter(Dev d);
+__global__ void k_candidates(Dev d, RuleTab rt);
+__global__ void k_cand_overflow(Dev d, RuleTab rt);
+__global__ void k_match(Dev d, RuleTab rt);
+__global__ void k_edit(Dev d, RuleTab rt);
+__global__ void k_newbonds(Dev d, int mode);
+__global__ void k_tiles(Dev d, int mode);
+__global__ void k_purge(Dev d, int which);
+__global__ void k_rebuild(Dev d, RuleTab rt, int all_new);
+__global__ void k_finalize(Dev d);
+__global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
+                           int set_pos, int set_force);
+
+__global__ void k_bond_forces(Dev d, FF ff);
+__global__ void k_angle_forces(Dev d, FF ff);
+__global__ void k_dihedral_forces(Dev d, FF ff);
+__global__ void k_ev_out(Dev d);
+
+}  // namespace dynbond

@@ -1,0 +1,969 @@
+// Kernels of one dynamic-bonding call (Svaneborg, arXiv:1108.4214, Appendix
+// steps 1-10), in launch order:
+//   k_bead        per bead: creation eligibility and cell histogram; breakage
+//                 nomination lists and killbond marks (steps 2-3, 5)
+//   k_scan_cells  exclusive scan of the cell histogram (single pass)
+//   k_scatter     counting-sort scatter of eligible beads into cell order
+//   k_candidates  per eligible bead: every creation partner in the 27
+//                 neighbouring cells, last-rule-wins typing, graph-distance
+//                 exclusion, maxbond (step 2); sorted per-bead lists
+//   k_match       rounds of mutual nomination for creation and breakage at
+//                 once (step 4), cooperative launch with a bounded barrier
+//   k_edit        trials, kill / break / convert / form applied to each
+//                 bead's own bond slots (steps 5, 7, 8)
+//   k_newbonds    ordered list of the bonds formed or retyped
+//   k_tiles       per-replica tile bases of the segmented passes
+//   k_purge       in-place ordered compaction of the angle / dihedral lists,
+//                 dropping records on removed or retyped bonds (step 6)
+//   k_rebuild     typed records of every path through a new bond (step 9)
+//   k_finalize    per-replica counts and statistics (step 10)
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dynbond {
+
+constexpr int PURGE_PER_THREAD = 8;
+constexpr int SCAN_PER_THREAD = 8;
+constexpr int NB_PER_THREAD = 4;
+
+__device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
+  if (v) atomicAdd((unsigned long long*)&d.stats[(long long)r * NSTAT + k], (unsigned long long)v);
+}
+
+// warp-aggregated append of `want` items; returns this lane's first index
+__device__ __forceinline__ int warp_alloc(int* counter, int want) {
+  int lane = threadIdx.x & 31;
+  int incl = warp_incl_scan(want);
+  int total = __shfl_sync(FULL, incl, 31);
+  int base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, total);
+  base = __shfl_sync(FULL, base, 31);
+  return base + incl - want;
+}
+
+// ---------------------------------------------------------------------------
+// k_bead
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bead(Dev d, RuleTab rt) {
+  const int4* __restrict__ pos = d.args->pos;
+  const long long N = d.N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
+    long long i = base + threadIdx.x;
+    bool valid = i < N;
+    int nbrk = 0, ncand_b = 0, r = 0;
+    bool ba = false;
+    if (valid) {
+      r = d.rep[i];
+      int bt = d.type[i];
+      uint4 s = d.slots[i];
+      int4 p = pos[i];
+      int L = (int)d.box[r];
+      if (p.x < 0 || p.y < 0 || p.z < 0 || p.x >= L || p.y >= L || p.z >= L) {
+        atomicOr(d.err, ERR_POS);
+        d.bead_cell[i] = -1;
+      } else {
+        // creation: eligible beads are binned (Appendix step 2 searches them)
+        if (creation_eligible(rt, bt, s)) {
+          int nc = d.nc[r];
+          long long cx = (long long)p.x * nc / L, cy = (long long)p.y * nc / L, cz = (long long)p.z * nc / L;
+          long long c = d.cell_base[r] + (cx * nc + cy) * nc + cz;
+          d.bead_rank[i] = atomicAdd(&d.cell_start[c], 1);
+          d.bead_cell[i] = (int)c;
+        } else {
+          d.bead_cell[i] = -1;
+        }
+        // breakage: symmetric bonds of a type named by breakbond / convertbond /
+        // killbond (Appendix steps 3 and 5), both ends reactive
+        if (rt.breakish && has_bit(rt.reactive, bt)) {
+          unsigned km = 0;
+          int4 ent[SLOTS];
+#pragma unroll
+          for (int q = 0; q < SLOTS; ++q) {
+            unsigned v = s_get(s, q);
+            if (!v || !has_bit(rt.breakish, s_type(v))) continue;
+            int bty = s_type(v), j = s_partner(v);
+            if (!has_bit(rt.reactive, d.type[j])) continue;
+            if (s_type_to(d.slots[j], (int)i) != bty) continue;
+            long long dd = dist2(p, pos[j], L);
+            int rule = -1;
+            for (int k = 0; k < rt.n; ++k) {
+              int kd = rt.kind[k];
+              if (rt.type[k] != bty) continue;
+              if (kd == DYNBOND_KILLBOND && dd > rt.r2[k]) km |= 1u << q;
+              if ((kd == DYNBOND_BREAKBOND && dd > rt.r2[k]) || kd == DYNBOND_CONVERTBOND) rule = k;
+            }
+            if (rule < 0) continue;
+            // insert sorted by (-d2, partner)
+            long long key = -dd;
+            int at = nbrk;
+            while (at > 0) {
+              long long pk = ((long long)(unsigned)ent[at - 1].w << 32) | (unsigned)ent[at - 1].z;
+              if (pk < key || (pk == key && ent[at - 1].x < j)) break;
+              ent[at] = ent[at - 1];
+              --at;
+            }
+            ent[at] = make_int4(j, rule, (int)(unsigned)(unsigned long long)key, (int)(key >> 32));
+            ++nbrk;
+            ncand_b += j > i;
+          }
+          if (km || nbrk) {
+            ba = true;
+            d.killmask[i] = (unsigned char)km;
+            d.brk_len[i] = (unsigned char)nbrk;
+            for (int q = 0; q < nbrk; ++q) d.brk[4 * i + q] = ent[q];
+            if (nbrk) {
+              d.mate[N + i] = -1;
+              d.ptr[N + i] = 0;
+            }
+          }
+        }
+      }
+    }
+    unsigned m = __ballot_sync(FULL, ba);
+    if (lane == 0 && valid) d.bm_ba[i >> 5] = m;
+    int slot = warp_alloc(&d.cnt->n_act_b, nbrk > 0 ? 1 : 0);
+    if (nbrk > 0) d.act_b[slot] = (int)i;
+    if (valid) stat_add(d, r, ST_BREAK_CANDIDATES, ncand_b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan_cells: in-place exclusive scan of the cell histogram
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
+  __shared__ long long sh[33];
+  __shared__ long long s_excl;
+  __shared__ long long s_tile;
+  const long long n = d.n_cells;
+  const long long per_tile = (long long)blockDim.x * SCAN_PER_THREAD;
+  const long long ntiles = (n + per_tile - 1) / per_tile;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[0], 1);
+    __syncthreads();
+    long long t = s_tile;
+    if (t >= ntiles) break;
+    long long beg = t * per_tile + (long long)threadIdx.x * SCAN_PER_THREAD;
+    int v[SCAN_PER_THREAD];
+    long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+      v[k] = beg + k < n ? d.cell_start[beg + k] : 0;
+      sum += v[k];
+    }
+    long long tot;
+    long long ex = block_excl_scan(sum, sh, &tot);
+    if (threadIdx.x == 0) s_excl = lookback(d.st_scan, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
+    __syncthreads();
+    if (s_excl < 0) return;
+    long long pre = s_excl + ex;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+      if (beg + k < n) d.cell_start[beg + k] = (int)pre;
+      pre += v[k];
+    }
+    if (t == ntiles - 1 && threadIdx.x == blockDim.x - 1) {
+      d.cell_start[n] = (int)pre;
+      d.cnt->n_sorted = (int)pre;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(Dev d) {
+  const int4* __restrict__ pos = d.args->pos;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += stride) {
+    int c = d.bead_cell[i];
+    if (c < 0) continue;
+    int4 p = pos[i];
+    p.w = (int)((i << 4) | d.type[i]);
+    d.sorted[d.cell_start[c] + d.bead_rank[i]] = p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_candidates
+// ---------------------------------------------------------------------------
+
+// Graph distance test on the bond graph before the call: never at distance 1,
+// at 2 only with paircheck13, at 3 only with paircheck14, always beyond.
+__device__ __forceinline__ bool pair_eligible(const Dev& d, const RuleTab& rt, int i, int j, const uint4& si,
+                                              const uint4& sj) {
+  int ni[SLOTS], nj[SLOTS];
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    ni[q] = s_partner(s_get(si, q));
+    nj[q] = s_partner(s_get(sj, q));
+    if (ni[q] == j) return false;
+  }
+  bool g2 = false;
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q)
+#pragma unroll
+    for (int w = 0; w < SLOTS; ++w) g2 |= ni[q] >= 0 && ni[q] == nj[w];
+  if (g2) return rt.pc13 != 0;
+  bool g3 = false;
+  for (int q = 0; q < SLOTS && !g3; ++q) {
+    if (ni[q] < 0) continue;
+    uint4 sa = d.slots[ni[q]];
+#pragma unroll
+    for (int q2 = 0; q2 < SLOTS; ++q2) {
+      int b = s_partner(s_get(sa, q2));
+      if (b < 0) continue;
+#pragma unroll
+      for (int w = 0; w < SLOTS; ++w) g3 |= nj[w] == b;
+    }
+  }
+  if (g3) return rt.pc14 != 0;
+  return true;
+}
+
+// Visit every creation candidate of the eligible bead at sorted index e:
+// partners in the 27 neighbouring cells (distinct cells when a replica has
+// fewer than 3 per axis), last matching creation rule, graph-distance
+// exclusion.  visit(j, d2, rule, type this bead stores).
+template <class V>
+__device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab& rt, const int4& me, int i, V& visit) {
+  int ti = me.w & 15;
+  int r = d.rep[i];
+  int L = (int)d.box[r], nc = d.nc[r];
+  long long cb = d.cell_base[r];
+  uint4 si = d.slots[i];
+  int c0[3] = {(int)((long long)me.x * nc / L), (int)((long long)me.y * nc / L), (int)((long long)me.z * nc / L)};
+  int offs[3] = {0, 1, nc - 1};
+  int noff = nc >= 3 ? 3 : nc;
+  for (int a = 0; a < noff; ++a) {
+    int cx = (c0[0] + offs[a]) % nc;
+    for (int b = 0; b < noff; ++b) {
+      int cy = (c0[1] + offs[b]) % nc;
+      for (int c = 0; c < noff; ++c) {
+        int cz = (c0[2] + offs[c]) % nc;
+        long long cell = cb + ((long long)cx * nc + cy) * nc + cz;
+        int q0 = d.cell_start[cell], q1 = d.cell_start[cell + 1];
+        for (int q = q0; q < q1; ++q) {
+          int4 o = d.sorted[q];
+          int j = o.w >> 4, tj = o.w & 15;
+          if (j == i || !rt.pair_rules[ti][tj]) continue;
+          long long dd = dist2(me, o, L);
+          if (dd > rt.r2max) continue;
+          uint4 sj = d.slots[j];
+          int sta, stb, k;
+          if (i < j) k = creation_rule(rt, ti, tj, si, sj, dd, &sta, &stb);
+          else k = creation_rule(rt, tj, ti, sj, si, dd, &stb, &sta);
+          if (k < 0) continue;
+          if (!pair_eligible(d, rt, i, j, si, sj)) continue;
+          visit(j, dd, k, sta);
+        }
+      }
+    }
+  }
+}
+
+// sorted insertion into a per-thread list of at most MAXC entries
+struct LocalList {
+  long long kd[MAXC];
+  int kp[MAXC], ki[MAXC];
+  int cnt = 0, pairs = 0, me = 0;
+  bool overflow = false;
+  __device__ void operator()(int j, long long dd, int k, int sta) {
+    pairs += j > me;
+    if (cnt == MAXC) {
+      overflow = true;
+      return;
+    }
+    int at = cnt;
+    while (at > 0 && (kd[at - 1] > dd || (kd[at - 1] == dd && kp[at - 1] > j))) {
+      kd[at] = kd[at - 1];
+      kp[at] = kp[at - 1];
+      ki[at] = ki[at - 1];
+      --at;
+    }
+    kd[at] = dd;
+    kp[at] = j;
+    ki[at] = k | (sta << 8);
+    ++cnt;
+  }
+};
+
+__device__ __forceinline__ void activate_creator(const Dev& d, int i, int start, int len) {
+  d.cand_start[i] = start;
+  d.cand_len[i] = len;
+  d.mate[i] = -1;
+  d.ptr[i] = 0;
+  atomicOr(&d.bm_ca[i >> 5], 1u << (i & 31));
+}
+
+__global__ void __launch_bounds__(256) k_candidates(Dev d, RuleTab rt) {
+  const int n = d.cnt->n_sorted;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    int e = base + threadIdx.x;
+    int i = -1, r = 0;
+    LocalList ll;
+    if (e < n) {
+      int4 me = d.sorted[e];
+      i = me.w >> 4;
+      r = d.rep[i];
+      ll.me = i;
+      scan_candidates(d, rt, me, i, ll);
+    }
+    // beads with more than MAXC candidates are finished by k_cand_overflow
+    int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
+    if (ll.overflow) d.ovf[oslot] = e;
+    int cnt = ll.overflow ? 0 : ll.cnt;
+    int at = warp_alloc(&d.cnt->cand_used, cnt);
+    if (cnt > 0) {
+      if ((long long)at + cnt > d.cand_cap) {
+        atomicOr(d.err, ERR_CAND_CAP);
+        cnt = 0;
+      } else {
+        for (int q = 0; q < cnt; ++q)
+          d.cand[at + q] =
+              make_int4(ll.kp[q], ll.ki[q], (int)(unsigned)(unsigned long long)ll.kd[q], (int)(ll.kd[q] >> 32));
+        activate_creator(d, i, at, cnt);
+      }
+    }
+    int slot = warp_alloc(&d.cnt->n_act_c, cnt > 0 ? 1 : 0);
+    if (cnt > 0) d.act_c[slot] = i;
+    if (ll.pairs && !ll.overflow) stat_add(d, r, ST_CANDIDATES, ll.pairs);
+  }
+}
+
+struct CountV {
+  int cnt = 0, pairs = 0, me = 0;
+  __device__ void operator()(int j, long long, int, int) {
+    ++cnt;
+    pairs += j > me;
+  }
+};
+struct WriteV {
+  int4* out;
+  __device__ void operator()(int j, long long dd, int k, int sta) {
+    *out++ = make_int4(j, k | (sta << 8), (int)(unsigned)(unsigned long long)dd, (int)(dd >> 32));
+  }
+};
+
+// Exact path for beads with more than MAXC candidates: count, allocate,
+// write, then sort the bead's list by (d2, partner) in place.
+__global__ void __launch_bounds__(128) k_cand_overflow(Dev d, RuleTab rt) {
+  const int n = d.cnt->n_ovf;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    int4 me = d.sorted[d.ovf[k]];
+    int i = me.w >> 4;
+    CountV cv;
+    cv.me = i;
+    scan_candidates(d, rt, me, i, cv);
+    int at = atomicAdd(&d.cnt->cand_used, cv.cnt);
+    if ((long long)at + cv.cnt > d.cand_cap) {
+      atomicOr(d.err, ERR_CAND_CAP);
+      continue;
+    }
+    WriteV wv{d.cand + at};
+    scan_candidates(d, rt, me, i, wv);
+    int4* lst = d.cand + at;
+    for (int a = 1; a < cv.cnt; ++a) {
+      int4 x = lst[a];
+      long long kx = ((long long)x.w << 32) | (unsigned)x.z;
+      int b = a;
+      while (b > 0) {
+        int4 y = lst[b - 1];
+        long long ky = ((long long)y.w << 32) | (unsigned)y.z;
+        if (ky < kx || (ky == kx && y.x < x.x)) break;
+        lst[b] = y;
+        --b;
+      }
+      lst[b] = x;
+    }
+    activate_creator(d, i, at, cv.cnt);
+    d.act_c[atomicAdd(&d.cnt->n_act_c, 1)] = i;
+    stat_add(d, d.rep[i], ST_CANDIDATES, cv.pairs);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_match: rounds of mutual nomination (creation: nearest partner; breakage:
+// most distant; ties to the lower partner id), until a round matches nothing
+// or max_rounds rounds.  Per-bead lists are sorted, so a bead's nominee is
+// its first entry whose partner is still unmatched.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_match(Dev d, RuleTab rt) {
+  const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b, nA = na_c + na_b;
+  const long long N = d.N;
+  const int stride = gridDim.x * blockDim.x;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  int round = 0;
+  while (true) {
+    // nomination
+    for (int idx = g; idx < nA; idx += stride) {
+      int sys = idx >= na_c;
+      int i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
+      long long o = sys ? N : 0;
+      if (d.mate[o + i] != -1) continue;
+      int p = d.ptr[o + i];
+      int len = sys ? d.brk_len[i] : d.cand_len[i];
+      const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
+      int j = -1;
+      while (p < len) {
+        int q = lst[p].x;
+        if (ld_cg(d.mate + o + q) == -1) {
+          j = q;
+          break;
+        }
+        ++p;
+      }
+      d.ptr[o + i] = p;
+      d.nom[o + i] = j;
+    }
+    if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    // mutual nominations are matched
+    for (int idx = g; idx < nA; idx += stride) {
+      int sys = idx >= na_c;
+      int i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
+      long long o = sys ? N : 0;
+      if (d.mate[o + i] != -1) continue;
+      int j = d.nom[o + i];
+      if (j >= 0 && ld_cg(d.nom + o + j) == i) {
+        d.mate[o + i] = j;
+        if (i < j) {
+          int r = d.rep[i];
+          atomicAdd(&d.cnt->round_matched[round], 1);
+          d.round_hit[sys * d.R + r] = 1;
+          stat_add(d, r, sys ? ST_BREAK_MATCHED : ST_CREATE_MATCHED, 1);
+        }
+      }
+    }
+    if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    int matched = ld_cg(&d.cnt->round_matched[round]);
+    if (blockIdx.x == 0) {
+      for (int k = threadIdx.x; k < 2 * d.R; k += blockDim.x) {
+        if (ld_cg(d.round_hit + k)) {
+          int r = k % d.R;
+          d.stats[(long long)r * NSTAT + (k < d.R ? ST_CREATE_ROUNDS : ST_BREAK_ROUNDS)] += 1;
+          d.round_hit[k] = 0;
+        }
+      }
+    }
+    ++round;
+    if (matched == 0) break;
+    if (rt.max_rounds && round >= rt.max_rounds) break;
+    if (round >= MAX_ROUNDS) {
+      if (g == 0) atomicOr(d.err, ERR_ROUNDS);
+      break;
+    }
+  }
+  if (g == 0) d.cnt->rounds_done = round;
+}
+
+// ---------------------------------------------------------------------------
+// k_edit: trials and in-place edit of each bead's own slots
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_edit(Dev d, RuleTab rt) {
+  const long long N = d.N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
+    long long i = base + threadIdx.x;
+    bool valid = i < N;
+    bool dirty = false, fresh = false;
+    if (valid) {
+      unsigned wca = d.bm_ca[i >> 5], wba = d.bm_ba[i >> 5];
+      bool ca = (wca >> (i & 31)) & 1u, ba = (wba >> (i & 31)) & 1u;
+      if (ca || ba) {
+        int r = d.rep[i];
+        uint4 s = d.slots[i];
+        unsigned removed = 0, changed = 0;
+        int conv_partner = -1, form_partner = -1, form_type = 0;
+        long long n_killed = 0, n_broken = 0, n_conv = 0, n_formed = 0;
+        if (ba) {
+          removed = d.killmask[i];
+#pragma unroll
+          for (int q = 0; q < SLOTS; ++q)
+            if ((removed >> q) & 1u) n_killed += s_partner(s_get(s, q)) > i;
+          int j = d.brk_len[i] ? d.mate[N + i] : -1;
+          if (j >= 0) {
+            int4 ent = d.brk[4 * i + d.ptr[N + i]];
+            int k = ent.y;
+            int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
+            if (trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k])) {
+              int q = 0;
+              while (q < SLOTS && s_partner(s_get(s, q)) != j) ++q;
+              bool killed = q < SLOTS && ((removed >> q) & 1u);
+              if (q == SLOTS) {
+                atomicOr(d.err, ERR_INTERNAL);
+              } else if (rt.kind[k] == DYNBOND_BREAKBOND) {
+                removed |= 1u << q;
+                n_broken += !killed && j > i;
+              } else if (!killed) {
+                changed |= 1u << q;
+                s_set(s, q, ((unsigned)j << 4) | (unsigned)rt.type2[k]);
+                conv_partner = j;
+                n_conv += j > i;
+              }
+            }
+          }
+        }
+        if (ca) {
+          int j = d.mate[i];
+          if (j >= 0) {
+            int4 ent = d.cand[d.cand_start[i] + d.ptr[i]];
+            int k = ent.y & 0xFF;
+            int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
+            if (trial(d, rt, a, b, r, TAG_FORM, d.T_form[(long long)r * MAXR + k])) {
+              form_partner = j;
+              form_type = (ent.y >> 8) & 15;
+              n_formed += j > i;
+            }
+          }
+        }
+        if (removed | changed | (unsigned)(form_partner >= 0)) {
+          uint4 ns = make_uint4(0, 0, 0, 0);
+          int4 rp = make_int4(-1, -1, -1, -1);
+          int nk = 0, nr = 0;
+#pragma unroll
+          for (int q = 0; q < SLOTS; ++q) {
+            unsigned v = s_get(s, q);
+            if (!v) continue;
+            if ((removed >> q) & 1u) {
+              if (nr == 0) rp.x = s_partner(v);
+              else if (nr == 1) rp.y = s_partner(v);
+              else if (nr == 2) rp.z = s_partner(v);
+              else rp.w = s_partner(v);
+              ++nr;
+              continue;
+            }
+            if ((changed >> q) & 1u) {
+              if (nr == 0) rp.x = s_partner(v);
+              else if (nr == 1) rp.y = s_partner(v);
+              else if (nr == 2) rp.z = s_partner(v);
+              else rp.w = s_partner(v);
+              ++nr;
+            }
+            s_set(ns, nk++, v);
+          }
+          if (form_partner >= 0) {
+            if (nk >= SLOTS) atomicOr(d.err, ERR_SLOTS);
+            else s_set(ns, nk++, ((unsigned)form_partner << 4) | (unsigned)form_type);
+          }
+          d.slots[i] = ns;
+          dirty = (removed | changed) != 0;
+          fresh = form_partner >= 0 || conv_partner >= 0;
+          if (dirty) d.rem[i] = rp;
+          if (fresh) d.newp[i] = make_int2(form_partner, conv_partner);
+          stat_add(d, r, ST_KILLED, n_killed);
+          stat_add(d, r, ST_BROKEN, n_broken);
+          stat_add(d, r, ST_CONVERTED, n_conv);
+          stat_add(d, r, ST_FORMED, n_formed);
+          long long delta = n_formed - n_broken - n_killed;
+          if (delta) atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)delta);
+        }
+      }
+    }
+    unsigned md = __ballot_sync(FULL, dirty), mn = __ballot_sync(FULL, fresh);
+    if (lane == 0 && valid) {
+      d.bm_dirty[i >> 5] = md;
+      d.bm_new[i >> 5] = mn;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_newbonds: ordered list of new bonds (u < v).  mode 0: bonds formed or
+// retyped in this call; mode 1: every bond (initial typing of the system).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
+  __shared__ long long sh[33];
+  __shared__ long long s_excl, s_tile;
+  const long long N = d.N;
+  const long long per_tile = (long long)blockDim.x * NB_PER_THREAD;
+  const long long ntiles = (N + per_tile - 1) / per_tile;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[1], 1);
+    __syncthreads();
+    long long t = s_tile;
+    if (t >= ntiles) break;
+    long long beg = t * per_tile + (long long)threadIdx.x * NB_PER_THREAD;
+    int partners[NB_PER_THREAD][SLOTS];
+    long long cnt = 0;
+#pragma unroll
+    for (int k = 0; k < NB_PER_THREAD; ++k) {
+      long long u = beg + k;
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) partners[k][q] = -1;
+      if (u >= N) continue;
+      if (mode == 0) {
+        if (!((d.bm_new[u >> 5] >> (u & 31)) & 1u)) continue;
+        int2 np = d.newp[u];
+        if (np.x > u) partners[k][0] = np.x;
+        if (np.y > u) partners[k][1] = np.y;
+      } else {
+        uint4 s = d.slots[u];
+#pragma unroll
+        for (int q = 0; q < SLOTS; ++q) {
+          int v = s_partner(s_get(s, q));
+          if (v > u) partners[k][q] = v;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) cnt += partners[k][q] >= 0;
+    }
+    long long tot;
+    long long ex = block_excl_scan(cnt, sh, &tot);
+    if (threadIdx.x == 0) s_excl = lookback(d.st_nb, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
+    __syncthreads();
+    if (s_excl < 0) return;
+    long long at = s_excl + ex;
+#pragma unroll
+    for (int k = 0; k < NB_PER_THREAD; ++k) {
+      long long u = beg + k;
+      if (u >= N) continue;
+      int nr = 0, r = -1;
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        int v = partners[k][q];
+        if (v < 0) continue;
+        if (r < 0) r = d.rep[u];
+        d.nbl[at++] = make_int4((int)u, v, r, 0);
+        ++nr;
+      }
+      if (nr) atomicAdd(&d.nbl_count[r], nr);
+    }
+    if (t == ntiles - 1 && threadIdx.x == blockDim.x - 1) d.cnt->n_nbl = (int)at;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_tiles: per-replica tile bases (one block)
+//   mode 0: purge tiles of the angle / dihedral lists
+//   mode 1: first index and tiles of each replica's new bonds
+//   mode 2: force tiles of the angle / dihedral lists
+// ---------------------------------------------------------------------------
+__device__ void block_tile_bases(const int* count, int R, int per_tile, int* base, int* first) {
+  __shared__ long long sh[33];
+  __shared__ long long carry, carry2;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    carry2 = 0;
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < R; r0 += blockDim.x) {
+    int r = r0 + threadIdx.x;
+    long long c = r < R ? count[r] : 0;
+    long long tiles = (c + per_tile - 1) / per_tile;
+    long long tot, tot2;
+    long long ex = block_excl_scan(tiles, sh, &tot);
+    long long ex2 = first ? block_excl_scan(c, sh, &tot2) : 0;
+    if (r < R) {
+      base[r] = (int)(carry + ex);
+      if (first) first[r] = (int)(carry2 + ex2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry += tot;
+      if (first) carry2 += tot2;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) base[R] = (int)carry;
+}
+
+__global__ void k_tiles(Dev d, int mode) {
+  if (mode == 0) {
+    block_tile_bases(d.n_ang, d.R, PURGE_TILE, d.tb_ang, nullptr);
+    __syncthreads();
+    block_tile_bases(d.n_dih, d.R, PURGE_TILE, d.tb_dih, nullptr);
+  } else if (mode == 1) {
+    block_tile_bases(d.nbl_count, d.R, REBUILD_TILE, d.tb_nb, d.nbl_first);
+  } else {
+    block_tile_bases(d.n_ang, d.R, FORCE_TILE, d.tb_ang, nullptr);
+    __syncthreads();
+    block_tile_bases(d.n_dih, d.R, FORCE_TILE, d.tb_dih, nullptr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_purge: drop every angle / dihedral containing a bond removed or retyped
+// in this call (Appendix step 6); ordered, in place, segment per replica.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_dirty(const Dev& d, int x) { return (d.bm_dirty[x >> 5] >> (x & 31)) & 1u; }
+
+__device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
+  if (!is_dirty(d, a) || !is_dirty(d, b)) return false;
+  int4 rp = d.rem[a];
+  return rp.x == b || rp.y == b || rp.z == b || rp.w == b;
+}
+
+__global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
+  __shared__ long long s_excl, s_tile;
+  const bool dih = which != 0;
+  int4* recs = dih ? d.dih : d.ang;
+  const int* count = dih ? d.n_dih : d.n_ang;
+  int* kept = dih ? d.kept_dih : d.kept_ang;
+  const int* tb = dih ? d.tb_dih : d.tb_ang;
+  unsigned long long* status = dih ? d.st_pd : d.st_pa;
+  const int per_rep = dih ? 18 : 6;
+  const int R = d.R;
+  const int ntiles = tb[R];
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[2 + which], 1);
+    __syncthreads();
+    int t = (int)s_tile;
+    if (t >= ntiles) break;
+    int r = find_seg(tb, R, t);
+    int lt = t - tb[r];
+    long long base = per_rep * d.off[r];
+    int n = count[r];
+    int beg = lt * PURGE_TILE + threadIdx.x;
+    int4 v[PURGE_PER_THREAD];
+    unsigned keep = 0;
+    int nkeep = 0;
+#pragma unroll
+    for (int k = 0; k < PURGE_PER_THREAD; ++k) {
+      int idx = beg + k * (int)blockDim.x;
+      if (idx >= n) continue;
+      v[k] = recs[base + idx];
+      bool gone;
+      if (!dih) {
+        gone = bond_gone(d, v[k].x, v[k].y) || bond_gone(d, v[k].y, v[k].z);
+      } else {
+        int dd = v[k].w & 0x0FFFFFFF;
+        gone = bond_gone(d, v[k].x, v[k].y) || bond_gone(d, v[k].y, v[k].z) || bond_gone(d, v[k].z, dd);
+      }
+      if (!gone) {
+        keep |= 1u << k;
+        ++nkeep;
+      }
+    }
+    // ordered compaction: records are numbered k-major within the tile
+    // (index = k * blockDim + thread), so scan over that order
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int s_cnt[PURGE_PER_THREAD][8];
+    __shared__ int s_off[PURGE_PER_THREAD][8];
+    unsigned bal[PURGE_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < PURGE_PER_THREAD; ++k) {
+      bal[k] = __ballot_sync(FULL, (keep >> k) & 1u);
+      if (lane == 0) s_cnt[k][wid] = __popc(bal[k]);
+    }
+    __syncthreads();
+    long long tot = 0;
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int k = 0; k < PURGE_PER_THREAD; ++k)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+          s_off[k][w] = acc;
+          acc += s_cnt[k][w];
+        }
+      tot = acc;
+      s_excl = lookback(status, t, tb[r], (unsigned long long)tot, d.spin_limit, d.err);
+      if (s_excl >= 0 && lt == tb[r + 1] - tb[r] - 1) {
+        kept[r] = (int)(s_excl + tot);
+      }
+    }
+    __syncthreads();
+    if (s_excl < 0) return;
+    long long excl = s_excl;
+    // nothing moves when no record before or inside this tile was dropped
+    bool full = excl == (long long)lt * PURGE_TILE && s_off[PURGE_PER_THREAD - 1][(blockDim.x >> 5) - 1] +
+                                                              s_cnt[PURGE_PER_THREAD - 1][(blockDim.x >> 5) - 1] ==
+                                                          min(PURGE_TILE, n - lt * PURGE_TILE);
+    if (!full) {
+#pragma unroll
+      for (int k = 0; k < PURGE_PER_THREAD; ++k) {
+        if (!((keep >> k) & 1u)) continue;
+        int rank = s_off[k][wid] + __popc(bal[k] & ((1u << lane) - 1));
+        recs[base + excl + rank] = v[k];
+      }
+    }
+    (void)nkeep;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_rebuild: typed angle / dihedral records of every non-cyclic path of the
+// new bond graph that contains a new bond (Appendix step 9; typing rules of
+// Sec. 2).  A path holding several new bonds is written by its lowest one.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long bkey(int a, int b) {
+  return a < b ? ((unsigned long long)(unsigned)a << 32) | (unsigned)b
+               : ((unsigned long long)(unsigned)b << 32) | (unsigned)a;
+}
+
+struct Rebuild {
+  const Dev& d;
+  const RuleTab& rt;
+  int all_new;
+  __device__ bool is_new(int p, int q) const {
+    if (all_new) return true;
+    if (!((d.bm_new[p >> 5] >> (p & 31)) & 1u) || !((d.bm_new[q >> 5] >> (q & 31)) & 1u)) return false;
+    int2 np = d.newp[p];
+    return np.x == q || np.y == q;
+  }
+  // true if another bond (p, q) of the path is new and ranks below (u, v)
+  __device__ bool outranked(int p, int q, unsigned long long kuv) const { return bkey(p, q) < kuv && is_new(p, q); }
+
+  template <class Emit>
+  __device__ void run(int u, int v, Emit& emit) const {
+    const unsigned long long kuv = bkey(u, v);
+    uint4 su = d.slots[u], sv = d.slots[v];
+    int tu = d.type[u], tv = d.type[v];
+    int st_uv = s_type_to(su, v), st_vu = s_type_to(sv, u);
+    // angles centred at u: (x, u, v) and at v: (u, v, y)
+    for (int q = 0; q < SLOTS; ++q) {
+      unsigned w = s_get(su, q);
+      int x = s_partner(w);
+      if (x < 0 || x == v || outranked(x, u, kuv)) continue;
+      int t = angle_type(rt, d.type[x], tu, tv, s_type(w), st_uv);
+      if (t) emit.angle(min(x, v), u, max(x, v), t);
+    }
+    for (int q = 0; q < SLOTS; ++q) {
+      unsigned w = s_get(sv, q);
+      int y = s_partner(w);
+      if (y < 0 || y == u || outranked(v, y, kuv)) continue;
+      int t = angle_type(rt, tu, tv, d.type[y], st_vu, s_type(w));
+      if (t) emit.angle(min(u, y), v, max(u, y), t);
+    }
+    // dihedrals with (u, v) in the middle: (x, u, v, y)
+    for (int q = 0; q < SLOTS; ++q) {
+      unsigned wx = s_get(su, q);
+      int x = s_partner(wx);
+      if (x < 0 || x == v || outranked(x, u, kuv)) continue;
+      int tx = d.type[x];
+      for (int q2 = 0; q2 < SLOTS; ++q2) {
+        unsigned wy = s_get(sv, q2);
+        int y = s_partner(wy);
+        if (y < 0 || y == u || y == x || outranked(v, y, kuv)) continue;
+        // r = st(u->x), s = st(v->u), s' = st(u->v), t = st(v->y)
+        int t = dihedral_type(rt, tx, tu, tv, d.type[y], s_type(wx), st_vu, st_uv, s_type(wy));
+        if (t) {
+          if (x < y) emit.dihedral(x, u, v, y, t);
+          else emit.dihedral(y, v, u, x, t);
+        }
+      }
+    }
+    // dihedrals starting at u: (u, v, y, z) and starting at v: (v, u, x, w)
+    for (int side = 0; side < 2; ++side) {
+      int a = side ? v : u, b = side ? u : v;  // path a - b - y - z
+      const uint4& sb = side ? su : sv;
+      int ta = side ? tv : tu, tb = side ? tu : tv;
+      int st_ba = side ? st_uv : st_vu;
+      for (int q = 0; q < SLOTS; ++q) {
+        unsigned wy = s_get(sb, q);
+        int y = s_partner(wy);
+        if (y < 0 || y == a || outranked(b, y, kuv)) continue;
+        uint4 sy = d.slots[y];
+        int ty = d.type[y];
+        int st_yb = s_type_to(sy, b);
+        for (int q2 = 0; q2 < SLOTS; ++q2) {
+          unsigned wz = s_get(sy, q2);
+          int z = s_partner(wz);
+          if (z < 0 || z == b || z == a || outranked(y, z, kuv)) continue;
+          // path (a, b, y, z): r = st(b->a), s = st(y->b), s' = st(b->y), t = st(y->z)
+          int t = dihedral_type(rt, ta, tb, ty, d.type[z], st_ba, st_yb, s_type(wy), s_type(wz));
+          if (t) {
+            if (a < z) emit.dihedral(a, b, y, z, t);
+            else emit.dihedral(z, y, b, a, t);
+          }
+        }
+      }
+    }
+  }
+};
+
+struct CountEmit {
+  int na = 0, nd = 0;
+  __device__ void angle(int, int, int, int) { ++na; }
+  __device__ void dihedral(int, int, int, int, int) { ++nd; }
+};
+struct WriteEmit {
+  int4* ang;
+  int4* dih;
+  const int4* ang_end;  // end of the replica's region (worst-case capacity)
+  const int4* dih_end;
+  unsigned* err;
+  __device__ void angle(int a, int b, int c, int t) {
+    if (ang < ang_end) *ang++ = make_int4(a, b, c, t);
+    else atomicOr(err, ERR_INTERNAL);
+  }
+  __device__ void dihedral(int a, int b, int c, int dd, int t) {
+    if (dih < dih_end) *dih++ = make_int4(a, b, c, dd | (t << 28));
+    else atomicOr(err, ERR_INTERNAL);
+  }
+};
+
+__global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, RuleTab rt, int all_new) {
+  __shared__ long long sh[33];
+  __shared__ long long s_excl, s_tile;
+  const int R = d.R;
+  const int ntiles = d.tb_nb[R];
+  Rebuild rb{d, rt, all_new};
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[4], 1);
+    __syncthreads();
+    int t = (int)s_tile;
+    if (t >= ntiles) break;
+    int r = find_seg(d.tb_nb, R, t);
+    int lt = t - d.tb_nb[r];
+    int idx = lt * REBUILD_TILE + threadIdx.x;
+    bool valid = idx < d.nbl_count[r];
+    int4 e = valid ? d.nbl[d.nbl_first[r] + idx] : make_int4(0, 0, 0, 0);
+    CountEmit ce;
+    if (valid) rb.run(e.x, e.y, ce);
+    long long packed = (long long)ce.na | ((long long)ce.nd << 32);
+    long long tot;
+    long long ex = block_excl_scan(packed, sh, &tot);
+    if (threadIdx.x == 0) {
+      s_excl = lookback(d.st_rb, t, d.tb_nb[r], (unsigned long long)tot, d.spin_limit, d.err);
+      if (s_excl >= 0 && lt == d.tb_nb[r + 1] - d.tb_nb[r] - 1) {
+        long long all = s_excl + tot;
+        d.added_ang[r] = (int)(all & 0xFFFFFFFFll);
+        d.added_dih[r] = (int)(all >> 32);
+      }
+    }
+    __syncthreads();
+    if (s_excl < 0) return;
+    if (valid && (ce.na || ce.nd)) {
+      long long pre = s_excl + ex;
+      WriteEmit we{d.ang + 6 * d.off[r] + d.kept_ang[r] + (pre & 0xFFFFFFFFll),
+                   d.dih + 18 * d.off[r] + d.kept_dih[r] + (pre >> 32), d.ang + 6 * d.off[r + 1],
+                   d.dih + 18 * d.off[r + 1], d.err};
+      rb.run(e.x, e.y, we);
+    }
+    __syncthreads();
+  }
+}
+
+// per-replica list counts and statistics after the call (one thread per replica)
+__global__ void k_finalize(Dev d) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < d.R; r += gridDim.x * blockDim.x) {
+    long long* st = d.stats + (long long)r * NSTAT;
+    int na = d.kept_ang[r] + d.added_ang[r], nd = d.kept_dih[r] + d.added_dih[r];
+    st[ST_ANG_REMOVED] = d.n_ang[r] - d.kept_ang[r];
+    st[ST_DIH_REMOVED] = d.n_dih[r] - d.kept_dih[r];
+    st[ST_ANG_ADDED] = d.added_ang[r];
+    st[ST_DIH_ADDED] = d.added_dih[r];
+    d.n_ang[r] = na;
+    d.n_dih[r] = nd;
+    st[ST_NBONDS] = d.n_bonds[r];
+    st[ST_NANGLES] = na;
+    st[ST_NDIHEDRALS] = nd;
+  }
+}
+
+__global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
+                           int set_pos, int set_force) {
+  if (set_pos) {
+    a->pos = pos;
+    a->step = step;
+  }
+  if (set_force) {
+    a->pos = pos;
+    a->force = force;
+    a->ev = ev;
+  }
+}
+
+}  // namespace dynbond

@@ -216,9 +216,10 @@ def _random_walk_strands(rng, n_strands, n_nt, box):
 def _replica_strands(rng, n_strands, n_nt, box, first_bead, n_duplex=0):
     """Positions, types and bonds of n_strands strands; the first 2*n_duplex
     strands are laid out as anti-parallel ladders of complementary sequences:
-    backbone spacing 1.0 along the ladder, each base 0.5 from its backbone
-    toward the partner strand and 0.8 from its partner base, with the
-    hybridization bonds already present."""
+    backbone spacing 1.0 along the ladder axis u, the two backbones 1.8 apart
+    along v, each base 0.5 toward the partner strand and 0.3 off the ladder
+    plane along w (so backbone-base-base-backbone is a U, not a straight line),
+    partner bases 0.8 apart, with the hybridization bonds already present."""
     nb = 2 * n_nt
     N = n_strands * nb
     seq = rng.integers(1, 5, size=(n_strands, n_nt)).astype(np.int32)
@@ -232,12 +233,13 @@ def _replica_strands(rng, n_strands, n_nt, box, first_bead, n_duplex=0):
         w = _unit_vectors(rng, 1)[0]
         v = w - np.dot(w, u) * u
         v /= np.linalg.norm(v)
+        w = np.cross(u, v)
         k = np.arange(n_nt)[:, None]
         pos[sa, 0::2] = o + k * u
-        pos[sa, 1::2] = o + k * u + 0.5 * v
+        pos[sa, 1::2] = o + k * u + 0.5 * v + 0.3 * w
         kb = (n_nt - 1 - np.arange(n_nt))[:, None]  # strand B's nucleotide m sits at rung n_nt-1-m
         pos[sb, 0::2] = o + kb * u + 1.8 * v
-        pos[sb, 1::2] = o + kb * u + 1.3 * v
+        pos[sb, 1::2] = o + kb * u + 1.3 * v + 0.3 * w
         ia = first_bead + sa * nb + 2 * np.arange(n_nt) + 1
         ib = first_bead + sb * nb + 2 * (n_nt - 1 - np.arange(n_nt)) + 1
         hyb.append(np.stack([ia, ib, np.full(n_nt, HYB), np.full(n_nt, HYB)], axis=1))

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Topology (bonds with the type each end stores, angles, dihedrals) and every
+per-replica statistic must match bit for bit after every call; bonded forces
+(FP32 per term) must match the FP64 oracle within
+|f_gpu - f_ref| <= FORCE_TOL * (|f_ref| + f_rms) per component, and the FP64-
+reduced energy / virial within EV_TOL of the largest magnitude."""
+
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1108_4214_gb300 import workloads as W
+
+from helpers import golden, golden_rules, ladder_1bead_positions, make_system
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FORCE_TOL = 2e-5
+EV_TOL = 2e-6
+
+
+def dynbond():
+    from paper_1108_4214_gb300 import dynbond as D
+    return D
+
+
+def assert_same(a, b, what):
+    if a.shape != b.shape or not np.array_equal(a, b):
+        sa = {tuple(x) for x in a.tolist()}
+        sb = {tuple(x) for x in b.tolist()}
+        raise AssertionError(f"{what}: gpu {a.shape} vs oracle {b.shape}; only gpu {sorted(sa - sb)[:5]} "
+                             f"only oracle {sorted(sb - sa)[:5]}")
+
+
+def compare_topology(ctx, o, where):
+    for name, g, r in zip(("bonds", "angles", "dihedrals"), ctx.topology(), o.topology()):
+        assert_same(g, r, f"{where}: {name}")
+
+
+def compare_forces(ctx, o, snap, where):
+    pos = torch.from_numpy(snap).cuda()
+    f, ev = ctx.forces(pos)
+    f = f.cpu().numpy()
+    ev = ev.cpu().numpy()
+    fr, evr = o.forces(snap)
+    assert np.all(f[:, 3] == 0)
+    err = np.abs(f[:, :3].astype(np.float64) - fr)
+    rms = np.sqrt(np.mean(fr ** 2))
+    worst = (err / (np.abs(fr) + rms)).max()
+    assert worst <= FORCE_TOL, f"{where}: force error {worst:.3g} (x (|f| + rms))"
+    scale = np.abs(evr).max(axis=1, keepdims=True)
+    evw = (np.abs(ev - evr) / scale).max()
+    assert evw <= EV_TOL, f"{where}: energy/virial error {evw:.3g}"
+    return worst, evw
+
+
+def run_parity(system, n_calls, snaps=None, params=None, flags=0, forces=True, start=0):
+    o = O.Oracle(system, params=params)
+    ctx = dynbond().Context(system, params=params, flags=flags)
+    compare_topology(ctx, o, "initial")
+    worst = []
+    for k in range(n_calls):
+        snap = snaps[k] if snaps is not None else system.snapshot(k)
+        st_g = ctx.step(torch.from_numpy(snap).cuda(), start + k, stats=True)
+        st_o = o.step(snap, start + k)
+        if not np.array_equal(st_g, st_o):
+            diff = {O.STAT_NAMES[j]: (st_g[:, j].tolist(), st_o[:, j].tolist())
+                    for j in range(len(O.STAT_NAMES)) if not np.array_equal(st_g[:, j], st_o[:, j])}
+            raise AssertionError(f"call {k}: statistics differ {diff}")
+        compare_topology(ctx, o, f"call {k}")
+        if forces:
+            worst.append(compare_forces(ctx, o, snap, f"call {k}"))
+    ctx.close()
+    return o, worst
+
+
+# ---------------------------------------------------------------------------
+
+def test_philox_oracle_matches_curand():
+    """Pins the oracle's Philox4x32-10 bit for bit against cuRAND's
+    Philox4_32_10: curand_init(seed, subsequence, 4m) then curand4() k times
+    draws Philox on the counter (m + k as 64 bits, subsequence as 64 bits)
+    with key = seed."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "native", "libcurand_philox.so")
+    if not os.path.exists(path):
+        import __graft_entry__
+        __graft_entry__._build_test_helper()
+    L = ctypes.CDLL(path)
+    L.curand_philox_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
+    rng = np.random.default_rng(1)
+    for _ in range(12):
+        seed = int(rng.integers(0, 2**63)) * 2 + 1
+        sub = int(rng.integers(0, 2**62))
+        m = int(rng.integers(0, 2**40))
+        n = 6
+        out = np.zeros((n, 4), np.uint32)
+        assert L.curand_philox_draw(seed, sub, 4 * m, n, out.ctypes.data) == 0
+        for k in range(n):
+            c = m + k
+            want = O.philox([c & 0xFFFFFFFF, c >> 32, sub & 0xFFFFFFFF, sub >> 32],
+                            [seed & 0xFFFFFFFF, seed >> 32])
+            assert np.array_equal(out[k], want), (seed, sub, m, k)
+
+
+def test_initial_typing_of_the_papers_dna_ladder():
+    g = golden("dna1bead_ladder_4mer.json")
+    s = make_system(g["types"], g["bonds"], ladder_1bead_positions(), 20.0, golden_rules(g["rules_fig2_9_to_14"]))
+    ctx = dynbond().Context(s)
+    _, a, d = ctx.topology()
+    assert a.tolist() == sorted(g["expected_angles"])
+    assert d.tolist() == sorted(g["expected_dihedrals"])
+
+
+def test_plain_2048_beads_ten_calls():
+    s = W.config1()
+    _, worst = run_parity(s, 10)
+    print("max force / ev error", max(w[0] for w in worst), max(w[1] for w in worst))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_systems_all_rule_kinds(seed):
+    rules = W.random_rules(seed)
+    s = W.random_small_system(seed, n_beads=60, box=3.0 + seed % 3, n_bonds=50, rules=rules,
+                              n_replicas=1 + seed % 3,
+                              params=dict(paircheck13=seed % 2, paircheck14=(seed // 2) % 2, max_rounds=seed % 3,
+                                          prob_mode=(seed // 3) % 2))
+    run_parity(s, 4)
+
+
+def test_rounds_matching_and_single_nomination():
+    pos2 = [[2.0, 2, 2], [2.0, 3.0, 2], [2.5, 2, 2], [2.95, 2.6, 2]]
+    rules = [dict(kind="createbond", btype=1, beads=(W.bit(1), W.bit(2)), dist=1.1, prob=1.0),
+             dict(kind="maxbond", bonds=W.bit(1), beads=W.bit(1, 2, 3, 4), max=1)]
+    for mr, want in ((0, 2), (1, 1)):
+        s = make_system([1, 2, 2, 1], [], pos2, 10.0, rules, params=dict(max_rounds=mr))
+        o, _ = run_parity(s, 1)
+        assert o.counts()[0] == want
+
+
+def test_duplex_melts_and_reforms():
+    rules = W.rules_dna2(p_form=1.0, p_break=1.0)
+    rng = np.random.default_rng(3)
+    pos, types, bonds = W._replica_strands(rng, 2, 12, 30.0, 0, n_duplex=1)
+    s = W.System(name="duplex", bead_offset=np.array([0, 48]), box_q=np.array([30 * W.QSCALE]), types=types,
+                 bonds=bonds, rules=rules, pos0=pos, seed=5, sigma_perturb=0.0, params=W.default_params(5))
+    snap = s.snapshot(0)
+    run_parity(s, 2, snaps=[snap, snap])
+
+
+def test_plain_1m_beads_parity():
+    s = W.config2()
+    snaps = s.snapshots(0, 3)
+    _, worst = run_parity(s, 3, snaps=snaps)
+    print("1M: max force / ev error", worst)
+
+
+def test_melting_1m_beads_parity():
+    s = W.scaled_config4(8192)
+    snaps = s.snapshots(0, 3)
+    run_parity(s, 3, snaps=snaps)
+
+
+def test_batched_ladder_parity_and_replica_independence():
+    full = W.config3(n_replicas=48)
+    snaps = full.snapshots(0, 3)
+    run_parity(full, 3, snaps=snaps)
+    # the same replicas run alone (same streams and scales) reach the same bonds
+    idx = [3, 17, 40]
+    sub = W.sub_replicas(full, idx)
+    ctx_b = dynbond().Context(full)
+    ctx_s = dynbond().Context(sub)
+    for k in range(3):
+        ctx_b.step(torch.from_numpy(snaps[k]).cuda(), k)
+        ctx_s.step(torch.from_numpy(snaps[k][sub._sel]).cuda(), k)
+    bb, _, _ = ctx_b.topology()
+    bs, _, _ = ctx_s.topology()
+    inv = np.zeros(full.n_beads, np.int64) - 1
+    inv[sub._sel] = np.arange(len(sub._sel))
+    keep = inv[bb[:, 0]] >= 0
+    mapped = bb[keep].copy()
+    mapped[:, 0] = inv[mapped[:, 0]]
+    mapped[:, 1] = inv[mapped[:, 1]]
+    assert np.array_equal(mapped[np.lexsort(mapped.T[::-1])], bs)
+
+
+def test_graph_and_direct_launches_agree():
+    s = W.config1()
+    D = dynbond()
+    a = D.Context(s)
+    b = D.Context(s, flags=D.FLAG_NO_GRAPH)
+    for k in range(3):
+        p = torch.from_numpy(s.snapshot(k)).cuda()
+        assert np.array_equal(a.step(p, k, stats=True), b.step(p, k, stats=True))
+    for x, y in zip(a.topology(), b.topology()):
+        assert np.array_equal(x, y)
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    s = W.config1()
+    D = dynbond()
+    a, b = D.Context(s), D.Context(s)
+    for k in range(2):
+        snap = s.snapshot(k)
+        f_h, ev_h, st_h = a.run_host(snap, k, stats=True)
+        p = torch.from_numpy(snap).cuda()
+        st_d = b.step(p, k, stats=True)
+        f_d, ev_d = b.forces(p)
+        assert np.array_equal(st_h, st_d)
+        assert np.allclose(f_h, f_d.cpu().numpy(), rtol=1e-5, atol=1e-4)
+        assert np.allclose(ev_h, ev_d.cpu().numpy(), rtol=1e-9)
+
+
+def test_position_outside_box_is_reported_and_sticks():
+    s = W.config1()
+    D = dynbond()
+    ctx = D.Context(s)
+    snap = s.snapshot(0)
+    snap[5, 1] = int(s.box_q[0])  # one past the edge
+    with pytest.raises(D.DynbondError) as e:
+        ctx.step(torch.from_numpy(snap).cuda(), 0, stats=True)
+    assert e.value.status == 1
+    with pytest.raises(D.DynbondError):
+        ctx.step(torch.from_numpy(s.snapshot(0)).cuda(), 0)
+
+
+def test_resume_from_exported_topology_reproduces_the_run():
+    s = W.config1()
+    D = dynbond()
+    a = D.Context(s)
+    snaps = s.snapshots(0, 6)
+    for k in range(3):
+        a.step(torch.from_numpy(snaps[k]).cuda(), k)
+    bonds, _, _ = a.topology()
+    import dataclasses
+    s2 = dataclasses.replace(s, bonds=bonds)
+    b = D.Context(s2)
+    for x, y in zip(a.topology(), b.topology()):
+        assert np.array_equal(x, y)
+    for k in range(3, 6):
+        p = torch.from_numpy(snaps[k]).cuda()
+        assert np.array_equal(a.step(p, k, stats=True)[:, :12], b.step(p, k, stats=True)[:, :12])
+    for x, y in zip(a.topology(), b.topology()):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.slow
+def test_melting_16m_beads_full_size_two_calls():
+    s = W.config4()
+    snaps = s.snapshots(0, 2)
+    run_parity(s, 2, snaps=snaps, forces=True)
