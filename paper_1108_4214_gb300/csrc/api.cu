@@ -21,6 +21,7 @@ struct dynbond_ctx {
   cudaStream_t stream = nullptr;
   dynbond_params prm{};
   RuleTab rt{};
+  RuleTab* d_rt = nullptr;  // device copy read by the kernels
   FF ff{};
   long long N = 0;
   int R = 0;
@@ -224,7 +225,7 @@ cudaError_t launch_match(dynbond_ctx* c) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_match, c->d, c->rt);
+  return cudaLaunchKernelEx(&cfg, k_match, c->d, (const RuleTab*)c->d_rt);
 }
 
 cudaError_t enqueue_step(dynbond_ctx* c) {
@@ -239,18 +240,18 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   cudaMemsetAsync(c->status_all, 0, c->status_bytes, s);
   k_tiles<<<1, 1024, 0, s>>>(d, 0);
   mark(c, c->ev_step, k++);
-  k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->rt);
+  k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
   mark(c, c->ev_step, k++);
   k_scan_cells<<<c->grid_scan, 256, 0, s>>>(d);
   k_scatter<<<c->grid_bead, 256, 0, s>>>(d);
   mark(c, c->ev_step, k++);
-  k_candidates<<<c->grid_cand, 256, 0, s>>>(d, c->rt);
-  k_cand_overflow<<<c->nsm, 128, 0, s>>>(d, c->rt);
+  k_candidates<<<c->grid_cand, 256, 0, s>>>(d, c->d_rt);
+  k_cand_overflow<<<c->nsm, 128, 0, s>>>(d, c->d_rt);
   mark(c, c->ev_step, k++);
   cudaError_t e = launch_match(c);
   if (e != cudaSuccess) return e;
   mark(c, c->ev_step, k++);
-  k_edit<<<c->grid_bead, 256, 0, s>>>(d, c->rt);
+  k_edit<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
   mark(c, c->ev_step, k++);
   k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 0);
   k_tiles<<<1, 1024, 0, s>>>(d, 1);
@@ -258,7 +259,7 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   k_purge<<<c->grid_seg, 256, 0, s>>>(d, 0);
   k_purge<<<c->grid_seg, 256, 0, s>>>(d, 1);
   mark(c, c->ev_step, k++);
-  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->rt, 0);
+  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->d_rt, 0);
   k_finalize<<<(c->R + 255) / 256, 256, 0, s>>>(d);
   mark(c, c->ev_step, k++);
   return cudaGetLastError();
@@ -460,14 +461,10 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   for (int r = 0; r < R; ++r) {
     long long L = sys->box_q[r];
     long long ncap = w > 0 ? L / w : 1;
-    double scale = params->cell_scale;
-    if (scale <= 0) {
-      long long ne = 0;
-      for (long long i = sys->bead_offset[r]; i < sys->bead_offset[r + 1]; ++i) ne += c->rt.role_rules[type[i]] != 0;
-      double vol = std::pow((double)L, 3.0);
-      double occ = w > 0 && ne > 0 ? (double)ne * std::pow((double)w, 3.0) / vol : 1.0;
-      scale = std::max(1.0, std::cbrt(1.0 / std::max(occ, 1e-12)));
-    }
+    // default: cells as narrow as the reach allows (the search scans
+    // contiguous z-runs of three cells, so narrow cells cost little); a
+    // larger cell_scale trades more visited entries for fewer lookups
+    double scale = params->cell_scale > 0 ? params->cell_scale : 1.0;
     long long n = w > 0 ? (long long)((double)L / (scale * (double)w)) : 1;
     n = std::max<long long>(1, std::min<long long>({n, ncap, 1024}));
     nc[r] = (int)n;
@@ -504,6 +501,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(p_tf, (size_t)R * MAXR);
   ALLOC(p_tb, (size_t)R * MAXR);
   ALLOC(d.args, 1);
+  ALLOC(c->d_rt, 1);
   ALLOC(d.slots, N);
   ALLOC(d.ang, 6 * N);
   ALLOC(d.dih, 18 * N);
@@ -530,6 +528,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.bm_ba, c->W);
   ALLOC(d.bm_dirty, c->W);
   ALLOC(d.bm_new, c->W);
+  ALLOC(d.live[0], 2 * N);
+  ALLOC(d.live[1], 2 * N);
   ALLOC(d.mate, 2 * N);
   ALLOC(d.nom, 2 * N);
   ALLOC(d.ptr, 2 * N);
@@ -610,6 +610,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   std::vector<long long> boxv(sys->box_q, sys->box_q + R), offv(sys->bead_offset, sys->bead_offset + R + 1);
   std::vector<int> zeros(R, 0);
   cudaStream_t s = c->stream;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_rt, &c->rt, sizeof(RuleTab), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_off, offv.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_box, boxv.data(), 8 * R, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_cb, cell_base.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
@@ -633,8 +634,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->grid_cand = bounded_grid(N, 256, c->nsm * 8);
   c->grid_nb = bounded_grid(N, 256 * 4, c->nsm * 4);
   c->grid_seg = c->nsm * 4;
-  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 256, 2),
-                                       bounded_grid(N, 256, c->nsm * 2)));
+  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 256, 4),
+                                       bounded_grid(N, 256, c->nsm * 4)));
 
   // ---- initial interactions: the typed set of every path of the initial graph
   CUDA_TRY(c, cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s));
@@ -642,7 +643,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemsetAsync(c->status_all, 0, c->status_bytes, s));
   k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 1);
   k_tiles<<<1, 1024, 0, s>>>(d, 1);
-  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->rt, 1);
+  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->d_rt, 1);
   k_finalize<<<(R + 255) / 256, 256, 0, s>>>(d);
   CUDA_TRY(c, cudaGetLastError());
   st = device_status(c);

@@ -79,6 +79,7 @@ struct Counters {
   unsigned bar[2];
   int rounds_done;
   int round_matched[MAX_ROUNDS];
+  int round_live[MAX_ROUNDS];  // entries carried into the next round
 };
 
 // Device view of a context.  Arrays marked [N] are indexed by global bead id.
@@ -129,6 +130,7 @@ struct Dev {
   unsigned* bm_ba;             // [W] breakage/kill-active beads
   unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
   unsigned* bm_new;            // [W] beads with a formed or retyped bond
+  int* live[2];                // [2*N] each: active (system << 31 | bead) entries between rounds
   int* mate;                   // [2*N] creation / breakage partner, -1 = none
   int* nom;                    // [2*N]
   int* ptr;                    // [2*N]
@@ -385,41 +387,76 @@ __device__ __forceinline__ T block_excl_scan(T v, T* sh, T* total) {
 }
 
 // ---------------------------------------------------------------------------
-// single-pass look-back (one thread per block calls it).  Tiles are taken in
-// ticket order, so every predecessor has started; each tile publishes its
-// aggregate after reading its input and its inclusive prefix after the
-// look-back.  status[t] = flag << 62 | value; flag 1 = aggregate, 2 = prefix.
-// Returns the exclusive prefix within the segment starting at seg_first, or
-// -1 after spin_limit unsuccessful polls (error bit set).
+// single-pass look-back, called by one full warp of the block.  Tiles are
+// taken in ticket order, so every predecessor has started; each tile
+// publishes its aggregate after reading its input and its inclusive prefix
+// after the look-back.  status[t] = flag << 62 | value; flag 1 = aggregate,
+// 2 = inclusive prefix.  The warp inspects 32 predecessors per poll.
+// Returns (in every lane) the exclusive prefix within the segment starting at
+// seg_first, or -1 after spin_limit unsuccessful polls (error bit set).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ long long lookback(unsigned long long* status, long long t, long long seg_first,
                                               unsigned long long agg, int spin_limit, unsigned* err) {
   const unsigned long long FA = 1ull << 62, FP = 2ull << 62, VM = (1ull << 62) - 1;
+  const int lane = threadIdx.x & 31;
   if (t == seg_first) {
-    st_release(status + t, FP | agg);
+    if (lane == 0) st_release(status + t, FP | agg);
     return 0;
   }
-  st_release(status + t, FA | agg);
+  if (lane == 0) st_release(status + t, FA | agg);
   unsigned long long excl = 0;
   long long p = t - 1;
   int spins = 0;
   while (true) {
-    unsigned long long s = ld_acquire(status + p);
-    unsigned long long f = s & (3ull << 62);
-    if (f == 0) {
+    long long idx = p - lane;
+    unsigned long long s = idx >= seg_first ? ld_acquire(status + idx) : FP;
+    unsigned long long f = s >> 62;
+    unsigned inc = __ballot_sync(FULL, f == 2), zero = __ballot_sync(FULL, f == 0);
+    unsigned need = inc ? ((inc & (0u - inc)) << 1) - 1 : FULL;  // lanes up to the first prefix
+    if (zero & need) {
       if (++spins > spin_limit) {
-        atomicOr(err, ERR_TIMEOUT);
+        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         return -1;
       }
       __nanosleep(32);
       continue;
     }
-    excl += s & VM;
-    if (f == FP || p == seg_first) break;
-    --p;
+    unsigned long long v = ((need >> lane) & 1u) ? (s & VM) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    excl += __shfl_sync(FULL, v, 0);
+    if (inc) break;
+    p -= 32;
   }
-  st_release(status + t, FP | (excl + agg));
+  if (lane == 0) st_release(status + t, FP | (excl + agg));
   return (long long)excl;
+}
+
+// Add v (per lane) to statistic k of replica r with one atomic per replica
+// present in the warp.  Every lane of the warp must call it.
+__device__ __forceinline__ void stat_add_warp(long long* stats, int r, int k, unsigned v) {
+  if (!__ballot_sync(FULL, v != 0)) return;
+  unsigned grp = __match_any_sync(FULL, r);
+  int lane = threadIdx.x & 31;
+  if (grp == FULL) {
+    unsigned sum = __reduce_add_sync(FULL, v);
+    if (lane == 0) atomicAdd((unsigned long long*)&stats[(long long)r * NSTAT + k], (unsigned long long)sum);
+  } else if (v) {
+    atomicAdd((unsigned long long*)&stats[(long long)r * NSTAT + k], (unsigned long long)v);
+  }
+}
+
+// Same for an int counter array indexed by replica.
+__device__ __forceinline__ void count_add_warp(int* counts, int r, unsigned v) {
+  if (!__ballot_sync(FULL, v != 0)) return;
+  unsigned grp = __match_any_sync(FULL, r);
+  int lane = threadIdx.x & 31;
+  if (grp == FULL) {
+    unsigned sum = __reduce_add_sync(FULL, v);
+    if (lane == 0) atomicAdd(&counts[r], (int)sum);
+  } else if (v) {
+    atomicAdd(&counts[r], (int)v);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -447,7 +484,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int spin_limit, unsigne
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (spins > 256) __nanosleep(32);
       }
     }
     __threadfence();

@@ -57,20 +57,38 @@ __device__ __forceinline__ float3 axpy(float a, float3 x, float3 y) {
 }
 __device__ __forceinline__ float3 scale(float a, float3 x) { return make_float3(a * x.x, a * x.y, a * x.z); }
 
+// Energy / virial accumulators: each FP32 term is added with an error-free
+// transformation (TwoSum), so a thread's partial sum is a float pair with
+// about twice the FP32 precision; warps combine the pairs the same way, and
+// only the per-warp totals enter FP64 (block sum, then one FP64 atomic per
+// component per block).  FP64 is thus used only where the reduction needs it.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bp = __fsub_rn(s, a);
+  float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
 struct EV {
-  double e[7];
+  float hi[7], lo[7];
   __device__ EV() {
 #pragma unroll
-    for (int k = 0; k < 7; ++k) e[k] = 0.0;
+    for (int k = 0; k < 7; ++k) hi[k] = lo[k] = 0.f;
+  }
+  __device__ void add(int k, float x) {
+    float s, e;
+    two_sum(hi[k], x, s, e);
+    hi[k] = s;
+    lo[k] = __fadd_rn(lo[k], e);
   }
   // W_ab += w r_a F_b (xx, yy, zz, xy, xz, yz)
   __device__ void vir(float3 r, float3 f, float w) {
-    e[1] += (double)(w * r.x * f.x);
-    e[2] += (double)(w * r.y * f.y);
-    e[3] += (double)(w * r.z * f.z);
-    e[4] += (double)(w * r.x * f.y);
-    e[5] += (double)(w * r.x * f.z);
-    e[6] += (double)(w * r.y * f.z);
+    add(1, __fmul_rn(__fmul_rn(w, r.x), f.x));
+    add(2, __fmul_rn(__fmul_rn(w, r.y), f.y));
+    add(3, __fmul_rn(__fmul_rn(w, r.z), f.z));
+    add(4, __fmul_rn(__fmul_rn(w, r.x), f.y));
+    add(5, __fmul_rn(__fmul_rn(w, r.x), f.z));
+    add(6, __fmul_rn(__fmul_rn(w, r.y), f.z));
   }
 };
 
@@ -80,11 +98,17 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    double v = acc.e[k];
+    float h = acc.hi[k], l = acc.lo[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-    if (lane == 0) sh[k][wid] = v;
-    acc.e[k] = 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      float h2 = __shfl_down_sync(FULL, h, o), l2 = __shfl_down_sync(FULL, l, o);
+      float s, e;
+      two_sum(h, h2, s, e);
+      h = s;
+      l = __fadd_rn(__fadd_rn(l, l2), e);
+    }
+    if (lane == 0) sh[k][wid] = (double)h + (double)l;
+    acc.hi[k] = acc.lo[k] = 0.f;
   }
   __syncthreads();
   if (threadIdx.x < 7) {
@@ -120,7 +144,7 @@ __global__ void __launch_bounds__(256) k_bond_forces(Dev d, FF ff) {
         float fscal = -2.0f * ff.bond_k[t] * dr / rr;
         float3 fq = scale(fscal, rij);
         f = make_float3(f.x + fq.x, f.y + fq.y, f.z + fq.z);
-        acc.e[0] += (double)(0.5f * ff.bond_k[t] * dr * dr);
+        acc.add(0, __fmul_rn(__fmul_rn(0.5f * ff.bond_k[t], dr), dr));
         acc.vir(rij, fq, 0.5f);
       }
       force[i] = make_float4(f.x, f.y, f.z, 0.f);
@@ -163,7 +187,7 @@ __global__ void __launch_bounds__(256) k_angle_forces(Dev d, FF ff) {
       add_force(force, a.x, Fa);
       add_force(force, a.y, Fb);
       add_force(force, a.z, Fc);
-      acc.e[0] += (double)(K * (1.0f + cs));
+      acc.add(0, __fmul_rn(K, 1.0f + cs));
       acc.vir(ra, Fa, 1.f);
       acc.vir(rc, Fc, 1.f);
     }
@@ -225,7 +249,7 @@ __global__ void __launch_bounds__(256) k_dihedral_forces(Dev d, FF ff) {
       add_force(force, ib, Fb);
       add_force(force, ic, Fc);
       add_force(force, id, Fd);
-      acc.e[0] += (double)(K * (1.0f + dd * cs));
+      acc.add(0, __fmul_rn(K, 1.0f + dd * cs));
       // virial relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
       acc.vir(F, Fa, 1.f);
       acc.vir(make_float3(-G.x, -G.y, -G.z), Fc, 1.f);

@@ -16,17 +16,17 @@ struct FF {
   float bond_k[16], bond_r0[16], angle_k[16], dih_k[16], dih_d[16];
 };
 
-__global__ void k_bead(Dev d, RuleTab rt);
+__global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_scan_cells(Dev d);
 __global__ void k_scatter(Dev d);
-__global__ void k_candidates(Dev d, RuleTab rt);
-__global__ void k_cand_overflow(Dev d, RuleTab rt);
-__global__ void k_match(Dev d, RuleTab rt);
-__global__ void k_edit(Dev d, RuleTab rt);
+__global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_match(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_edit(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_newbonds(Dev d, int mode);
 __global__ void k_tiles(Dev d, int mode);
 __global__ void k_purge(Dev d, int which);
-__global__ void k_rebuild(Dev d, RuleTab rt, int all_new);
+__global__ void k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new);
 __global__ void k_finalize(Dev d);
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
                            int set_pos, int set_force);

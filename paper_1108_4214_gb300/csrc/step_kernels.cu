@@ -44,7 +44,8 @@ __device__ __forceinline__ int warp_alloc(int* counter, int want) {
 // ---------------------------------------------------------------------------
 // k_bead
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bead(Dev d, RuleTab rt) {
+__global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
+  const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, RuleTab rt) {
             if (nbrk) {
               d.mate[N + i] = -1;
               d.ptr[N + i] = 0;
+              d.nom[N + i] = ent[0].x;  // round 0 nomination: the most distant partner
             }
           }
         }
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, RuleTab rt) {
     if (lane == 0 && valid) d.bm_ba[i >> 5] = m;
     int slot = warp_alloc(&d.cnt->n_act_b, nbrk > 0 ? 1 : 0);
     if (nbrk > 0) d.act_b[slot] = (int)i;
-    if (valid) stat_add(d, r, ST_BREAK_CANDIDATES, ncand_b);
+    stat_add_warp(d.stats, r, ST_BREAK_CANDIDATES, (unsigned)ncand_b);
   }
 }
 
@@ -154,7 +156,10 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
     }
     long long tot;
     long long ex = block_excl_scan(sum, sh, &tot);
-    if (threadIdx.x == 0) s_excl = lookback(d.st_scan, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
+    if (threadIdx.x < 32) {
+      long long x = lookback(d.st_scan, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
+      if (threadIdx.x == 0) s_excl = x;
+    }
     __syncthreads();
     if (s_excl < 0) return;
     long long pre = s_excl + ex;
@@ -189,8 +194,8 @@ __global__ void __launch_bounds__(256) k_scatter(Dev d) {
 
 // Graph distance test on the bond graph before the call: never at distance 1,
 // at 2 only with paircheck13, at 3 only with paircheck14, always beyond.
-__device__ __forceinline__ bool pair_eligible(const Dev& d, const RuleTab& rt, int i, int j, const uint4& si,
-                                              const uint4& sj) {
+__device__ __forceinline__ bool pair_eligible(const uint4* __restrict__ slots, const RuleTab& rt, int i, int j,
+                                              const uint4& si, const uint4& sj) {
   int ni[SLOTS], nj[SLOTS];
 #pragma unroll
   for (int q = 0; q < SLOTS; ++q) {
@@ -207,7 +212,7 @@ __device__ __forceinline__ bool pair_eligible(const Dev& d, const RuleTab& rt, i
   bool g3 = false;
   for (int q = 0; q < SLOTS && !g3; ++q) {
     if (ni[q] < 0) continue;
-    uint4 sa = d.slots[ni[q]];
+    uint4 sa = slots[ni[q]];
 #pragma unroll
     for (int q2 = 0; q2 < SLOTS; ++q2) {
       int b = s_partner(s_get(sa, q2));
@@ -220,94 +225,179 @@ __device__ __forceinline__ bool pair_eligible(const Dev& d, const RuleTab& rt, i
   return true;
 }
 
-// Visit every creation candidate of the eligible bead at sorted index e:
-// partners in the 27 neighbouring cells (distinct cells when a replica has
-// fewer than 3 per axis), last matching creation rule, graph-distance
-// exclusion.  visit(j, d2, rule, type this bead stores).
-template <class V>
-__device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab& rt, const int4& me, int i, V& visit) {
+// Per-bead candidate list kept in registers / local memory by the fast path.
+struct LocalList {
+  long long kd[MAXC];
+  int kp[MAXC], ki[MAXC];
+  int cnt, pairs, me;
+  bool overflow;
+};
+
+// Rare path of the neighbour scan, kept out of line so the hot loop stays
+// small: last matching creation rule, graph-distance exclusion, sorted
+// insertion (mode 0: into the local list; 1: count; 2: write to `out`).
+__device__ __noinline__ void cand_slow(const uint4* __restrict__ slots, const RuleTab* __restrict__ rtp, int i, int j,
+                                       int ti, int tj, long long dd, uint4 si, LocalList* ll, int mode, int4** out) {
+  const RuleTab& rt = *rtp;
+  uint4 sj = slots[j];
+  int sta, stb, k;
+  if (i < j) k = creation_rule(rt, ti, tj, si, sj, dd, &sta, &stb);
+  else k = creation_rule(rt, tj, ti, sj, si, dd, &stb, &sta);
+  if (k < 0 || !pair_eligible(slots, rt, i, j, si, sj)) return;
+  ll->pairs += j > i;
+  if (mode == 2) {
+    *(*out)++ = make_int4(j, k | (sta << 8), (int)(unsigned)(unsigned long long)dd, (int)(dd >> 32));
+    return;
+  }
+  if (mode == 1) {
+    ++ll->cnt;
+    return;
+  }
+  if (ll->cnt == MAXC) {
+    ll->overflow = true;
+    return;
+  }
+  int at = ll->cnt;
+  while (at > 0 && (ll->kd[at - 1] > dd || (ll->kd[at - 1] == dd && ll->kp[at - 1] > j))) {
+    ll->kd[at] = ll->kd[at - 1];
+    ll->kp[at] = ll->kp[at - 1];
+    ll->ki[at] = ll->ki[at - 1];
+    --at;
+  }
+  ll->kd[at] = dd;
+  ll->kp[at] = j;
+  ll->ki[at] = k | (sta << 8);
+  ++ll->cnt;
+}
+
+// Visit every creation candidate of eligible bead i (sorted entry `me`):
+// entries of the 27 neighbouring cells (distinct cells when a replica has
+// fewer than 3 per axis) whose bead type can pair with this one and that lie
+// within the largest creation distance are collected first; the rule and
+// graph-distance tests then run on them after the scan, so the lanes of a
+// warp take the rare path together instead of one after another.
+__device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned tmask,
+                                                long long r2max, const int4& me, int i, LocalList* ll, int mode,
+                                                int4** out) {
   int ti = me.w & 15;
   int r = d.rep[i];
   int L = (int)d.box[r], nc = d.nc[r];
   long long cb = d.cell_base[r];
-  uint4 si = d.slots[i];
-  int c0[3] = {(int)((long long)me.x * nc / L), (int)((long long)me.y * nc / L), (int)((long long)me.z * nc / L)};
-  int offs[3] = {0, 1, nc - 1};
+  int cx = (int)((long long)me.x * nc / L), cy = (int)((long long)me.y * nc / L), cz = (int)((long long)me.z * nc / L);
+  // x and y: the distinct neighbouring columns; z: the three neighbouring
+  // cells of a column are contiguous in cell order, so each column is one or
+  // two contiguous runs of the sorted array
   int noff = nc >= 3 ? 3 : nc;
-  for (int a = 0; a < noff; ++a) {
-    int cx = (c0[0] + offs[a]) % nc;
+  int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
+  int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
+  int z0, z1, w0 = 0, w1 = -1;  // main run [z0, z1], wrapped run [w0, w1]
+  if (nc >= 3) {
+    z0 = cz - 1;
+    z1 = cz + 1;
+    if (z0 < 0) {  // cz = 0: cells nc-1, 0, 1
+      z0 = 0;
+      w0 = w1 = nc - 1;
+    } else if (z1 >= nc) {  // cz = nc-1: cells nc-2, nc-1, 0
+      z1 = nc - 1;
+      w0 = w1 = 0;
+    }
+  } else {
+    z0 = 0;
+    z1 = nc - 1;
+  }
+  int pj[MAXC];
+  long long pd[MAXC];
+  int np = 0;
+  bool more = false;
+  for (int a = 0; a < noff; ++a)
     for (int b = 0; b < noff; ++b) {
-      int cy = (c0[1] + offs[b]) % nc;
-      for (int c = 0; c < noff; ++c) {
-        int cz = (c0[2] + offs[c]) % nc;
-        long long cell = cb + ((long long)cx * nc + cy) * nc + cz;
-        int q0 = d.cell_start[cell], q1 = d.cell_start[cell + 1];
+      long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
+      for (int run = 0; run < 2; ++run) {
+        int lo = run ? w0 : z0, hi = run ? w1 : z1;
+        if (hi < lo) continue;
+        int q0 = d.cell_start[row + lo], q1 = d.cell_start[row + hi + 1];
         for (int q = q0; q < q1; ++q) {
           int4 o = d.sorted[q];
-          int j = o.w >> 4, tj = o.w & 15;
-          if (j == i || !rt.pair_rules[ti][tj]) continue;
+          if (!((tmask >> (o.w & 15)) & 1u)) continue;
           long long dd = dist2(me, o, L);
-          if (dd > rt.r2max) continue;
-          uint4 sj = d.slots[j];
-          int sta, stb, k;
-          if (i < j) k = creation_rule(rt, ti, tj, si, sj, dd, &sta, &stb);
-          else k = creation_rule(rt, tj, ti, sj, si, dd, &stb, &sta);
-          if (k < 0) continue;
-          if (!pair_eligible(d, rt, i, j, si, sj)) continue;
-          visit(j, dd, k, sta);
+          if (dd > r2max || (o.w >> 4) == i) continue;
+          if (np < MAXC) {
+            pj[np] = o.w;
+            pd[np] = dd;
+            ++np;
+          } else {
+            more = true;
+          }
         }
       }
     }
+  if (more && mode == 0) {
+    ll->overflow = true;  // finished exactly by k_cand_overflow
+    return;
   }
+  if (more) {  // counting / writing passes of the overflow path: rescan without a buffer
+    uint4 si = d.slots[i];
+    for (int a = 0; a < noff; ++a)
+      for (int b = 0; b < noff; ++b) {
+        long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
+        for (int run = 0; run < 2; ++run) {
+          int lo = run ? w0 : z0, hi = run ? w1 : z1;
+          if (hi < lo) continue;
+          int q0 = d.cell_start[row + lo], q1 = d.cell_start[row + hi + 1];
+          for (int q = q0; q < q1; ++q) {
+            int4 o = d.sorted[q];
+            int tj = o.w & 15;
+            if (!((tmask >> tj) & 1u)) continue;
+            long long dd = dist2(me, o, L);
+            if (dd > r2max || (o.w >> 4) == i) continue;
+            cand_slow(d.slots, rtp, i, o.w >> 4, ti, tj, dd, si, ll, mode, out);
+          }
+        }
+      }
+    return;
+  }
+  if (np == 0) return;
+  uint4 si = d.slots[i];
+  for (int k = 0; k < np; ++k) cand_slow(d.slots, rtp, i, pj[k] >> 4, ti, pj[k] & 15, pd[k], si, ll, mode, out);
 }
-
-// sorted insertion into a per-thread list of at most MAXC entries
-struct LocalList {
-  long long kd[MAXC];
-  int kp[MAXC], ki[MAXC];
-  int cnt = 0, pairs = 0, me = 0;
-  bool overflow = false;
-  __device__ void operator()(int j, long long dd, int k, int sta) {
-    pairs += j > me;
-    if (cnt == MAXC) {
-      overflow = true;
-      return;
-    }
-    int at = cnt;
-    while (at > 0 && (kd[at - 1] > dd || (kd[at - 1] == dd && kp[at - 1] > j))) {
-      kd[at] = kd[at - 1];
-      kp[at] = kp[at - 1];
-      ki[at] = ki[at - 1];
-      --at;
-    }
-    kd[at] = dd;
-    kp[at] = j;
-    ki[at] = k | (sta << 8);
-    ++cnt;
-  }
-};
 
 __device__ __forceinline__ void activate_creator(const Dev& d, int i, int start, int len) {
   d.cand_start[i] = start;
   d.cand_len[i] = len;
   d.mate[i] = -1;
   d.ptr[i] = 0;
+  d.nom[i] = d.cand[start].x;  // round 0: nobody is matched yet, so the nearest partner
   atomicOr(&d.bm_ca[i >> 5], 1u << (i & 31));
 }
 
-__global__ void __launch_bounds__(256) k_candidates(Dev d, RuleTab rt) {
+// bit tj of the mask of bead type ti: some creation rule pairs ti with tj
+__device__ __forceinline__ void load_type_masks(const RuleTab& rt, unsigned* s_mask) {
+  if (threadIdx.x < 16) {
+    unsigned m = 0;
+    for (int b = 0; b < 16; ++b) m |= (rt.pair_rules[threadIdx.x][b] != 0) << b;
+    s_mask[threadIdx.x] = m;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+  __shared__ unsigned s_mask[16];
+  load_type_masks(*rtp, s_mask);
+  const long long r2max = rtp->r2max;
   const int n = d.cnt->n_sorted;
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     int e = base + threadIdx.x;
     int i = -1, r = 0;
     LocalList ll;
+    ll.cnt = ll.pairs = 0;
+    ll.overflow = false;
     if (e < n) {
       int4 me = d.sorted[e];
       i = me.w >> 4;
       r = d.rep[i];
       ll.me = i;
-      scan_candidates(d, rt, me, i, ll);
+      scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &ll, 0, nullptr);
     }
     // beads with more than MAXC candidates are finished by k_cand_overflow
     int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
@@ -327,41 +417,32 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, RuleTab rt) {
     }
     int slot = warp_alloc(&d.cnt->n_act_c, cnt > 0 ? 1 : 0);
     if (cnt > 0) d.act_c[slot] = i;
-    if (ll.pairs && !ll.overflow) stat_add(d, r, ST_CANDIDATES, ll.pairs);
+    stat_add_warp(d.stats, r, ST_CANDIDATES, ll.overflow ? 0u : (unsigned)ll.pairs);
   }
 }
 
-struct CountV {
-  int cnt = 0, pairs = 0, me = 0;
-  __device__ void operator()(int j, long long, int, int) {
-    ++cnt;
-    pairs += j > me;
-  }
-};
-struct WriteV {
-  int4* out;
-  __device__ void operator()(int j, long long dd, int k, int sta) {
-    *out++ = make_int4(j, k | (sta << 8), (int)(unsigned)(unsigned long long)dd, (int)(dd >> 32));
-  }
-};
-
 // Exact path for beads with more than MAXC candidates: count, allocate,
 // write, then sort the bead's list by (d2, partner) in place.
-__global__ void __launch_bounds__(128) k_cand_overflow(Dev d, RuleTab rt) {
+__global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp) {
+  __shared__ unsigned s_mask[16];
+  load_type_masks(*rtp, s_mask);
+  const long long r2max = rtp->r2max;
   const int n = d.cnt->n_ovf;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     int4 me = d.sorted[d.ovf[k]];
     int i = me.w >> 4;
-    CountV cv;
+    LocalList cv;
+    cv.cnt = cv.pairs = 0;
     cv.me = i;
-    scan_candidates(d, rt, me, i, cv);
+    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 1, nullptr);
     int at = atomicAdd(&d.cnt->cand_used, cv.cnt);
     if ((long long)at + cv.cnt > d.cand_cap) {
       atomicOr(d.err, ERR_CAND_CAP);
       continue;
     }
-    WriteV wv{d.cand + at};
-    scan_candidates(d, rt, me, i, wv);
+    int pairs = cv.pairs;
+    int4* w = d.cand + at;
+    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 2, &w);
     int4* lst = d.cand + at;
     for (int a = 1; a < cv.cnt; ++a) {
       int4 x = lst[a];
@@ -378,7 +459,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, RuleTab rt) {
     }
     activate_creator(d, i, at, cv.cnt);
     d.act_c[atomicAdd(&d.cnt->n_act_c, 1)] = i;
-    stat_add(d, d.rep[i], ST_CANDIDATES, cv.pairs);
+    stat_add(d, d.rep[i], ST_CANDIDATES, pairs);
   }
 }
 
@@ -388,19 +469,33 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, RuleTab rt) {
 // or max_rounds rounds.  Per-bead lists are sorted, so a bead's nominee is
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_match(Dev d, RuleTab rt) {
-  const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b, nA = na_c + na_b;
+__global__ void __launch_bounds__(256) k_match(Dev d, const RuleTab* __restrict__ rtp) {
+  const RuleTab& rt = *rtp;
+  const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b;
   const long long N = d.N;
   const int stride = gridDim.x * blockDim.x;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  // round 0 reads the two activation lists; later rounds read the compacted
+  // list of beads that were still unmatched and nominated someone
+  int n = na_c + na_b;
   int round = 0;
   while (true) {
-    // nomination
-    for (int idx = g; idx < nA; idx += stride) {
-      int sys = idx >= na_c;
-      int i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
+    const int* src = round ? d.live[(round - 1) & 1] : nullptr;
+    int* dst = d.live[round & 1];
+    // nomination: first list entry whose partner is still unmatched (round 0
+    // was written by the list producers)
+    for (int idx = round ? g : n; idx < n; idx += stride) {
+      int sys, i;
+      if (src) {
+        int e = src[idx];
+        sys = (unsigned)e >> 31;
+        i = e & 0x7FFFFFFF;
+      } else {
+        sys = idx >= na_c;
+        i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
+      }
       long long o = sys ? N : 0;
-      if (d.mate[o + i] != -1) continue;
       int p = d.ptr[o + i];
       int len = sys ? d.brk_len[i] : d.cand_len[i];
       const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
@@ -416,23 +511,40 @@ __global__ void __launch_bounds__(256) k_match(Dev d, RuleTab rt) {
       d.ptr[o + i] = p;
       d.nom[o + i] = j;
     }
-    if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
-    // mutual nominations are matched
-    for (int idx = g; idx < nA; idx += stride) {
-      int sys = idx >= na_c;
-      int i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
-      long long o = sys ? N : 0;
-      if (d.mate[o + i] != -1) continue;
-      int j = d.nom[o + i];
-      if (j >= 0 && ld_cg(d.nom + o + j) == i) {
-        d.mate[o + i] = j;
-        if (i < j) {
-          int r = d.rep[i];
-          atomicAdd(&d.cnt->round_matched[round], 1);
-          d.round_hit[sys * d.R + r] = 1;
-          stat_add(d, r, sys ? ST_BREAK_MATCHED : ST_CREATE_MATCHED, 1);
+    if (round && !grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    // mutual nominations are matched; unmatched nominators carry over
+    for (int base = g - lane; base < n; base += stride) {
+      int idx = base + lane;
+      int sys = 0, r = 0, i = -1;
+      bool hit = false, keep = false;
+      if (idx < n) {
+        if (src) {
+          int e = src[idx];
+          sys = (unsigned)e >> 31;
+          i = e & 0x7FFFFFFF;
+        } else {
+          sys = idx >= na_c;
+          i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
+        }
+        long long o = sys ? N : 0;
+        int j = d.nom[o + i];
+        if (j >= 0 && ld_cg(d.nom + o + j) == i) {
+          d.mate[o + i] = j;
+          if (i < j) {
+            r = d.rep[i];
+            hit = true;
+            d.round_hit[sys * d.R + r] = 1;
+          }
+        } else {
+          keep = j >= 0;
         }
       }
+      unsigned m = __ballot_sync(FULL, hit);
+      if (lane == 0 && m) atomicAdd(&d.cnt->round_matched[round], __popc(m));
+      stat_add_warp(d.stats, r, ST_CREATE_MATCHED, hit && !sys);
+      stat_add_warp(d.stats, r, ST_BREAK_MATCHED, hit && sys);
+      int at = warp_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
+      if (keep) dst[at] = (int)((unsigned)sys << 31 | (unsigned)i);
     }
     if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
     int matched = ld_cg(&d.cnt->round_matched[round]);
@@ -445,8 +557,9 @@ __global__ void __launch_bounds__(256) k_match(Dev d, RuleTab rt) {
         }
       }
     }
+    n = ld_cg(&d.cnt->round_live[round]);
     ++round;
-    if (matched == 0) break;
+    if (matched == 0 || n == 0) break;
     if (rt.max_rounds && round >= rt.max_rounds) break;
     if (round >= MAX_ROUNDS) {
       if (g == 0) atomicOr(d.err, ERR_ROUNDS);
@@ -459,7 +572,8 @@ __global__ void __launch_bounds__(256) k_match(Dev d, RuleTab rt) {
 // ---------------------------------------------------------------------------
 // k_edit: trials and in-place edit of each bead's own slots
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_edit(Dev d, RuleTab rt) {
+__global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__ rtp) {
+  const RuleTab& rt = *rtp;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
@@ -467,15 +581,16 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, RuleTab rt) {
     long long i = base + threadIdx.x;
     bool valid = i < N;
     bool dirty = false, fresh = false;
+    int r = 0;
+    unsigned n_killed = 0, n_broken = 0, n_conv = 0, n_formed = 0;
     if (valid) {
       unsigned wca = d.bm_ca[i >> 5], wba = d.bm_ba[i >> 5];
       bool ca = (wca >> (i & 31)) & 1u, ba = (wba >> (i & 31)) & 1u;
       if (ca || ba) {
-        int r = d.rep[i];
+        r = d.rep[i];
         uint4 s = d.slots[i];
         unsigned removed = 0, changed = 0;
         int conv_partner = -1, form_partner = -1, form_type = 0;
-        long long n_killed = 0, n_broken = 0, n_conv = 0, n_formed = 0;
         if (ba) {
           removed = d.killmask[i];
 #pragma unroll
@@ -551,12 +666,22 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, RuleTab rt) {
           fresh = form_partner >= 0 || conv_partner >= 0;
           if (dirty) d.rem[i] = rp;
           if (fresh) d.newp[i] = make_int2(form_partner, conv_partner);
-          stat_add(d, r, ST_KILLED, n_killed);
-          stat_add(d, r, ST_BROKEN, n_broken);
-          stat_add(d, r, ST_CONVERTED, n_conv);
-          stat_add(d, r, ST_FORMED, n_formed);
-          long long delta = n_formed - n_broken - n_killed;
-          if (delta) atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)delta);
+        }
+      }
+    }
+    stat_add_warp(d.stats, r, ST_KILLED, n_killed);
+    stat_add_warp(d.stats, r, ST_BROKEN, n_broken);
+    stat_add_warp(d.stats, r, ST_CONVERTED, n_conv);
+    stat_add_warp(d.stats, r, ST_FORMED, n_formed);
+    {
+      int dv = (int)n_formed - (int)n_broken - (int)n_killed;
+      if (__ballot_sync(FULL, dv != 0)) {
+        unsigned grp = __match_any_sync(FULL, r);
+        if (grp == FULL) {
+          int sum = (int)__reduce_add_sync(FULL, (unsigned)dv);
+          if (lane == 0 && sum) atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)sum);
+        } else if (dv) {
+          atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)dv);
         }
       }
     }
@@ -610,10 +735,15 @@ __global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
     }
     long long tot;
     long long ex = block_excl_scan(cnt, sh, &tot);
-    if (threadIdx.x == 0) s_excl = lookback(d.st_nb, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
+    if (threadIdx.x < 32) {
+      long long x = lookback(d.st_nb, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
+      if (threadIdx.x == 0) s_excl = x;
+    }
     __syncthreads();
     if (s_excl < 0) return;
     long long at = s_excl + ex;
+    int r0 = beg < N ? d.rep[beg] : 0;
+    unsigned n0 = 0;
 #pragma unroll
     for (int k = 0; k < NB_PER_THREAD; ++k) {
       long long u = beg + k;
@@ -627,8 +757,10 @@ __global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
         d.nbl[at++] = make_int4((int)u, v, r, 0);
         ++nr;
       }
-      if (nr) atomicAdd(&d.nbl_count[r], nr);
+      if (nr && r == r0) n0 += nr;
+      else if (nr) atomicAdd(&d.nbl_count[r], nr);
     }
+    count_add_warp(d.nbl_count, r0, n0);
     if (t == ntiles - 1 && threadIdx.x == blockDim.x - 1) d.cnt->n_nbl = (int)at;
     __syncthreads();
   }
@@ -697,6 +829,7 @@ __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
 
 __global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
   __shared__ long long s_excl, s_tile;
+  __shared__ int s_tot;
   const bool dih = which != 0;
   int4* recs = dih ? d.dih : d.ang;
   const int* count = dih ? d.n_dih : d.n_ang;
@@ -748,7 +881,6 @@ __global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
       if (lane == 0) s_cnt[k][wid] = __popc(bal[k]);
     }
     __syncthreads();
-    long long tot = 0;
     if (threadIdx.x == 0) {
       int acc = 0;
       for (int k = 0; k < PURGE_PER_THREAD; ++k)
@@ -756,10 +888,14 @@ __global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
           s_off[k][w] = acc;
           acc += s_cnt[k][w];
         }
-      tot = acc;
-      s_excl = lookback(status, t, tb[r], (unsigned long long)tot, d.spin_limit, d.err);
-      if (s_excl >= 0 && lt == tb[r + 1] - tb[r] - 1) {
-        kept[r] = (int)(s_excl + tot);
+      s_tot = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      long long x = lookback(status, t, tb[r], (unsigned long long)s_tot, d.spin_limit, d.err);
+      if (threadIdx.x == 0) {
+        s_excl = x;
+        if (x >= 0 && lt == tb[r + 1] - tb[r] - 1) kept[r] = (int)(x + s_tot);
       }
     }
     __syncthreads();
@@ -894,7 +1030,8 @@ struct WriteEmit {
   }
 };
 
-__global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, RuleTab rt, int all_new) {
+__global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new) {
+  const RuleTab& rt = *rtp;
   __shared__ long long sh[33];
   __shared__ long long s_excl, s_tile;
   const int R = d.R;
@@ -915,12 +1052,15 @@ __global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, RuleTab rt, int
     long long packed = (long long)ce.na | ((long long)ce.nd << 32);
     long long tot;
     long long ex = block_excl_scan(packed, sh, &tot);
-    if (threadIdx.x == 0) {
-      s_excl = lookback(d.st_rb, t, d.tb_nb[r], (unsigned long long)tot, d.spin_limit, d.err);
-      if (s_excl >= 0 && lt == d.tb_nb[r + 1] - d.tb_nb[r] - 1) {
-        long long all = s_excl + tot;
-        d.added_ang[r] = (int)(all & 0xFFFFFFFFll);
-        d.added_dih[r] = (int)(all >> 32);
+    if (threadIdx.x < 32) {
+      long long x = lookback(d.st_rb, t, d.tb_nb[r], (unsigned long long)tot, d.spin_limit, d.err);
+      if (threadIdx.x == 0) {
+        s_excl = x;
+        if (x >= 0 && lt == d.tb_nb[r + 1] - d.tb_nb[r] - 1) {
+          long long all = x + tot;
+          d.added_ang[r] = (int)(all & 0xFFFFFFFFll);
+          d.added_dih[r] = (int)(all >> 32);
+        }
       }
     }
     __syncthreads();
