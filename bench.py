@@ -323,7 +323,7 @@ def main():
     step_gbs = alg / (res["ms"] * 1e-3) / 1e9
     rank, world, _ = dist_env()
     cpu = cpu_baseline(args.cpu_baseline_seconds) if world == 1 else None
-    kernels_per_step = 15 + 6
+    kernels_per_step = 14 + 5  # step graph 13 + argument kernel; forces graph 4 + argument kernel
     line = dict(
         metric=METRIC, value=res["value"], unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=res["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64+f32",

@@ -182,6 +182,27 @@ dynbond_status build_rules(dynbond_ctx* c, const dynbond_rule* rules, int n) {
     if (r.kind == DYNBOND_BREAKBOND || r.kind == DYNBOND_CONVERTBOND || r.kind == DYNBOND_KILLBOND)
       rt.breakish |= 1u << r.type;
   }
+  // precompiled lookups: stored types per bead type; break/convert/kill
+  // rules grouped by bond type (list order kept within a type)
+  for (int k = 0; k < n; ++k) {
+    const dynbond_rule& r = rules[k];
+    if (r.kind != DYNBOND_CREATEBOND && r.kind != DYNBOND_CREATEDIRBOND) continue;
+    int t2 = r.kind == DYNBOND_CREATEDIRBOND ? r.type2 : r.type;
+    for (int a = 0; a < 16; ++a) {
+      if ((r.bead_mask[0] >> a) & 1u) rt.role_store[a] |= 1u << r.type;
+      if ((r.bead_mask[1] >> a) & 1u) rt.role_store[a] |= 1u << t2;
+    }
+  }
+  int nbk = 0;
+  for (int t = 0; t < 16; ++t) {
+    rt.bk_start[t] = nbk;
+    for (int k = 0; k < n; ++k) {
+      const dynbond_rule& r = rules[k];
+      if ((r.kind == DYNBOND_BREAKBOND || r.kind == DYNBOND_CONVERTBOND || r.kind == DYNBOND_KILLBOND) && r.type == t)
+        rt.bk_list[nbk++] = k;
+    }
+  }
+  rt.bk_start[16] = nbk;
   const dynbond_params& p = c->prm;
   rt.reactive = p.reactive_mask;
   rt.pc13 = p.paircheck13 != 0;
@@ -218,7 +239,7 @@ void mark(dynbond_ctx* c, std::vector<cudaEvent_t>& ev, size_t k) {
 cudaError_t launch_match(dynbond_ctx* c) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->grid_match);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(1024);
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -233,12 +254,7 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   cudaStream_t s = c->stream;
   size_t k = 0;
   mark(c, c->ev_step, k++);
-  cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s);
-  cudaMemsetAsync(d.cell_start, 0, sizeof(int) * (c->n_cells + 1), s);
-  cudaMemsetAsync(d.bm_ca, 0, sizeof(unsigned) * c->W, s);
-  cudaMemsetAsync(c->small, 0, c->small_bytes, s);
-  cudaMemsetAsync(c->status_all, 0, c->status_bytes, s);
-  k_tiles<<<1, 1024, 0, s>>>(d, 0);
+  k_setup<<<c->nsm * 2, 1024, 0, s>>>(d);
   mark(c, c->ev_step, k++);
   k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
   mark(c, c->ev_step, k++);
@@ -256,11 +272,10 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 0);
   k_tiles<<<1, 1024, 0, s>>>(d, 1);
   mark(c, c->ev_step, k++);
-  k_purge<<<c->grid_seg, 256, 0, s>>>(d, 0);
-  k_purge<<<c->grid_seg, 256, 0, s>>>(d, 1);
+  k_purge<<<c->nsm * 2, PURGE_TILE / 8, 0, s>>>(d);
   mark(c, c->ev_step, k++);
   k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->d_rt, 0);
-  k_finalize<<<(c->R + 255) / 256, 256, 0, s>>>(d);
+  k_finalize<<<1, 1024, 0, s>>>(d);
   mark(c, c->ev_step, k++);
   return cudaGetLastError();
 }
@@ -270,14 +285,9 @@ cudaError_t enqueue_forces(dynbond_ctx* c) {
   cudaStream_t s = c->stream;
   size_t k = 0;
   mark(c, c->ev_forces, k++);
-  cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * c->R, s);
-  k_tiles<<<1, 1024, 0, s>>>(d, 2);
-  mark(c, c->ev_forces, k++);
   k_bond_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
   mark(c, c->ev_forces, k++);
-  k_angle_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
-  mark(c, c->ev_forces, k++);
-  k_dihedral_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
+  k_angle_dihedral_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
   mark(c, c->ev_forces, k++);
   k_ev_out<<<1, 256, 0, s>>>(d);
   return cudaGetLastError();
@@ -472,6 +482,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   }
   c->n_cells = cell_base[R];
   c->W = N / 32 + 1;
+  c->d.W = c->W;
 
   Dev& d = c->d;
   d.N = N;
@@ -541,6 +552,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.tb_dih, R + 1);
   ALLOC(d.tb_nb, R + 1);
   ALLOC(d.tb_beads, R + 1);
+  ALLOC(d.tb_fang, R + 1);
+  ALLOC(d.tb_fdih, R + 1);
   ALLOC(d.ev_acc, 7 * R);
   // per-call counters zeroed together: kept/added counts, new-bond counts,
   // round flags, statistics
@@ -551,6 +564,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     ALLOC(base, bytes);
     c->small = base;
     c->small_bytes = bytes;
+    d.small = (int*)base;
+    d.small_words = (long long)(bytes / sizeof(int));
     int* ip = (int*)base;
     d.kept_ang = ip;
     d.kept_dih = ip + R;
@@ -561,8 +576,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     d.stats = (long long*)(base + ((ints * sizeof(int) + 15) / 16) * 16);
   }
   {
-    c->st_scan_n = c->n_cells / (256 * 8) + 2;
-    c->st_nb_n = N / (256 * 4) + 2;
+    c->st_scan_n = c->n_cells / (256 * 32) + 2;
+    c->st_nb_n = N / (256 * 64) + 2;
     c->st_pa_n = 6 * N / PURGE_TILE + R + 2;
     c->st_pd_n = 18 * N / PURGE_TILE + R + 2;
     c->st_rb_n = 2 * N / REBUILD_TILE + R + 2;
@@ -571,6 +586,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     ALLOC(base, tot);
     c->status_all = base;
     c->status_bytes = (size_t)tot * 8;
+    d.status_all = base;
+    d.status_words = tot;
     d.st_scan = base;
     d.st_nb = d.st_scan + c->st_scan_n;
     d.st_pa = d.st_nb + c->st_nb_n;
@@ -630,12 +647,13 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
 
   // ---- launch geometry
   c->grid_bead = bounded_grid(N, 256, c->nsm * 8);
-  c->grid_scan = bounded_grid(c->n_cells, 256 * 8, c->nsm * 4);
+  c->grid_scan = bounded_grid(c->n_cells, 256 * 32, c->nsm * 4);
   c->grid_cand = bounded_grid(N, 256, c->nsm * 8);
-  c->grid_nb = bounded_grid(N, 256 * 4, c->nsm * 4);
+  c->grid_nb = bounded_grid(N, 256 * 64, c->nsm * 4);
   c->grid_seg = c->nsm * 4;
-  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 256, 4),
-                                       bounded_grid(N, 256, c->nsm * 4)));
+  // one 1024-thread block per SM: full latency hiding with few barrier arrivals
+  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 1024, 1),
+                                       bounded_grid(N, 1024, c->nsm)));
 
   // ---- initial interactions: the typed set of every path of the initial graph
   CUDA_TRY(c, cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s));
@@ -644,15 +662,16 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 1);
   k_tiles<<<1, 1024, 0, s>>>(d, 1);
   k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->d_rt, 1);
-  k_finalize<<<(R + 255) / 256, 256, 0, s>>>(d);
+  k_finalize<<<1, 1024, 0, s>>>(d);
+  CUDA_TRY(c, cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * R, s));
   CUDA_TRY(c, cudaGetLastError());
   st = device_status(c);
   if (st) return (st);
 
   // ---- profiling events and graphs
   if (c->profile) {
-    c->names_step = {"step_setup", "bead", "cells", "candidates", "match", "edit", "newbonds", "purge", "rebuild"};
-    c->names_forces = {"forces_setup", "bond_forces", "angle_forces", "dihedral_forces"};
+    c->names_step = {"setup", "bead", "cells", "candidates", "match", "edit", "newbonds", "purge", "rebuild"};
+    c->names_forces = {"bond_forces", "angle_dihedral_forces"};
     c->ev_step.resize(c->names_step.size() + 1);
     c->ev_forces.resize(c->names_forces.size() + 1);
     for (auto& e : c->ev_step) CUDA_TRY(c, cudaEventCreate(&e));

@@ -57,6 +57,10 @@ struct RuleTab {
   int maxbond_idx[MAXR], angle_idx[MAXR], dihedral_idx[MAXR];
   int pc13, pc14, max_rounds, prob_mode;
   uint32_t key0, key1;
+  // precompiled lookups
+  uint32_t role_store[16];      // bond types a bead of type t could store under some creation rule
+  int bk_start[17];             // breakbond / convertbond / killbond rules of bond type t:
+  int bk_list[MAXR];            //   bk_list[bk_start[t] .. bk_start[t+1]) in list order
 };
 
 // Arguments that change from call to call, read from device memory so that a
@@ -144,6 +148,13 @@ struct Dev {
   int* tb_dih;                 // [R+1]
   int* tb_nb;                  // [R+1]
   int* tb_beads;               // [R+1] (static)
+  int* tb_fang;                // [R+1] force tile bases of the final lists
+  int* tb_fdih;                // [R+1]
+  long long W;                 // bitmap words
+  int* small;                  // per-call per-replica scratch, zeroed by k_setup
+  long long small_words;
+  unsigned long long* status_all;  // all look-back status words, zeroed by k_setup
+  long long status_words;
   unsigned long long* st_scan; // look-back status words
   unsigned long long* st_nb;
   unsigned long long* st_pa;
@@ -282,14 +293,12 @@ __device__ __forceinline__ bool maxbond_ok(const RuleTab& rt, int bt, const uint
 // Can the bead take part in any creation pair (reactive, named by a creation
 // rule in some role with room for the type it would store)?
 __device__ __forceinline__ bool creation_eligible(const RuleTab& rt, int bt, const uint4& s) {
-  if (!has_bit(rt.reactive, bt)) return false;
-  uint32_t m = rt.role_rules[bt];
+  if (!has_bit(rt.reactive, bt) || s_deg(s) >= SLOTS) return false;
+  uint32_t m = rt.role_store[bt];
   while (m) {
-    int k = __ffs(m) - 1;
+    int t = __ffs(m) - 1;
     m &= m - 1;
-    if (has_bit(rt.bead[k][0], bt) && maxbond_ok(rt, bt, s, rt.type[k])) return true;
-    int t2 = rt.kind[k] == DYNBOND_CREATEDIRBOND ? rt.type2[k] : rt.type[k];
-    if (has_bit(rt.bead[k][1], bt) && maxbond_ok(rt, bt, s, t2)) return true;
+    if (maxbond_ok(rt, bt, s, t)) return true;
   }
   return false;
 }
@@ -418,7 +427,7 @@ __device__ __forceinline__ long long lookback(unsigned long long* status, long l
         if (lane == 0) atomicOr(err, ERR_TIMEOUT);
         return -1;
       }
-      __nanosleep(32);
+      if (spins > 4096) __nanosleep(32);  // predecessors are normally microseconds away: poll first
       continue;
     }
     unsigned long long v = ((need >> lane) & 1u) ? (s & VM) : 0ull;
@@ -462,32 +471,26 @@ __device__ __forceinline__ void count_add_warp(int* counts, int r, unsigned v) {
 // ---------------------------------------------------------------------------
 // grid barrier for co-resident (cooperative) launches, bounded: returns false
 // (error bit set) if the other blocks do not arrive within spin_limit polls.
-// bar[0] = arrivals, bar[1] = generation.
+// bar[0] counts arrivals monotonically within a launch (zeroed before it):
+// the k-th barrier completes when the count reaches k * gridDim.x.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool grid_sync(unsigned* bar, int spin_limit, unsigned* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned gen = ld_acquire_u32(bar + 1);
-    __threadfence();
-    unsigned arrived = atomicAdd(bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      int spins = 0;
-      while (ld_acquire_u32(bar + 1) == gen) {
-        if (++spins > spin_limit || (*(volatile unsigned*)err & ERR_TIMEOUT)) {
-          atomicOr(err, ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        if (spins > 256) __nanosleep(32);
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    unsigned target = (old / gridDim.x + 1) * gridDim.x;
+    int spins = 0;
+    while ((int)(ld_acquire_u32(bar) - target) < 0) {
+      if (++spins > spin_limit || (*(volatile unsigned*)err & ERR_TIMEOUT)) {
+        atomicOr(err, ERR_TIMEOUT);
+        ok = 0;
+        break;
       }
+      if (spins > 512) __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;

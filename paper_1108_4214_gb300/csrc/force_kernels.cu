@@ -7,7 +7,8 @@
 //   dihedrals E = K (1 + d cos phi) (Sec. 3), forces from the
 //             Blondel-Karplus (J. Comput. Chem. 17, 1132 (1996)) derivatives
 //             of phi, free of the sin(phi) = 0 singularity.
-// Work items are (replica, tile) pairs so each block reduces one replica.
+// Work items are (replica, tile) pairs; a block reduces its energy / virial
+// when it moves to another replica and at its end.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -81,6 +82,15 @@ struct EV {
     hi[k] = s;
     lo[k] = __fadd_rn(lo[k], e);
   }
+  // W_ab += r_a F_b + q_a G_b, the two terms summed in FP32 first
+  __device__ void vir2(float3 r, float3 f, float3 q, float3 g) {
+    add(1, r.x * f.x + q.x * g.x);
+    add(2, r.y * f.y + q.y * g.y);
+    add(3, r.z * f.z + q.z * g.z);
+    add(4, r.x * f.y + q.x * g.y);
+    add(5, r.x * f.z + q.x * g.z);
+    add(6, r.y * f.z + q.y * g.z);
+  }
   // W_ab += w r_a F_b (xx, yy, zz, xy, xz, yz)
   __device__ void vir(float3 r, float3 f, float w) {
     add(1, __fmul_rn(__fmul_rn(w, r.x), f.x));
@@ -119,149 +129,236 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
   __syncthreads();
 }
 
+// bonds: BEAD_TILE beads per work item, BEAD_PER_THREAD per thread with
+// every load issued before the arithmetic
+constexpr int BEAD_PER_THREAD = BEAD_TILE / 256;
+
 __global__ void __launch_bounds__(256) k_bond_forces(Dev d, FF ff) {
   const int4* __restrict__ pos = d.args->pos;
   float4* __restrict__ force = d.args->force;
   const int R = d.R, nitems = d.tb_beads[R];
+  EV acc;
+  int racc = -1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     int r = find_seg(d.tb_beads, R, it);
+    if (r != racc) {
+      if (racc >= 0) flush_ev(d, acc, racc);
+      racc = r;
+    }
     long long beg = d.off[r] + (long long)(it - d.tb_beads[r]) * BEAD_TILE;
     long long end = min(beg + BEAD_TILE, d.off[r + 1]);
     int L = (int)d.box[r];
-    EV acc;
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
-      int4 p = pos[i];
-      uint4 s = d.slots[i];
+    int4 p[BEAD_PER_THREAD];
+    uint4 s[BEAD_PER_THREAD];
+#pragma unroll
+    for (int u = 0; u < BEAD_PER_THREAD; ++u) {
+      long long i = beg + threadIdx.x + u * 256;
+      s[u] = make_uint4(0, 0, 0, 0);
+      if (i < end) {
+        p[u] = pos[i];
+        s[u] = d.slots[i];
+      }
+    }
+    int4 q[BEAD_PER_THREAD][SLOTS];
+#pragma unroll
+    for (int u = 0; u < BEAD_PER_THREAD; ++u)
+#pragma unroll
+      for (int k = 0; k < SLOTS; ++k) {
+        unsigned v = s_get(s[u], k);
+        if (v) q[u][k] = pos[s_partner(v)];
+      }
+    float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < BEAD_PER_THREAD; ++u) {
+      long long i = beg + threadIdx.x + u * 256;
+      if (i >= end) continue;
       float3 f = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < SLOTS; ++q) {
-        unsigned v = s_get(s, q);
+      for (int k = 0; k < SLOTS; ++k) {
+        unsigned v = s_get(s[u], k);
         if (!v) continue;
         int t = s_type(v);
-        float3 rij = relq(p, pos[s_partner(v)], L);
-        float rr = sqrtf(dot3(rij, rij));
-        float dr = rr - ff.bond_r0[t];
-        float fscal = -2.0f * ff.bond_k[t] * dr / rr;
+        float3 rij = relq(p[u], q[u][k], L);
+        float ir = rsqrtf(dot3(rij, rij));
+        float dr = dot3(rij, rij) * ir - ff.bond_r0[t];
+        float fscal = -2.0f * ff.bond_k[t] * dr * ir;
         float3 fq = scale(fscal, rij);
         f = make_float3(f.x + fq.x, f.y + fq.y, f.z + fq.z);
-        acc.add(0, __fmul_rn(__fmul_rn(0.5f * ff.bond_k[t], dr), dr));
-        acc.vir(rij, fq, 0.5f);
+        e += 0.5f * ff.bond_k[t] * dr * dr;
+        w[0] += rij.x * fq.x;
+        w[1] += rij.y * fq.y;
+        w[2] += rij.z * fq.z;
+        w[3] += rij.x * fq.y;
+        w[4] += rij.x * fq.z;
+        w[5] += rij.y * fq.z;
       }
       force[i] = make_float4(f.x, f.y, f.z, 0.f);
     }
-    flush_ev(d, acc, r);
+    acc.add(0, e);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc.add(k + 1, 0.5f * w[k]);
   }
+  if (racc >= 0) flush_ev(d, acc, racc);
 }
 
 __device__ __forceinline__ void add_force(float4* f, int i, float3 v) {
   atomicAdd(f + i, make_float4(v.x, v.y, v.z, 0.f));
 }
 
-__global__ void __launch_bounds__(256) k_angle_forces(Dev d, FF ff) {
+constexpr int ANG_PER_THREAD = FORCE_TILE / 256;
+constexpr int DIH_PER_THREAD = FORCE_TILE / 256;
+
+// Angles and dihedrals in one launch: items [0, tb_fang[R]) are angle tiles,
+// the rest dihedral tiles; both add their forces with float4 atomics.
+__global__ void __launch_bounds__(256) k_angle_dihedral_forces(Dev d, FF ff) {
   const int4* __restrict__ pos = d.args->pos;
   float4* force = d.args->force;
-  const int R = d.R, nitems = d.tb_ang[R];
+  const int R = d.R, na_items = d.tb_fang[R], nitems = na_items + d.tb_fdih[R];
+  const unsigned N = (unsigned)d.N;
+  EV acc;
+  int racc = -1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int r = find_seg(d.tb_ang, R, it);
-    int lt = it - d.tb_ang[r];
-    const int4* recs = d.ang + 6 * d.off[r];
-    int beg = lt * FORCE_TILE, end = min(beg + FORCE_TILE, d.n_ang[r]);
-    int L = (int)d.box[r];
-    EV acc;
-    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
-      int4 a = recs[k];
-      if ((unsigned)a.x >= (unsigned)d.N || (unsigned)a.y >= (unsigned)d.N || (unsigned)a.z >= (unsigned)d.N) {
-        atomicOr(d.err, ERR_INTERNAL);
-        continue;
-      }
-      int4 pb = pos[a.y];
-      float3 ra = relq(pos[a.x], pb, L), rc = relq(pos[a.z], pb, L);
-      float K = ff.angle_k[a.w];
-      float la2 = dot3(ra, ra), lc2 = dot3(rc, rc);
-      float inv = rsqrtf(la2 * lc2);
-      float cs = dot3(ra, rc) * inv;
-      // F_A = -K d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
-      float3 Fa = scale(-K, axpy(-cs / la2, ra, scale(inv, rc)));
-      float3 Fc = scale(-K, axpy(-cs / lc2, rc, scale(inv, ra)));
-      float3 Fb = make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z);
-      add_force(force, a.x, Fa);
-      add_force(force, a.y, Fb);
-      add_force(force, a.z, Fc);
-      acc.add(0, __fmul_rn(K, 1.0f + cs));
-      acc.vir(ra, Fa, 1.f);
-      acc.vir(rc, Fc, 1.f);
+    const bool dih = it >= na_items;
+    const int* tb = dih ? d.tb_fdih : d.tb_fang;
+    int t0 = dih ? it - na_items : it;
+    int r = find_seg(tb, R, t0);
+    if (r != racc) {
+      if (racc >= 0) flush_ev(d, acc, racc);
+      racc = r;
     }
-    flush_ev(d, acc, r);
+    int lt = t0 - tb[r];
+    int L = (int)d.box[r];
+    float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (!dih) {
+      const int4* recs = d.ang + 6 * d.off[r];
+      int beg = lt * FORCE_TILE, end = min(beg + FORCE_TILE, d.n_ang[r]);
+      int4 a[ANG_PER_THREAD], pa[ANG_PER_THREAD], pb[ANG_PER_THREAD], pc[ANG_PER_THREAD];
+      bool ok[ANG_PER_THREAD];
+#pragma unroll
+      for (int u = 0; u < ANG_PER_THREAD; ++u) {
+        int k = beg + threadIdx.x + u * 256;
+        ok[u] = k < end;
+        if (ok[u]) a[u] = recs[k];
+        ok[u] = ok[u] && (unsigned)a[u].x < N && (unsigned)a[u].y < N && (unsigned)a[u].z < N;
+        if (k < end && !ok[u]) atomicOr(d.err, ERR_INTERNAL);
+      }
+#pragma unroll
+      for (int u = 0; u < ANG_PER_THREAD; ++u)
+        if (ok[u]) {
+          pa[u] = pos[a[u].x];
+          pb[u] = pos[a[u].y];
+          pc[u] = pos[a[u].z];
+        }
+#pragma unroll
+      for (int u = 0; u < ANG_PER_THREAD; ++u) {
+        if (!ok[u]) continue;
+        float3 ra = relq(pa[u], pb[u], L), rc = relq(pc[u], pb[u], L);
+        float K = ff.angle_k[a[u].w];
+        float ia = rsqrtf(dot3(ra, ra)), ic = rsqrtf(dot3(rc, rc));
+        float inv = ia * ic;
+        float cs = dot3(ra, rc) * inv;
+        // F_A = -K d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
+        float3 Fa = scale(-K, axpy(-cs * ia * ia, ra, scale(inv, rc)));
+        float3 Fc = scale(-K, axpy(-cs * ic * ic, rc, scale(inv, ra)));
+        float3 Fb = make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z);
+        add_force(force, a[u].x, Fa);
+        add_force(force, a[u].y, Fb);
+        add_force(force, a[u].z, Fc);
+        e += K * (1.0f + cs);
+        w[0] += ra.x * Fa.x + rc.x * Fc.x;
+        w[1] += ra.y * Fa.y + rc.y * Fc.y;
+        w[2] += ra.z * Fa.z + rc.z * Fc.z;
+        w[3] += ra.x * Fa.y + rc.x * Fc.y;
+        w[4] += ra.x * Fa.z + rc.x * Fc.z;
+        w[5] += ra.y * Fa.z + rc.y * Fc.z;
+      }
+    } else {
+      const int4* recs = d.dih + 18 * d.off[r];
+      int beg = lt * FORCE_TILE, end = min(beg + FORCE_TILE, d.n_dih[r]);
+      int4 rec[DIH_PER_THREAD], P[DIH_PER_THREAD][4];
+      bool ok[DIH_PER_THREAD];
+#pragma unroll
+      for (int u = 0; u < DIH_PER_THREAD; ++u) {
+        int k = beg + threadIdx.x + u * 256;
+        ok[u] = k < end;
+        if (ok[u]) rec[u] = recs[k];
+        unsigned id = (unsigned)(rec[u].w & 0x0FFFFFFF);
+        ok[u] = ok[u] && (unsigned)rec[u].x < N && (unsigned)rec[u].y < N && (unsigned)rec[u].z < N && id < N;
+        if (k < end && !ok[u]) atomicOr(d.err, ERR_INTERNAL);
+      }
+#pragma unroll
+      for (int u = 0; u < DIH_PER_THREAD; ++u)
+        if (ok[u]) {
+          P[u][0] = pos[rec[u].x];
+          P[u][1] = pos[rec[u].y];
+          P[u][2] = pos[rec[u].z];
+          P[u][3] = pos[rec[u].w & 0x0FFFFFFF];
+        }
+#pragma unroll
+      for (int u = 0; u < DIH_PER_THREAD; ++u) {
+        if (!ok[u]) continue;
+        int ia = rec[u].x, ib = rec[u].y, ic = rec[u].z, id = rec[u].w & 0x0FFFFFFF;
+        int t = (int)((unsigned)rec[u].w >> 28);
+        // Blondel-Karplus: F = r_A - r_B, G = r_B - r_C, H = r_D - r_C,
+        // A = F x G, B = H x G; cos phi = A.B / (|A||B|), phi = 180 deg trans.
+        // The cross, dot and triple products are formed exactly from the
+        // integer displacements and rounded once, so near-collinear quartets
+        // keep FP32 accuracy; the rest is FP32.
+        int3 Fi = reli(P[u][0], P[u][1], L), Gi = reli(P[u][1], P[u][2], L), Hi = reli(P[u][3], P[u][2], L);
+        L3 Ai = crossi(Fi, Gi), Bi = crossi(Hi, Gi);
+        const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
+        float3 F = tof(Fi, s20), G = tof(Gi, s20), H = tof(Hi, s20);
+        float3 A = tof(Ai, s40), B = tof(Bi, s40);
+        float A2 = dot3(A, A), B2 = dot3(B, B);
+        float gg = (float)doti(Gi, Gi) * s40;
+        float irg = rsqrtf(gg), rg = gg * irg;
+        float rab = rsqrtf(A2 * B2);
+        float cs = dot3(A, B) * rab;
+        // (B x A).G = -|G|^2 F.B, so sin phi = -|G| (F.B) / (|A||B|)
+        float sn = -rg * triplei(Fi, Bi, -60) * rab;
+        float K = ff.dih_k[t], dd = ff.dih_d[t];
+        // E = K (1 + d cos phi): -dE/dphi = K d sin phi
+        float mdE = K * dd * sn;
+        float fg = (float)doti(Fi, Gi) * s40, hg = (float)doti(Hi, Gi) * s40;
+        float ia2 = __frcp_rn(A2), ib2 = __frcp_rn(B2);
+        // dphi/dr_A = -|G|/A^2 A ; dphi/dr_D = |G|/B^2 B
+        // dphi/dr_B = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B
+        // dphi/dr_C = -F.G/(A^2|G|) A + (H.G/(B^2|G|) - |G|/B^2) B
+        float3 dA = scale(-rg * ia2, A);
+        float3 dD = scale(rg * ib2, B);
+        float3 dB = axpy(-hg * ib2 * irg, B, scale(rg * ia2 + fg * ia2 * irg, A));
+        float3 dC = axpy(hg * ib2 * irg - rg * ib2, B, scale(-fg * ia2 * irg, A));
+        float3 Fa = scale(mdE, dA), Fb = scale(mdE, dB), Fc = scale(mdE, dC), Fd = scale(mdE, dD);
+        add_force(force, ia, Fa);
+        add_force(force, ib, Fb);
+        add_force(force, ic, Fc);
+        add_force(force, id, Fd);
+        e += K * (1.0f + dd * cs);
+        // virial relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
+        float3 mg = make_float3(-G.x, -G.y, -G.z), hm = make_float3(H.x - G.x, H.y - G.y, H.z - G.z);
+        w[0] += F.x * Fa.x + mg.x * Fc.x + hm.x * Fd.x;
+        w[1] += F.y * Fa.y + mg.y * Fc.y + hm.y * Fd.y;
+        w[2] += F.z * Fa.z + mg.z * Fc.z + hm.z * Fd.z;
+        w[3] += F.x * Fa.y + mg.x * Fc.y + hm.x * Fd.y;
+        w[4] += F.x * Fa.z + mg.x * Fc.z + hm.x * Fd.z;
+        w[5] += F.y * Fa.z + mg.y * Fc.z + hm.y * Fd.z;
+      }
+    }
+    acc.add(0, e);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc.add(k + 1, w[k]);
   }
+  if (racc >= 0) flush_ev(d, acc, racc);
 }
 
-__global__ void __launch_bounds__(256) k_dihedral_forces(Dev d, FF ff) {
-  const int4* __restrict__ pos = d.args->pos;
-  float4* force = d.args->force;
-  const int R = d.R, nitems = d.tb_dih[R];
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int r = find_seg(d.tb_dih, R, it);
-    int lt = it - d.tb_dih[r];
-    const int4* recs = d.dih + 18 * d.off[r];
-    int beg = lt * FORCE_TILE, end = min(beg + FORCE_TILE, d.n_dih[r]);
-    int L = (int)d.box[r];
-    EV acc;
-    for (int k = beg + threadIdx.x; k < end; k += blockDim.x) {
-      int4 rec = recs[k];
-      int ia = rec.x, ib = rec.y, ic = rec.z, id = rec.w & 0x0FFFFFFF;
-      int t = (int)((unsigned)rec.w >> 28);
-      if ((unsigned)ia >= (unsigned)d.N || (unsigned)ib >= (unsigned)d.N || (unsigned)ic >= (unsigned)d.N ||
-          (unsigned)id >= (unsigned)d.N) {
-        atomicOr(d.err, ERR_INTERNAL);
-        continue;
-      }
-      int4 pb = pos[ib], pc = pos[ic];
-      // Blondel-Karplus: F = r_A - r_B, G = r_B - r_C, H = r_D - r_C,
-      // A = F x G, B = H x G; cos phi = A.B / (|A||B|), phi = 180 deg trans.
-      // The cross, dot and triple products are formed exactly from the integer
-      // displacements and rounded once, so near-collinear quartets keep FP32
-      // accuracy; the rest is FP32.
-      int3 Fi = reli(pos[ia], pb, L), Gi = reli(pb, pc, L), Hi = reli(pos[id], pc, L);
-      L3 Ai = crossi(Fi, Gi), Bi = crossi(Hi, Gi);
-      const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
-      float3 F = tof(Fi, s20), G = tof(Gi, s20), H = tof(Hi, s20);
-      float3 A = tof(Ai, s40), B = tof(Bi, s40);
-      float A2 = dot3(A, A), B2 = dot3(B, B);
-      float rg = sqrtf((float)doti(Gi, Gi) * s40);
-      float rab = rsqrtf(A2 * B2);
-      float cs = dot3(A, B) * rab;
-      // (B x A).G = -|G|^2 F.B, so sin phi = -|G| (F.B) / (|A||B|)
-      float sn = -rg * triplei(Fi, Bi, -60) * rab;
-      float K = ff.dih_k[t], dd = ff.dih_d[t];
-      // E = K (1 + d cos phi): -dE/dphi = K d sin phi
-      float mdE = K * dd * sn;
-      float fg = (float)doti(Fi, Gi) * s40, hg = (float)doti(Hi, Gi) * s40;
-      float ia2 = 1.0f / A2, ib2 = 1.0f / B2;
-      // dphi/dr_A = -|G|/A^2 A ; dphi/dr_D = |G|/B^2 B
-      // dphi/dr_B = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B
-      // dphi/dr_C = -F.G/(A^2|G|) A + (H.G/(B^2|G|) - |G|/B^2) B
-      float3 dA = scale(-rg * ia2, A);
-      float3 dD = scale(rg * ib2, B);
-      float3 dB = axpy(-hg * ib2 / rg, B, scale(rg * ia2 + fg * ia2 / rg, A));
-      float3 dC = axpy(hg * ib2 / rg - rg * ib2, B, scale(-fg * ia2 / rg, A));
-      float3 Fa = scale(mdE, dA), Fb = scale(mdE, dB), Fc = scale(mdE, dC), Fd = scale(mdE, dD);
-      add_force(force, ia, Fa);
-      add_force(force, ib, Fb);
-      add_force(force, ic, Fc);
-      add_force(force, id, Fd);
-      acc.add(0, __fmul_rn(K, 1.0f + dd * cs));
-      // virial relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
-      acc.vir(F, Fa, 1.f);
-      acc.vir(make_float3(-G.x, -G.y, -G.z), Fc, 1.f);
-      acc.vir(make_float3(H.x - G.x, H.y - G.y, H.z - G.z), Fd, 1.f);
-    }
-    flush_ev(d, acc, r);
-  }
-}
-
+// copy the reduced energy / virial out and clear the accumulators for the
+// next force call
 __global__ void k_ev_out(Dev d) {
   double* out = d.args->ev;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 7 * d.R; k += gridDim.x * blockDim.x) out[k] = d.ev_acc[k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 7 * d.R; k += gridDim.x * blockDim.x) {
+    out[k] = d.ev_acc[k];
+    d.ev_acc[k] = 0.0;
+  }
 }
 
 }  // namespace dynbond

@@ -6,10 +6,10 @@
 
 namespace dynbond {
 
-constexpr int PURGE_TILE = 2048;   // 256 threads x 8 records
+constexpr int PURGE_TILE = 4096;   // 512 threads x 8 records
 constexpr int REBUILD_TILE = 256;  // new bonds per tile, one per thread
-constexpr int FORCE_TILE = 1024;   // records per force work item
-constexpr int BEAD_TILE = 1024;    // beads per force work item
+constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
+constexpr int BEAD_TILE = 512;     // beads per force work item (2 per thread)
 
 // bonded force-field tables in FP32 (kernel parameter space)
 struct FF {
@@ -25,15 +25,15 @@ __global__ void k_match(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_edit(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_newbonds(Dev d, int mode);
 __global__ void k_tiles(Dev d, int mode);
-__global__ void k_purge(Dev d, int which);
+__global__ void k_purge(Dev d);
 __global__ void k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new);
 __global__ void k_finalize(Dev d);
+__global__ void k_setup(Dev d);
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
                            int set_pos, int set_force);
 
 __global__ void k_bond_forces(Dev d, FF ff);
-__global__ void k_angle_forces(Dev d, FF ff);
-__global__ void k_dihedral_forces(Dev d, FF ff);
+__global__ void k_angle_dihedral_forces(Dev d, FF ff);
 __global__ void k_ev_out(Dev d);
 
 }  // namespace dynbond

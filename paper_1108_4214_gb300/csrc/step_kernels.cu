@@ -22,9 +22,10 @@
 
 namespace dynbond {
 
-constexpr int PURGE_PER_THREAD = 8;
-constexpr int SCAN_PER_THREAD = 8;
-constexpr int NB_PER_THREAD = 4;
+constexpr int PURGE_PER_THREAD = 8;  // records per thread; PURGE_TILE / 8 threads per block
+constexpr int SCAN_PER_THREAD = 32;  // cells per thread in the histogram scan
+constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
+constexpr int NB_WORDS = 2;  // bitmap words (64 beads) per thread in the new-bond list
 
 __device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
   if (v) atomicAdd((unsigned long long*)&d.stats[(long long)r * NSTAT + k], (unsigned long long)v);
@@ -89,9 +90,9 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
             if (s_type_to(d.slots[j], (int)i) != bty) continue;
             long long dd = dist2(p, pos[j], L);
             int rule = -1;
-            for (int k = 0; k < rt.n; ++k) {
+            for (int q2 = rt.bk_start[bty], q3 = rt.bk_start[bty + 1]; q2 < q3; ++q2) {
+              int k = rt.bk_list[q2];
               int kd = rt.kind[k];
-              if (rt.type[k] != bty) continue;
               if (kd == DYNBOND_KILLBOND && dd > rt.r2[k]) km |= 1u << q;
               if ((kd == DYNBOND_BREAKBOND && dd > rt.r2[k]) || kd == DYNBOND_CONVERTBOND) rule = k;
             }
@@ -148,12 +149,24 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
     if (t >= ntiles) break;
     long long beg = t * per_tile + (long long)threadIdx.x * SCAN_PER_THREAD;
     int v[SCAN_PER_THREAD];
+    const bool full = beg + SCAN_PER_THREAD <= n;
+    if (full) {
+      const int4* src = reinterpret_cast<const int4*>(d.cell_start + beg);
+#pragma unroll
+      for (int k = 0; k < SCAN_PER_THREAD / 4; ++k) {
+        int4 x = src[k];
+        v[4 * k] = x.x;
+        v[4 * k + 1] = x.y;
+        v[4 * k + 2] = x.z;
+        v[4 * k + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < SCAN_PER_THREAD; ++k) v[k] = beg + k < n ? d.cell_start[beg + k] : 0;
+    }
     long long sum = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-      v[k] = beg + k < n ? d.cell_start[beg + k] : 0;
-      sum += v[k];
-    }
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) sum += v[k];
     long long tot;
     long long ex = block_excl_scan(sum, sh, &tot);
     if (threadIdx.x < 32) {
@@ -163,10 +176,27 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
     __syncthreads();
     if (s_excl < 0) return;
     long long pre = s_excl + ex;
+    if (full) {
+      int4* dst = reinterpret_cast<int4*>(d.cell_start + beg);
 #pragma unroll
-    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-      if (beg + k < n) d.cell_start[beg + k] = (int)pre;
-      pre += v[k];
+      for (int k = 0; k < SCAN_PER_THREAD / 4; ++k) {
+        int4 x;
+        x.x = (int)pre;
+        pre += v[4 * k];
+        x.y = (int)pre;
+        pre += v[4 * k + 1];
+        x.z = (int)pre;
+        pre += v[4 * k + 2];
+        x.w = (int)pre;
+        pre += v[4 * k + 3];
+        dst[k] = x;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        if (beg + k < n) d.cell_start[beg + k] = (int)pre;
+        pre += v[k];
+      }
     }
     if (t == ntiles - 1 && threadIdx.x == blockDim.x - 1) {
       d.cell_start[n] = (int)pre;
@@ -309,13 +339,33 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   long long pd[MAXC];
   int np = 0;
   bool more = false;
-  for (int a = 0; a < noff; ++a)
-    for (int b = 0; b < noff; ++b) {
+  // all column ranges first (independent loads in flight together)
+  int rq0[9], rq1[9];
+#pragma unroll
+  for (int ab = 0; ab < 9; ++ab) {
+    int a = ab / 3, b = ab % 3;
+    rq0[ab] = rq1[ab] = 0;
+    if (a < noff && b < noff) {
       long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
-      for (int run = 0; run < 2; ++run) {
-        int lo = run ? w0 : z0, hi = run ? w1 : z1;
-        if (hi < lo) continue;
-        int q0 = d.cell_start[row + lo], q1 = d.cell_start[row + hi + 1];
+      rq0[ab] = d.cell_start[row + z0];
+      rq1[ab] = d.cell_start[row + z1 + 1];
+    }
+  }
+  for (int ab = 0; ab < 9; ++ab) {
+    int a = ab / 3, b = ab % 3;
+    if (a >= noff || b >= noff) continue;
+    long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
+    for (int run = 0; run < 2; ++run) {
+      int q0, q1;
+      if (run == 0) {
+        q0 = rq0[ab];
+        q1 = rq1[ab];
+      } else {
+        if (w1 < w0) continue;
+        q0 = d.cell_start[row + w0];
+        q1 = d.cell_start[row + w1 + 1];
+      }
+      {
         for (int q = q0; q < q1; ++q) {
           int4 o = d.sorted[q];
           if (!((tmask >> (o.w & 15)) & 1u)) continue;
@@ -331,6 +381,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
         }
       }
     }
+  }
   if (more && mode == 0) {
     ll->overflow = true;  // finished exactly by k_cand_overflow
     return;
@@ -469,7 +520,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
 // or max_rounds rounds.  Per-bead lists are sorted, so a bead's nominee is
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_match(Dev d, const RuleTab* __restrict__ rtp) {
+__global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
   const RuleTab& rt = *rtp;
   const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b;
   const long long N = d.N;
@@ -480,12 +531,16 @@ __global__ void __launch_bounds__(256) k_match(Dev d, const RuleTab* __restrict_
   // list of beads that were still unmatched and nominated someone
   int n = na_c + na_b;
   int round = 0;
+  // once few beads remain, block 0 finishes the rounds alone with block
+  // barriers instead of grid barriers
+  bool solo = false;
+  int gg = g, st = stride;
   while (true) {
     const int* src = round ? d.live[(round - 1) & 1] : nullptr;
     int* dst = d.live[round & 1];
     // nomination: first list entry whose partner is still unmatched (round 0
     // was written by the list producers)
-    for (int idx = round ? g : n; idx < n; idx += stride) {
+    for (int idx = round ? gg : n; idx < n; idx += st) {
       int sys, i;
       if (src) {
         int e = src[idx];
@@ -511,9 +566,12 @@ __global__ void __launch_bounds__(256) k_match(Dev d, const RuleTab* __restrict_
       d.ptr[o + i] = p;
       d.nom[o + i] = j;
     }
-    if (round && !grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    if (round) {
+      if (solo) __syncthreads();
+      else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    }
     // mutual nominations are matched; unmatched nominators carry over
-    for (int base = g - lane; base < n; base += stride) {
+    for (int base = gg - lane; base < n; base += st) {
       int idx = base + lane;
       int sys = 0, r = 0, i = -1;
       bool hit = false, keep = false;
@@ -546,7 +604,8 @@ __global__ void __launch_bounds__(256) k_match(Dev d, const RuleTab* __restrict_
       int at = warp_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
       if (keep) dst[at] = (int)((unsigned)sys << 31 | (unsigned)i);
     }
-    if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    if (solo) __syncthreads();
+    else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
     int matched = ld_cg(&d.cnt->round_matched[round]);
     if (blockIdx.x == 0) {
       for (int k = threadIdx.x; k < 2 * d.R; k += blockDim.x) {
@@ -564,6 +623,12 @@ __global__ void __launch_bounds__(256) k_match(Dev d, const RuleTab* __restrict_
     if (round >= MAX_ROUNDS) {
       if (g == 0) atomicOr(d.err, ERR_ROUNDS);
       break;
+    }
+    if (!solo && n <= SOLO_LIVE) {
+      if (blockIdx.x != 0) return;
+      solo = true;
+      gg = threadIdx.x;
+      st = blockDim.x;
     }
   }
   if (g == 0) d.cnt->rounds_done = round;
@@ -697,41 +762,58 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__
 // k_newbonds: ordered list of new bonds (u < v).  mode 0: bonds formed or
 // retyped in this call; mode 1: every bond (initial typing of the system).
 // ---------------------------------------------------------------------------
+// Owned new bonds of bead u: partners above u (mode 0: formed / retyped in
+// this call; mode 1: every bond).
+__device__ __forceinline__ int owned_new(const Dev& d, long long u, int mode, int* out) {
+  int n = 0;
+  if (mode == 0) {
+    int2 np = d.newp[u];
+    if (np.x > u) out[n++] = np.x;
+    if (np.y > u) out[n++] = np.y;
+  } else {
+    uint4 s = d.slots[u];
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      int v = s_partner(s_get(s, q));
+      if (v > u) out[n++] = v;
+    }
+  }
+  return n;
+}
+
 __global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
   __shared__ long long sh[33];
   __shared__ long long s_excl, s_tile;
   const long long N = d.N;
-  const long long per_tile = (long long)blockDim.x * NB_PER_THREAD;
-  const long long ntiles = (N + per_tile - 1) / per_tile;
+  const long long W = (N + 31) / 32;
+  const long long words_per_tile = (long long)blockDim.x * NB_WORDS;
+  const long long ntiles = (W + words_per_tile - 1) / words_per_tile;
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[1], 1);
     __syncthreads();
     long long t = s_tile;
     if (t >= ntiles) break;
-    long long beg = t * per_tile + (long long)threadIdx.x * NB_PER_THREAD;
-    int partners[NB_PER_THREAD][SLOTS];
+    long long w0 = t * words_per_tile + (long long)threadIdx.x * NB_WORDS;
+    unsigned bits[NB_WORDS];
     long long cnt = 0;
 #pragma unroll
-    for (int k = 0; k < NB_PER_THREAD; ++k) {
-      long long u = beg + k;
-#pragma unroll
-      for (int q = 0; q < SLOTS; ++q) partners[k][q] = -1;
-      if (u >= N) continue;
+    for (int k = 0; k < NB_WORDS; ++k) {
+      long long w = w0 + k;
+      bits[k] = 0;
+      if (w >= W) continue;
       if (mode == 0) {
-        if (!((d.bm_new[u >> 5] >> (u & 31)) & 1u)) continue;
-        int2 np = d.newp[u];
-        if (np.x > u) partners[k][0] = np.x;
-        if (np.y > u) partners[k][1] = np.y;
+        bits[k] = d.bm_new[w];
       } else {
-        uint4 s = d.slots[u];
-#pragma unroll
-        for (int q = 0; q < SLOTS; ++q) {
-          int v = s_partner(s_get(s, q));
-          if (v > u) partners[k][q] = v;
-        }
+        long long hi = min(32ll, N - 32 * w);
+        bits[k] = hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
       }
-#pragma unroll
-      for (int q = 0; q < SLOTS; ++q) cnt += partners[k][q] >= 0;
+      unsigned b = bits[k];
+      while (b) {
+        int l = __ffs(b) - 1;
+        b &= b - 1;
+        int tmp[SLOTS];
+        cnt += owned_new(d, 32 * w + l, mode, tmp);
+      }
     }
     long long tot;
     long long ex = block_excl_scan(cnt, sh, &tot);
@@ -742,23 +824,23 @@ __global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
     __syncthreads();
     if (s_excl < 0) return;
     long long at = s_excl + ex;
-    int r0 = beg < N ? d.rep[beg] : 0;
+    int r0 = w0 < W ? d.rep[32 * w0] : 0;
     unsigned n0 = 0;
 #pragma unroll
-    for (int k = 0; k < NB_PER_THREAD; ++k) {
-      long long u = beg + k;
-      if (u >= N) continue;
-      int nr = 0, r = -1;
-#pragma unroll
-      for (int q = 0; q < SLOTS; ++q) {
-        int v = partners[k][q];
-        if (v < 0) continue;
-        if (r < 0) r = d.rep[u];
-        d.nbl[at++] = make_int4((int)u, v, r, 0);
-        ++nr;
+    for (int k = 0; k < NB_WORDS; ++k) {
+      unsigned b = bits[k];
+      while (b) {
+        int l = __ffs(b) - 1;
+        b &= b - 1;
+        long long u = 32 * (w0 + k) + l;
+        int tmp[SLOTS];
+        int nr = owned_new(d, u, mode, tmp);
+        if (!nr) continue;
+        int r = d.rep[u];
+        for (int q = 0; q < nr; ++q) d.nbl[at++] = make_int4((int)u, tmp[q], r, 0);
+        if (r == r0) n0 += nr;
+        else atomicAdd(&d.nbl_count[r], nr);
       }
-      if (nr && r == r0) n0 += nr;
-      else if (nr) atomicAdd(&d.nbl_count[r], nr);
     }
     count_add_warp(d.nbl_count, r0, n0);
     if (t == ntiles - 1 && threadIdx.x == blockDim.x - 1) d.cnt->n_nbl = (int)at;
@@ -808,10 +890,6 @@ __global__ void k_tiles(Dev d, int mode) {
     block_tile_bases(d.n_dih, d.R, PURGE_TILE, d.tb_dih, nullptr);
   } else if (mode == 1) {
     block_tile_bases(d.nbl_count, d.R, REBUILD_TILE, d.tb_nb, d.nbl_first);
-  } else {
-    block_tile_bases(d.n_ang, d.R, FORCE_TILE, d.tb_ang, nullptr);
-    __syncthreads();
-    block_tile_bases(d.n_dih, d.R, FORCE_TILE, d.tb_dih, nullptr);
   }
 }
 
@@ -827,31 +905,33 @@ __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
   return rp.x == b || rp.y == b || rp.z == b || rp.w == b;
 }
 
-__global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
+__global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) {
   __shared__ long long s_excl, s_tile;
   __shared__ int s_tot;
-  const bool dih = which != 0;
-  int4* recs = dih ? d.dih : d.ang;
-  const int* count = dih ? d.n_dih : d.n_ang;
-  int* kept = dih ? d.kept_dih : d.kept_ang;
-  const int* tb = dih ? d.tb_dih : d.tb_ang;
-  unsigned long long* status = dih ? d.st_pd : d.st_pa;
-  const int per_rep = dih ? 18 : 6;
+  __shared__ int s_cnt[PURGE_PER_THREAD][32];
+  __shared__ int s_off[PURGE_PER_THREAD][32];
   const int R = d.R;
-  const int ntiles = tb[R];
+  const int na_tiles = d.tb_ang[R];
+  const int ntiles = na_tiles + d.tb_dih[R];
+  const int nw = blockDim.x >> 5;
   while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[2 + which], 1);
+    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[2], 1);
     __syncthreads();
-    int t = (int)s_tile;
-    if (t >= ntiles) break;
+    int tg = (int)s_tile;
+    if (tg >= ntiles) break;
+    // tiles [0, na_tiles) compact the angle lists, the rest the dihedral lists
+    const bool dih = tg >= na_tiles;
+    const int t = dih ? tg - na_tiles : tg;
+    int4* recs = dih ? d.dih : d.ang;
+    const int* tb = dih ? d.tb_dih : d.tb_ang;
+    unsigned long long* status = dih ? d.st_pd : d.st_pa;
     int r = find_seg(tb, R, t);
     int lt = t - tb[r];
-    long long base = per_rep * d.off[r];
-    int n = count[r];
+    long long base = (dih ? 18 : 6) * d.off[r];
+    int n = (dih ? d.n_dih : d.n_ang)[r];
     int beg = lt * PURGE_TILE + threadIdx.x;
     int4 v[PURGE_PER_THREAD];
     unsigned keep = 0;
-    int nkeep = 0;
 #pragma unroll
     for (int k = 0; k < PURGE_PER_THREAD; ++k) {
       int idx = beg + k * (int)blockDim.x;
@@ -864,16 +944,11 @@ __global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
         int dd = v[k].w & 0x0FFFFFFF;
         gone = bond_gone(d, v[k].x, v[k].y) || bond_gone(d, v[k].y, v[k].z) || bond_gone(d, v[k].z, dd);
       }
-      if (!gone) {
-        keep |= 1u << k;
-        ++nkeep;
-      }
+      if (!gone) keep |= 1u << k;
     }
     // ordered compaction: records are numbered k-major within the tile
     // (index = k * blockDim + thread), so scan over that order
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int s_cnt[PURGE_PER_THREAD][8];
-    __shared__ int s_off[PURGE_PER_THREAD][8];
     unsigned bal[PURGE_PER_THREAD];
 #pragma unroll
     for (int k = 0; k < PURGE_PER_THREAD; ++k) {
@@ -881,30 +956,27 @@ __global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
       if (lane == 0) s_cnt[k][wid] = __popc(bal[k]);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int acc = 0;
-      for (int k = 0; k < PURGE_PER_THREAD; ++k)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-          s_off[k][w] = acc;
-          acc += s_cnt[k][w];
-        }
-      s_tot = acc;
-    }
-    __syncthreads();
     if (threadIdx.x < 32) {
-      long long x = lookback(status, t, tb[r], (unsigned long long)s_tot, d.spin_limit, d.err);
-      if (threadIdx.x == 0) {
+      // warp 0: exclusive offsets over (k, warp) order, then the look-back
+      int acc = 0;
+      for (int k = 0; k < PURGE_PER_THREAD; ++k) {
+        int c = lane < nw ? s_cnt[k][lane] : 0;
+        int inc = warp_incl_scan(c);
+        if (lane < nw) s_off[k][lane] = acc + inc - c;
+        acc += __shfl_sync(FULL, inc, 31);
+      }
+      long long x = lookback(status, t, tb[r], (unsigned long long)acc, d.spin_limit, d.err);
+      if (lane == 0) {
+        s_tot = acc;
         s_excl = x;
-        if (x >= 0 && lt == tb[r + 1] - tb[r] - 1) kept[r] = (int)(x + s_tot);
+        if (x >= 0 && lt == tb[r + 1] - tb[r] - 1) (dih ? d.kept_dih : d.kept_ang)[r] = (int)(x + acc);
       }
     }
     __syncthreads();
     if (s_excl < 0) return;
     long long excl = s_excl;
     // nothing moves when no record before or inside this tile was dropped
-    bool full = excl == (long long)lt * PURGE_TILE && s_off[PURGE_PER_THREAD - 1][(blockDim.x >> 5) - 1] +
-                                                              s_cnt[PURGE_PER_THREAD - 1][(blockDim.x >> 5) - 1] ==
-                                                          min(PURGE_TILE, n - lt * PURGE_TILE);
+    bool full = excl == (long long)lt * PURGE_TILE && s_tot == min(PURGE_TILE, n - lt * PURGE_TILE);
     if (!full) {
 #pragma unroll
       for (int k = 0; k < PURGE_PER_THREAD; ++k) {
@@ -913,7 +985,6 @@ __global__ void __launch_bounds__(256) k_purge(Dev d, int which) {
         recs[base + excl + rank] = v[k];
       }
     }
-    (void)nkeep;
     __syncthreads();
   }
 }
@@ -1076,9 +1147,29 @@ __global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, const RuleTab* 
   }
 }
 
-// per-replica list counts and statistics after the call (one thread per replica)
-__global__ void k_finalize(Dev d) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < d.R; r += gridDim.x * blockDim.x) {
+// Per-call setup (one launch): zero the counters, the cell histogram, the
+// creation-active bitmap, the per-replica scratch and the look-back status
+// words; block 0 also computes the purge tile bases from the list counts.
+__global__ void __launch_bounds__(1024) k_setup(Dev d) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int* cnt = reinterpret_cast<int*>(d.cnt);
+  for (long long k = g; k < (long long)(sizeof(Counters) / sizeof(int)); k += stride) cnt[k] = 0;
+  for (long long k = g; k <= d.n_cells; k += stride) d.cell_start[k] = 0;
+  for (long long k = g; k < d.W; k += stride) d.bm_ca[k] = 0;
+  for (long long k = g; k < d.small_words; k += stride) d.small[k] = 0;
+  for (long long k = g; k < d.status_words; k += stride) d.status_all[k] = 0ull;
+  if (blockIdx.x == 0) {
+    block_tile_bases(d.n_ang, d.R, PURGE_TILE, d.tb_ang, nullptr);
+    __syncthreads();
+    block_tile_bases(d.n_dih, d.R, PURGE_TILE, d.tb_dih, nullptr);
+  }
+}
+
+// Per-replica list counts and statistics after the call, then the force tile
+// bases of the final lists (one block).
+__global__ void __launch_bounds__(1024) k_finalize(Dev d) {
+  for (int r = threadIdx.x; r < d.R; r += blockDim.x) {
     long long* st = d.stats + (long long)r * NSTAT;
     int na = d.kept_ang[r] + d.added_ang[r], nd = d.kept_dih[r] + d.added_dih[r];
     st[ST_ANG_REMOVED] = d.n_ang[r] - d.kept_ang[r];
@@ -1091,6 +1182,10 @@ __global__ void k_finalize(Dev d) {
     st[ST_NANGLES] = na;
     st[ST_NDIHEDRALS] = nd;
   }
+  __syncthreads();
+  block_tile_bases(d.n_ang, d.R, FORCE_TILE, d.tb_fang, nullptr);
+  __syncthreads();
+  block_tile_bases(d.n_dih, d.R, FORCE_TILE, d.tb_fdih, nullptr);
 }
 
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
