@@ -56,7 +56,8 @@ enum {
   DYNBOND_MAX_CANDIDATES = 24,/* creation candidates one bead keeps in registers; beads with more
                                  take an exact two-pass path (no limit) */
   DYNBOND_MAX_ROUNDS = 4096,  /* matching rounds of one call */
-  DYNBOND_EV = 7              /* energy + 6 virial components per replica */
+  DYNBOND_EV = 7,             /* energy + 6 virial components per replica */
+  DYNBOND_NOALLOC_MAX_REPLICAS = 4096 /* replicas of one dynbond_forces_noalloc call */
 };
 
 /* Rule kinds: the rule set of the fix (Fig. 1). */
@@ -273,6 +274,39 @@ dynbond_status dynbond_sync(dynbond_ctx* ctx);
  * their static names, and returns the number of phases in *n_out.
  */
 dynbond_status dynbond_phase_times(dynbond_ctx* ctx, float* ms, const char** names, int32_t n, int32_t* n_out);
+
+/*
+ * Bonded forces without any device allocation, for callers that must not
+ * call cudaMalloc: for example a host engine that has handed the GPU's memory
+ * to its own pool allocator before loading this library, or a latency-critical
+ * loop that cannot accept cudaMalloc's implicit device synchronization.  The
+ * paper has no counterpart; this is a service of the library.
+ *
+ * It evaluates the forces of dynbond_forces for a topology the caller passes
+ * in (no context needed).  Every array is caller-owned device memory:
+ *   d_pos        int4[n_beads] positions (as for dynbond_step);
+ *   d_slots      uint32[n_beads*4] bond slots: (partner << 4 | type this bead
+ *                stores), 0 = empty slot;
+ *   d_bead_offset int64[n_replicas+1], d_box_q int64[n_replicas];
+ *   d_angles     int32[n_angles*4] (a, b, c, type), replica = that of b;
+ *   d_dihedrals  int32[n_dihedrals*5] (a, b, c, d, type), replica = that of b;
+ *   d_force      float4[n_beads] output (overwritten, w = 0);
+ *   d_ev         double[n_replicas*7] output (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).
+ * Its scratch (the FP64 accumulators of up to DYNBOND_NOALLOC_MAX_REPLICAS
+ * replicas, 229 KB) is a fixed array in device memory that every GPU loading
+ * the library holds until the process exits; n_replicas above that limit
+ * returns EINVAL.  The first call on a device looks up the array's device
+ * address once (cudaGetSymbolAddress), so make that first call outside any
+ * stream capture.  All calls on a device share the array: calls that overlap
+ * on the GPU (different streams, no ordering) race and give wrong energies.
+ * Work is enqueued on `stream`; returns EINVAL for bad sizes or NULL
+ * pointers, ECUDA if a CUDA call fails.
+ */
+dynbond_status dynbond_forces_noalloc(const int32_t* d_pos, const uint32_t* d_slots, const int64_t* d_bead_offset,
+                                      const int64_t* d_box_q, int32_t n_replicas, int64_t n_beads,
+                                      const int32_t* d_angles, int64_t n_angles, const int32_t* d_dihedrals,
+                                      int64_t n_dihedrals, const dynbond_forcefield* ff, float* d_force,
+                                      double* d_ev, dynbond_stream stream);
 
 /* Human-readable text of the last error of ctx (never NULL). */
 const char* dynbond_last_error(const dynbond_ctx* ctx);

@@ -27,7 +27,9 @@ STAT_NAMES = [
     "n_bonds", "n_angles", "n_dihedrals", "create_rounds", "break_rounds",
 ]
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
-           "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy"]
+           "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
+           "dynbond_forces_noalloc"]
+NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
                                           ctypes.c_double, ctypes.c_void_p)
@@ -103,6 +105,8 @@ def load() -> ctypes.CDLL:
     L.dynbond_status_string.argtypes = [c_i32]
     L.dynbond_destroy.restype = None
     L.dynbond_destroy.argtypes = [c_p]
+    L.dynbond_forces_noalloc.restype = c_i32
+    L.dynbond_forces_noalloc.argtypes = [c_p, c_p, c_p, c_p, c_i32, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, c_p]
     _lib = L
     return L
 
@@ -282,3 +286,35 @@ class Context:
         names = (ctypes.c_char_p * 32)()
         self._check(self.L.dynbond_phase_times(self.h, ms, names, 32, ctypes.byref(n)))
         return {names[k].decode(): float(ms[k]) for k in range(n.value)}
+
+
+def forcefield_struct(f) -> ForceField:
+    ff = ForceField()
+    for t in range(16):
+        ff.bond_k[t], ff.bond_r0[t] = float(f["bond_k"][t]), float(f["bond_r0"][t])
+        ff.angle_k[t], ff.dihedral_k[t] = float(f["angle_k"][t]), float(f["dihedral_k"][t])
+        ff.dihedral_d[t] = int(f["dihedral_d"][t])
+    return ff
+
+
+def forces_noalloc(pos, slots, bead_offset, box_q, angles, dihedrals, forcefield, force=None, ev=None, stream=None):
+    """dynbond_forces_noalloc: bonded forces of a caller-supplied topology
+    without any allocation inside the library.  All tensors are CUDA tensors:
+    pos int32 [N, 4], slots uint32-as-int32 [N, 4] (partner << 4 | stored
+    type, 0 = empty), bead_offset int64 [R+1], box_q int64 [R], angles int32
+    [na, 4], dihedrals int32 [nd, 5].  Returns (force float32 [N, 4], ev
+    float64 [R, 7]); the outputs may be preallocated by the caller."""
+    import torch
+    L = load()
+    N, R = pos.shape[0], box_q.shape[0]
+    if force is None:
+        force = torch.empty((N, 4), dtype=torch.float32, device=pos.device)
+    if ev is None:
+        ev = torch.empty((R, 7), dtype=torch.float64, device=pos.device)
+    ff = forcefield_struct(forcefield)
+    st = L.dynbond_forces_noalloc(c_p(_ptr(pos)), c_p(_ptr(slots)), c_p(_ptr(bead_offset)), c_p(_ptr(box_q)), R, N,
+                                  c_p(_ptr(angles)), angles.shape[0], c_p(_ptr(dihedrals)), dihedrals.shape[0],
+                                  ctypes.byref(ff), c_p(_ptr(force)), c_p(_ptr(ev)), _stream_handle(stream))
+    if st != 0:
+        raise DynbondError(st, "dynbond_forces_noalloc failed")
+    return force, ev
