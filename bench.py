@@ -135,6 +135,38 @@ def algorithmic_bytes(stats_before, st, N, R):
     return b
 
 
+PHASE_KERNEL = {"bead": "k_bead", "candidates": "k_candidates", "match": "k_match", "edit": "k_edit",
+                "purge": "k_purge", "bond_forces": "k_bond_forces",
+                "angle_dihedral_forces": "k_angle_dihedral_forces"}
+
+
+def sources_sha1():
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1108_4214_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                    glob.glob(os.path.join(csrc, "*.h"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(phase):
+    """DRAM bytes per launch of the phase's kernel from the committed ncu
+    summary, or None if none was recorded or the kernel sources changed since."""
+    kern = PHASE_KERNEL.get(phase)
+    path = os.path.join(ROOT, "profiles", "traffic_plain-1M.txt")
+    if kern is None or not os.path.exists(path):
+        return None
+    sha = sources_sha1()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and parts[0] == kern and parts[2] == sha:
+            return int(parts[1])
+    return None
+
+
 def kernel_bytes(phase, N, st, na_before, nd_before):
     """Algorithmic bytes of one launch of the phase that dominates the step."""
     if phase == "bead":
@@ -144,10 +176,8 @@ def kernel_bytes(phase, N, st, na_before, nd_before):
                                                      st["n_dihedrals"] - st["dihedrals_added"])
     if phase == "bond_forces":
         return 16 * N + 16 * N + 16 * N  # positions, slots, forces
-    if phase == "angle_forces":
-        return 16 * st["n_angles"] + 3 * 2 * 16 * st["n_angles"]  # records + 3 force read-modify-writes
-    if phase == "dihedral_forces":
-        return 16 * st["n_dihedrals"] + 4 * 2 * 16 * st["n_dihedrals"]
+    if phase == "angle_dihedral_forces":  # records + one force read-modify-write per role
+        return 16 * (st["n_angles"] + st["n_dihedrals"]) + 2 * 16 * (3 * st["n_angles"] + 4 * st["n_dihedrals"])
     if phase == "candidates":
         return 16 * N // 2 + 16 * N // 2 + 16 * 2 * st["candidates"]
     if phase == "cells":
@@ -317,8 +347,9 @@ def main():
     roof = None
     if kb is not None and ph[dom] > 0:
         ach = kb / (ph[dom] * 1e-3) / 1e9
-        roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
-                    peak_source=peak_kind, bytes_per_launch=kb, ms_per_launch=ph[dom], traffic=None)
+        roof = dict(bound="hbm", kernel=PHASE_KERNEL.get(dom, dom), achieved=ach, peak=peak, unit="GB/s",
+                    frac=ach / peak, peak_source=peak_kind, bytes_per_launch=kb, ms_per_launch=ph[dom],
+                    traffic=recorded_traffic(dom))
     alg = algorithmic_bytes((res["na_before"], res["nd_before"]), res["stats"], res["N"], res["R"])
     step_gbs = alg / (res["ms"] * 1e-3) / 1e9
     rank, world, _ = dist_env()
