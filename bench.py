@@ -204,6 +204,7 @@ def run_gpu(args):
     snaps = [torch.from_numpy(x).to(dev) for x in snaps_np]
     stream = torch.cuda.current_stream()
     ctx = dynbond.Context(s, flags=dynbond.FLAG_PROFILE, stream=stream)
+    tuning = ctx.autotune(snaps[0])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     force = torch.empty((N, 4), dtype=torch.float32, device=dev)
     ev = torch.empty((R, 7), dtype=torch.float64, device=dev)
@@ -248,7 +249,7 @@ def run_gpu(args):
     value = N * K * world / (total_ms / 1e3)
     result = dict(value=value, ms=total_ms / K, N=N, R=R, phases={k: float(np.mean(v)) for k, v in phases.items()},
                   stats=stats, na_before=na_before, nd_before=nd_before, clocks=clk.summary(), rank=rank,
-                  world=world, name=s.name)
+                  world=world, name=s.name, tuning=tuning)
 
     # end to end through the host-buffer entry point: pinned host input, result read back
     pin_pos = torch.empty((N, 4), dtype=torch.int32).pin_memory()
@@ -277,6 +278,78 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return result
+
+
+def run_batched(steps: int, warmup: int):
+    """Batched vs plain on the 512-replica temperature ladder: one context
+    holding every replica (one launch sequence per call, autotuned geometry)
+    against one context per replica called one after another on the same
+    stream.  Both time step + forces per call with CUDA events, L2 flushed
+    between calls."""
+    import torch
+
+    from paper_1108_4214_gb300 import dynbond
+    from paper_1108_4214_gb300 import workloads as W
+    full = W.config3()
+    N = full.n_beads
+    snaps = full.snapshots(0, steps + warmup)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(run_call):
+        for k in range(warmup):
+            run_call(k)
+        torch.cuda.synchronize()
+        total = 0.0
+        for k in range(warmup, warmup + steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run_call(k)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+        return total
+
+    pos_all = [torch.from_numpy(x).to(dev) for x in snaps]
+    ctx = dynbond.Context(full, stream=stream)
+    f = torch.empty((N, 4), dtype=torch.float32, device=dev)
+    ev = torch.empty((full.n_replicas, 7), dtype=torch.float64, device=dev)
+    tuning = ctx.autotune(pos_all[0])
+
+    def batched_call(k):
+        ctx.step(pos_all[k], k)
+        ctx.forces(pos_all[k], f, ev)
+    t_b = timed(batched_call)
+    ctx.sync()
+    ctx.close()
+
+    subs, sub_pos, sub_f, sub_ev = [], [], [], []
+    for r in range(full.n_replicas):
+        sub = W.sub_replicas(full, [r])
+        c = dynbond.Context(sub, stream=stream, flags=dynbond.FLAG_NO_AUTOTUNE)
+        sl = slice(int(full.bead_offset[r]), int(full.bead_offset[r + 1]))
+        subs.append(c)
+        sub_pos.append([p[sl] for p in pos_all])
+        sub_f.append(f[sl])
+        sub_ev.append(ev[r:r + 1])
+
+    def plain_call(k):
+        for r, c in enumerate(subs):
+            c.step(sub_pos[r][k], k)
+            c.forces(sub_pos[r][k], sub_f[r], sub_ev[r])
+    t_p = timed(plain_call)
+    for c in subs:
+        c.sync()
+        c.close()
+    vb = N * steps / (t_b / 1e3)
+    vp = N * steps / (t_p / 1e3)
+    return dict(workload=full.name, replicas=full.n_replicas, beads=N, steps=steps, warmup=warmup,
+                value=vb, ms_per_step=t_b / steps, plain_value=vp, plain_ms_per_step=t_p / steps,
+                speedup=vb / vp, tuning=tuning, unit=UNIT,
+                plain="one context per replica, called one after another on one stream")
 
 
 def cpu_baseline(seconds: float):
@@ -340,6 +413,7 @@ def main():
     res = run_gpu(args)
     if res["rank"] != 0:
         return
+    batched = None if args.no_batched or res["world"] > 1 else run_batched(10, 3)
     peak, peak_kind = peaks()
     ph = res["phases"]
     dom = max((k for k in ph if not k.endswith("setup")), key=lambda k: ph[k])
@@ -360,12 +434,13 @@ def main():
         ms_per_step=res["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64+f32",
         data="synthetic",
         config=dict(workload=res["name"], beads=res["N"], replicas=res["R"], parallelism=f"replicas x{world}",
-                    l2="flushed between timed steps (256 MB write)", step="dynbond_step + dynbond_forces"),
+                    l2="flushed between timed steps (256 MB write)", step="dynbond_step + dynbond_forces",
+                    tuning=res["tuning"]),
         roofline=roof,
         step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=step_gbs, peak=peak, unit="GB/s",
                            frac=step_gbs / peak, peak_source=peak_kind),
         phases_ms=ph, cpu_baseline=cpu, e2e=res["e2e"], gpu_launches=kernels_per_step * args.steps,
-        clocks=res["clocks"], stats_last_call=res["stats"],
+        clocks=res["clocks"], stats_last_call=res["stats"], batched=batched,
     )
     print(json.dumps(line), flush=True)
 

@@ -104,7 +104,8 @@ typedef struct dynbond_rule {
 
 enum {
   DYNBOND_FLAG_NO_GRAPH = 1,  /* launch kernels one by one instead of replaying a CUDA graph */
-  DYNBOND_FLAG_PROFILE = 2    /* record CUDA events between phases (dynbond_phase_times) */
+  DYNBOND_FLAG_PROFILE = 2,   /* record CUDA events between phases (dynbond_phase_times) */
+  DYNBOND_FLAG_NO_AUTOTUNE = 4 /* with cell_scale 0: use cells as wide as the reach, never autotune */
 };
 
 /*
@@ -119,8 +120,9 @@ enum {
  *   reactive_mask bead types of the reactive group; every rule acts only on
  *                 pairs / bonds of two reactive beads.
  *   flags         DYNBOND_FLAG_*.
- *   cell_scale    0 = autotune; k >= 1: cell edge >= k x the largest creation
- *                 distance (never changes results).
+ *   cell_scale    0 = autotune on the first dynbond_step (dynbond_autotune);
+ *                 k >= 1: cell edge = k x the largest creation distance.
+ *                 The cell geometry never changes results.
  *   block_size    0 = default (256) threads per block for the bead passes.
  *   spin_limit    0 = default; iterations of every bounded device-side wait.
  */
@@ -262,6 +264,25 @@ dynbond_status dynbond_run_host(dynbond_ctx* ctx, const int32_t* h_pos, uint64_t
 
 /* Export the current topology (two-call protocol above).  Synchronizes. */
 dynbond_status dynbond_get_topology(dynbond_ctx* ctx, dynbond_topology* topo);
+
+/*
+ * Autotuning of launch geometry (not part of the paper): the cell edge (1, 1.5,
+ * 2 or 3 x the largest creation distance) and the bead-pass grid size (4, 8 or
+ * 16 blocks per SM) are chosen by timing the front of a call (cell binning and
+ * candidate search, which write scratch only) on the positions d_pos; the
+ * fastest is kept and the captured work is rebuilt.  No choice changes results.
+ * Runs by itself on the first dynbond_step of a context created with
+ * cell_scale 0.  out (nullable) receives the choice.
+ */
+typedef struct dynbond_tuning {
+  double cell_scale;
+  int32_t bead_blocks_per_sm;
+  int32_t candidate_blocks_per_sm;
+  float front_ms;   /* device time of the timed front at the chosen geometry */
+  int32_t tuned;
+} dynbond_tuning;
+
+dynbond_status dynbond_autotune(dynbond_ctx* ctx, const int32_t* d_pos, dynbond_tuning* out);
 
 /* Wait for the context's stream and return any device-side error. */
 dynbond_status dynbond_sync(dynbond_ctx* ctx);

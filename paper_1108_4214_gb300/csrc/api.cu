@@ -48,6 +48,14 @@ struct dynbond_ctx {
   int4* h2d_pos = nullptr;
   float4* d2h_force = nullptr;
   double* d2h_ev = nullptr;
+  // cell geometry (re-chosen by the autotuner; never changes results)
+  std::vector<long long> h_box;
+  long long reach = 0;          // smallest integer cell width covering the largest creation distance
+  long long max_cells = 0;      // cells allocated (geometry at scale 1)
+  int* d_nc = nullptr;
+  long long* d_cb = nullptr;
+  dynbond_tuning tuning{};
+  bool tuned = false;
 };
 
 namespace {
@@ -357,6 +365,63 @@ void collect_profile(dynbond_ctx* c, int which) {
   for (size_t k = 0; k + 1 < ev.size(); ++k) cudaEventElapsedTime(&out[k], ev[k], ev[k + 1]);
 }
 
+// Cell grid of every replica for a cell edge of `scale` x the reach (at least
+// the reach, at most 1024 cells per axis); uploads it and sizes the scan.
+dynbond_status set_geometry(dynbond_ctx* c, double scale) {
+  const int R = c->R;
+  std::vector<int> nc(R);
+  std::vector<long long> cb(R + 1, 0);
+  for (int r = 0; r < R; ++r) {
+    long long L = c->h_box[r];
+    long long ncap = c->reach > 0 ? L / c->reach : 1;
+    long long n = c->reach > 0 ? (long long)((double)L / (scale * (double)c->reach)) : 1;
+    n = std::max<long long>(1, std::min<long long>({n, ncap, 1024}));
+    nc[r] = (int)n;
+    cb[r + 1] = cb[r] + n * n * n;
+  }
+  if (c->max_cells && cb[R] > c->max_cells) return fail(c, DYNBOND_EINVAL, "cell geometry larger than allocated");
+  c->n_cells = cb[R];
+  c->d.n_cells = c->n_cells;
+  c->grid_scan = bounded_grid(c->n_cells, 256 * 32, c->nsm * 4);
+  if (c->d_nc) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_cb, cb.data(), 8 * (R + 1), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  c->tuning.cell_scale = scale;
+  return DYNBOND_OK;
+}
+
+dynbond_status capture_graphs(dynbond_ctx* c) {
+  if (c->g_step) cudaGraphExecDestroy(c->g_step);
+  if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
+  c->g_step = c->g_forces = nullptr;
+  if (!c->use_graph) return DYNBOND_OK;
+  if (capture(c, enqueue_step, &c->g_step) != cudaSuccess || capture(c, enqueue_forces, &c->g_forces) != cudaSuccess) {
+    if (c->g_step) cudaGraphExecDestroy(c->g_step);
+    if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
+    c->g_step = c->g_forces = nullptr;
+    c->use_graph = false;
+    cudaGetLastError();
+    c->last_error = "CUDA graph capture unavailable; launching kernels directly";
+  }
+  return DYNBOND_OK;
+}
+
+// The front of a call up to the candidate lists; it writes per-call scratch
+// only, so it can be timed repeatedly without changing the topology.
+cudaError_t enqueue_front(dynbond_ctx* c) {
+  const Dev& d = c->d;
+  cudaStream_t s = c->stream;
+  k_setup<<<c->nsm * 2, 1024, 0, s>>>(d);
+  k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
+  k_scan_cells<<<c->grid_scan, 256, 0, s>>>(d);
+  k_scatter<<<c->grid_bead, 256, 0, s>>>(d);
+  k_candidates<<<c->grid_cand, 256, 0, s>>>(d, c->d_rt);
+  k_cand_overflow<<<c->nsm, 128, 0, s>>>(d, c->d_rt);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -461,26 +526,14 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaGetDevice(&c->device));
   CUDA_TRY(c, cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
 
-  // cells: edge >= largest creation distance, widened so a cell holds about
-  // one creation-capable bead (results do not depend on the choice)
-  std::vector<int> nc(R);
-  std::vector<long long> cell_base(R + 1, 0);
-  long long w = 0;
-  while (w * w < c->rt.r2max) ++w;  // smallest integer width covering the reach
-  if (c->rt.r2max > 0 && w < 1) w = 1;
-  for (int r = 0; r < R; ++r) {
-    long long L = sys->box_q[r];
-    long long ncap = w > 0 ? L / w : 1;
-    // default: cells as narrow as the reach allows (the search scans
-    // contiguous z-runs of three cells, so narrow cells cost little); a
-    // larger cell_scale trades more visited entries for fewer lookups
-    double scale = params->cell_scale > 0 ? params->cell_scale : 1.0;
-    long long n = w > 0 ? (long long)((double)L / (scale * (double)w)) : 1;
-    n = std::max<long long>(1, std::min<long long>({n, ncap, 1024}));
-    nc[r] = (int)n;
-    cell_base[r + 1] = cell_base[r] + n * n * n;
-  }
-  c->n_cells = cell_base[R];
+  // cells: edge >= the largest creation distance; the default (and the
+  // autotuner's largest grid) is cells exactly as wide as that reach
+  c->h_box.assign(sys->box_q, sys->box_q + R);
+  c->reach = 0;
+  while (c->reach * c->reach < c->rt.r2max) ++c->reach;
+  st = set_geometry(c, params->cell_scale > 0 ? (double)params->cell_scale : 1.0);
+  if (st) return st;
+  c->max_cells = c->n_cells;
   c->W = N / 32 + 1;
   c->d.W = c->W;
 
@@ -506,6 +559,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(p_box, R);
   ALLOC(p_cb, R + 1);
   ALLOC(p_nc, R);
+  c->d_nc = p_nc;
+  c->d_cb = p_cb;
   ALLOC(p_rep, N);
   ALLOC(p_type, N);
   ALLOC(p_stream, R);
@@ -630,8 +685,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemcpyAsync(c->d_rt, &c->rt, sizeof(RuleTab), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_off, offv.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_box, boxv.data(), 8 * R, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(c, cudaMemcpyAsync(p_cb, cell_base.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(c, cudaMemcpyAsync(p_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, s));
+  st = set_geometry(c, c->tuning.cell_scale);
+  if (st) return st;
   CUDA_TRY(c, cudaMemcpyAsync(p_rep, rep.data(), 4 * N, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_type, type.data(), N, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_stream, strm.data(), 4 * R, cudaMemcpyHostToDevice, s));
@@ -647,7 +702,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
 
   // ---- launch geometry
   c->grid_bead = bounded_grid(N, 256, c->nsm * 8);
-  c->grid_scan = bounded_grid(c->n_cells, 256 * 32, c->nsm * 4);
+  c->tuning.bead_blocks_per_sm = 8;
+  c->tuning.candidate_blocks_per_sm = 8;
   c->grid_cand = bounded_grid(N, 256, c->nsm * 8);
   c->grid_nb = bounded_grid(N, 256 * 64, c->nsm * 4);
   c->grid_seg = c->nsm * 4;
@@ -677,18 +733,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     for (auto& e : c->ev_step) CUDA_TRY(c, cudaEventCreate(&e));
     for (auto& e : c->ev_forces) CUDA_TRY(c, cudaEventCreate(&e));
   }
-  if (c->use_graph) {
-    if (capture(c, enqueue_step, &c->g_step) != cudaSuccess ||
-        capture(c, enqueue_forces, &c->g_forces) != cudaSuccess) {
-      if (c->g_step) cudaGraphExecDestroy(c->g_step);
-      if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
-      c->g_step = c->g_forces = nullptr;
-      c->use_graph = false;
-      cudaGetLastError();
-      c->last_error = "CUDA graph capture unavailable; launching kernels directly";
-    }
-  }
-  return DYNBOND_OK;
+  c->tuned = params->cell_scale > 0 || (params->flags & DYNBOND_FLAG_NO_AUTOTUNE);
+  return capture_graphs(c);
 }
 
 }  // namespace
@@ -714,6 +760,10 @@ dynbond_status dynbond_create(const dynbond_params* params, const dynbond_rule* 
 dynbond_status dynbond_step(dynbond_ctx* c, const int32_t* d_pos, uint64_t step, dynbond_stats* h_stats) {
   if (!c || !d_pos) return DYNBOND_EINVAL;
   if (c->sticky) return c->sticky;
+  if (!c->tuned) {
+    dynbond_status st = dynbond_autotune(c, d_pos, nullptr);
+    if (st) return st;
+  }
   k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, step, 1, 0);
   cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_step, c->stream) : enqueue_step(c);
   if (e != cudaSuccess) {
@@ -758,6 +808,54 @@ dynbond_status dynbond_run_host(dynbond_ctx* c, const int32_t* h_pos, uint64_t s
   if (st) return st;
   if (h_stats) CUDA_TRY(c, cudaMemcpy(h_stats, c->d.stats, sizeof(dynbond_stats) * c->R, cudaMemcpyDeviceToHost));
   return DYNBOND_OK;
+}
+
+dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tuning* out) {
+  if (!c || !d_pos) return DYNBOND_EINVAL;
+  if (c->sticky) return c->sticky;
+  dynbond_status st = DYNBOND_OK;
+  if (c->max_cells) {
+    const double scales[] = {1.0, 1.5, 2.0, 3.0};
+    const int grids[] = {4, 8, 16};
+    cudaEvent_t e0, e1;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    CUDA_TRY(c, cudaEventCreate(&e1));
+    k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, 0, 1, 0);
+    float best = 1e30f;
+    double best_scale = 1.0;
+    int best_grid = 8;
+    for (double sc : scales) {
+      if ((st = set_geometry(c, sc))) break;
+      for (int gm : grids) {
+        c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * gm);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and clocks
+          cudaEventRecord(e0, c->stream);
+          enqueue_front(c);
+          cudaEventRecord(e1, c->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) break;
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms < best) {
+          best = ms;
+          best_scale = sc;
+          best_grid = gm;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!st) st = set_geometry(c, best_scale);
+    c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * best_grid);
+    c->tuning.bead_blocks_per_sm = c->tuning.candidate_blocks_per_sm = best_grid;
+    c->tuning.front_ms = best;
+    if (!st) st = device_status(c);
+    if (!st) st = capture_graphs(c);
+  }
+  c->tuned = true;
+  c->tuning.tuned = 1;
+  if (out) *out = c->tuning;
+  return st;
 }
 
 dynbond_status dynbond_sync(dynbond_ctx* c) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdynbond.
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOTCONVERGED"}
 KINDS = dict(createbond=1, createdirbond=2, breakbond=3, convertbond=4, killbond=5, createangle=6,
              createdihedral=7, maxbond=8)
-FLAG_NO_GRAPH, FLAG_PROFILE = 1, 2
+FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_NO_AUTOTUNE = 1, 2, 4
 STAT_NAMES = [
     "candidates", "create_matched", "bonds_formed", "break_candidates", "break_matched", "bonds_broken",
     "bonds_killed", "bonds_converted", "angles_removed", "angles_added", "dihedrals_removed", "dihedrals_added",
@@ -28,7 +28,7 @@ STAT_NAMES = [
 ]
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
            "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
-           "dynbond_forces_noalloc"]
+           "dynbond_forces_noalloc", "dynbond_autotune"]
 NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
@@ -65,6 +65,11 @@ class SystemDesc(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, c_i64) for n in STAT_NAMES]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("cell_scale", c_dbl), ("bead_blocks_per_sm", c_i32), ("candidate_blocks_per_sm", c_i32),
+                ("front_ms", ctypes.c_float), ("tuned", c_i32)]
 
 
 class Topology(ctypes.Structure):
@@ -105,6 +110,8 @@ def load() -> ctypes.CDLL:
     L.dynbond_status_string.argtypes = [c_i32]
     L.dynbond_destroy.restype = None
     L.dynbond_destroy.argtypes = [c_p]
+    L.dynbond_autotune.restype = c_i32
+    L.dynbond_autotune.argtypes = [c_p, c_p, c_p]
     L.dynbond_forces_noalloc.restype = c_i32
     L.dynbond_forces_noalloc.argtypes = [c_p, c_p, c_p, c_p, c_i32, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, c_p]
     _lib = L
@@ -268,6 +275,12 @@ class Context:
 
     def sync(self):
         self._check(self.L.dynbond_sync(self.h))
+
+    def autotune(self, pos) -> Dict:
+        """dynbond_autotune on device positions; returns the chosen geometry."""
+        t = Tuning()
+        self._check(self.L.dynbond_autotune(self.h, c_p(_ptr(pos)), ctypes.byref(t)))
+        return {n: getattr(t, n) for n, _ in Tuning._fields_}
 
     def topology(self):
         """(bonds [nb, 4], angles [na, 4], dihedrals [nd, 5]) canonical and sorted (numpy)."""

@@ -253,3 +253,19 @@ def test_melting_16m_beads_full_size_two_calls():
     s = W.config4()
     snaps = s.snapshots(0, 2)
     run_parity(s, 2, snaps=snaps, forces=True)
+
+
+def test_autotuned_and_fixed_geometries_give_identical_results():
+    s = W.config1()
+    D = dynbond()
+    ctxs = [D.Context(s), D.Context(s, flags=D.FLAG_NO_AUTOTUNE), D.Context(s, params=dict(cell_scale=3))]
+    for k in range(4):
+        p = torch.from_numpy(s.snapshot(k)).cuda()
+        sts = [c.step(p, k, stats=True) for c in ctxs]
+        assert all(np.array_equal(sts[0], x) for x in sts[1:])
+    tops = [c.topology() for c in ctxs]
+    for t in tops[1:]:
+        for x, y in zip(tops[0], t):
+            assert np.array_equal(x, y)
+    info = ctxs[0].autotune(torch.from_numpy(s.snapshot(4)).cuda())
+    assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.5, 2.0, 3.0)
