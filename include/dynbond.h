@@ -329,6 +329,38 @@ dynbond_status dynbond_forces_noalloc(const int32_t* d_pos, const uint32_t* d_sl
                                       int64_t n_dihedrals, const dynbond_forcefield* ff, float* d_force,
                                       double* d_ev, dynbond_stream stream);
 
+/*
+ * Molecular-dynamics harness (the DPD systems of Sec. 3): velocity-Verlet
+ * with the DPD force field F_ij = (a w - gamma w^2 (rhat . v_ij) +
+ * sigma w xi / sqrt(dt)) rhat, sigma^2 = 2 kT gamma, w = 1 - r / rc, between
+ * every pair closer than rc except beads fewer than 3 bonds apart, plus the
+ * bonded forces of the context.  Positions stay on the int32 grid: each drift
+ * adds round(v dt 2^20) and wraps into the box.  xi is a Gaussian drawn from
+ * Philox4x32-10 on (lower id, higher id, step), the same for both beads of a
+ * pair.  One replica per context.  dynbond_md_advance runs n_steps steps from
+ * step index first_step on d_pos (int4[N], updated) and d_vel (float4[N],
+ * updated, w ignored), recomputing the forces at first_step first (the
+ * topology may have changed since the last call); d_ev (nullable, device
+ * double[7]) receives the bonded energy / virial of the last step.  Waits for
+ * completion.
+ */
+typedef struct dynbond_dpd {
+  double a;      /* conservative amplitude */
+  double gamma;  /* friction */
+  double kT;
+  double rc;     /* cutoff */
+  double dt;
+  double mass;
+  uint64_t seed;
+} dynbond_dpd;
+
+typedef struct dynbond_md dynbond_md;
+
+dynbond_status dynbond_md_create(dynbond_ctx* ctx, const dynbond_dpd* dpd, dynbond_md** out);
+dynbond_status dynbond_md_advance(dynbond_md* md, int32_t* d_pos, float* d_vel, int64_t n_steps, uint64_t first_step,
+                                  double* d_ev);
+void dynbond_md_destroy(dynbond_md* md);
+
 /* Human-readable text of the last error of ctx (never NULL). */
 const char* dynbond_last_error(const dynbond_ctx* ctx);
 

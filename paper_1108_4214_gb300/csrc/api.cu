@@ -424,6 +424,15 @@ cudaError_t enqueue_front(dynbond_ctx* c) {
 
 }  // namespace
 
+const uint4* dynbond::internal_slots(const dynbond_ctx* c, long long* n_beads, long long* box_q, int* n_replicas,
+                                     cudaStream_t* stream) {
+  *n_beads = c->N;
+  *box_q = c->h_box.empty() ? 0 : c->h_box[0];
+  *n_replicas = c->R;
+  *stream = c->stream;
+  return c->d.slots;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

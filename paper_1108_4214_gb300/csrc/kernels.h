@@ -32,6 +32,10 @@ __global__ void k_setup(Dev d);
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
                            int set_pos, int set_force);
 
+// the context's bond slots and geometry, for the MD harness (defined in api.cu)
+const uint4* internal_slots(const dynbond_ctx* ctx, long long* n_beads, long long* box_q, int* n_replicas,
+                            cudaStream_t* stream);
+
 __global__ void k_bond_forces(Dev d, FF ff);
 __global__ void k_angle_dihedral_forces(Dev d, FF ff);
 __global__ void k_ev_out(Dev d);

@@ -28,7 +28,8 @@ STAT_NAMES = [
 ]
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
            "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
-           "dynbond_forces_noalloc", "dynbond_autotune"]
+           "dynbond_forces_noalloc", "dynbond_autotune", "dynbond_md_create", "dynbond_md_advance",
+           "dynbond_md_destroy"]
 NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
@@ -72,6 +73,11 @@ class Tuning(ctypes.Structure):
                 ("front_ms", ctypes.c_float), ("tuned", c_i32)]
 
 
+class DPD(ctypes.Structure):
+    _fields_ = [("a", c_dbl), ("gamma", c_dbl), ("kT", c_dbl), ("rc", c_dbl), ("dt", c_dbl), ("mass", c_dbl),
+                ("seed", c_u64)]
+
+
 class Topology(ctypes.Structure):
     _fields_ = [("n_bonds", c_i64), ("n_angles", c_i64), ("n_dihedrals", c_i64), ("bonds", c_p),
                 ("angles", c_p), ("dihedrals", c_p)]
@@ -110,6 +116,12 @@ def load() -> ctypes.CDLL:
     L.dynbond_status_string.argtypes = [c_i32]
     L.dynbond_destroy.restype = None
     L.dynbond_destroy.argtypes = [c_p]
+    L.dynbond_md_create.restype = c_i32
+    L.dynbond_md_create.argtypes = [c_p, c_p, ctypes.POINTER(c_p)]
+    L.dynbond_md_advance.restype = c_i32
+    L.dynbond_md_advance.argtypes = [c_p, c_p, c_p, c_i64, c_u64, c_p]
+    L.dynbond_md_destroy.restype = None
+    L.dynbond_md_destroy.argtypes = [c_p]
     L.dynbond_autotune.restype = c_i32
     L.dynbond_autotune.argtypes = [c_p, c_p, c_p]
     L.dynbond_forces_noalloc.restype = c_i32
@@ -331,3 +343,34 @@ def forces_noalloc(pos, slots, bead_offset, box_q, angles, dihedrals, forcefield
     if st != 0:
         raise DynbondError(st, "dynbond_forces_noalloc failed")
     return force, ev
+
+
+class MD:
+    """dynbond_md_*: velocity-Verlet DPD harness around a one-replica Context."""
+
+    def __init__(self, ctx: Context, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.01, mass=1.0, seed=12345):
+        self.L = load()
+        self.ctx = ctx
+        p = DPD(a=a, gamma=gamma, kT=kT, rc=rc, dt=dt, mass=mass, seed=seed % (1 << 64))
+        h = c_p()
+        st = self.L.dynbond_md_create(ctx.h, ctypes.byref(p), ctypes.byref(h))
+        if st != 0:
+            raise DynbondError(st, "dynbond_md_create failed (one replica, positive rc, dt, mass)")
+        self.h = h
+
+    def advance(self, pos, vel, n_steps: int, first_step: int, ev=None):
+        st = self.L.dynbond_md_advance(self.h, c_p(_ptr(pos)), c_p(_ptr(vel)), int(n_steps), int(first_step),
+                                       c_p(_ptr(ev)))
+        if st != 0:
+            raise DynbondError(st, "dynbond_md_advance failed")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.dynbond_md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -301,6 +301,22 @@ def scaled_config4(n_strands: int, seed: int = 4) -> System:
                       n_duplex=n_strands // 4)
 
 
+def config5() -> System:
+    """32768 strands x 64 nt = 4,194,304 beads at density 0.5 (L = 203.2),
+    seed 5: the end-to-end DPD loop."""
+    return dna_system("dpd-4M (32768 strands x 64 nt, rho=0.5)", 32768, 64, 0.5, 5, rules_dna2())
+
+
+def initial_velocities(n_beads: int, kT: float = 1.0, mass: float = 1.0, seed: int = 5) -> np.ndarray:
+    """Maxwell-Boltzmann velocities float32 [N, 4] (w = 0), zero total momentum."""
+    rng = np.random.default_rng([seed, 31337])
+    v = rng.normal(0.0, math.sqrt(kT / mass), size=(n_beads, 3))
+    v -= v.mean(axis=0)
+    out = np.zeros((n_beads, 4), np.float32)
+    out[:, :3] = v
+    return out
+
+
 def ladder_sizes(n_replicas=512, seed=3, lo=2048, hi=65536, median=8192, sigma=0.693):
     rng = np.random.default_rng([seed, 1])
     z = rng.normal(size=n_replicas)
