@@ -32,7 +32,7 @@ struct dynbond_ctx {
   cudaGraphExec_t g_step = nullptr, g_forces = nullptr;
   bool use_graph = true;
   int block = 256;
-  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_nb = 0, grid_seg = 0;
+  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_nb = 0, grid_seg = 0, grid_force = 0;
   long long st_scan_n = 0, st_nb_n = 0, st_pa_n = 0, st_pd_n = 0, st_rb_n = 0;
   void* small = nullptr;
   size_t small_bytes = 0;
@@ -293,9 +293,9 @@ cudaError_t enqueue_forces(dynbond_ctx* c) {
   cudaStream_t s = c->stream;
   size_t k = 0;
   mark(c, c->ev_forces, k++);
-  k_bond_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
+  k_bond_forces<<<c->grid_force, 256, 0, s>>>(d, c->ff);
   mark(c, c->ev_forces, k++);
-  k_angle_dihedral_forces<<<c->grid_bead, 256, 0, s>>>(d, c->ff);
+  k_angle_dihedral_forces<<<c->grid_force, 256, 0, s>>>(d, c->ff);
   mark(c, c->ev_forces, k++);
   k_ev_out<<<1, 256, 0, s>>>(d);
   return cudaGetLastError();
@@ -711,6 +711,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
 
   // ---- launch geometry
   c->grid_bead = bounded_grid(N, 256, c->nsm * 8);
+  c->grid_force = bounded_grid(N, 256, c->nsm * 8);
   c->tuning.bead_blocks_per_sm = 8;
   c->tuning.candidate_blocks_per_sm = 8;
   c->grid_cand = bounded_grid(N, 256, c->nsm * 8);

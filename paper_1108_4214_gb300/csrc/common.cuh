@@ -239,6 +239,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
+// Once any device error is recorded (a bounded wait gave up, a capacity or
+// consistency check failed, a bad position), every later kernel of the call
+// returns at once, so no kernel consumes half-built data.
+__device__ __forceinline__ bool aborted(const unsigned* err) { return *(const volatile unsigned*)err != 0u; }
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round the counter
 // words 0 and 2 are multiplied by the two round multipliers, high halves are

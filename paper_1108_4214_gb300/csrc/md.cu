@@ -45,6 +45,7 @@ __global__ void md_clear(MdDev m) {
 }
 
 __global__ void md_bin(MdDev m, const int4* __restrict__ pos) {
+  if (aborted(m.err)) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += (long long)gridDim.x * blockDim.x) {
     int4 p = pos[i];
     long long c = (((long long)p.x * m.nc / m.L) * m.nc + (long long)p.y * m.nc / m.L) * m.nc +
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(256) md_scan(MdDev m) {
 }
 
 __global__ void md_scatter(MdDev m, const int4* __restrict__ pos) {
+  if (aborted(m.err)) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += (long long)gridDim.x * blockDim.x) {
     int4 p = pos[i];
     p.w = (int)i;
@@ -129,6 +131,7 @@ __device__ __forceinline__ float md_gauss(const MdDev& m, int lo, int hi, unsign
 // same random number), written with plain stores
 __global__ void __launch_bounds__(256) md_dpd(MdDev m, const int4* __restrict__ pos, const float4* __restrict__ vel,
                                                const uint4* __restrict__ slots, unsigned long long step) {
+  if (aborted(m.err)) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m.N; e += (long long)gridDim.x * blockDim.x) {
     int4 me = m.sorted[e];
     int i = me.w;
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(256) md_dpd(MdDev m, const int4* __restrict__ 
 
 // v += dt/2 F/m, then (drift) x += v dt rounded onto the grid and wrapped
 __global__ void md_kick(MdDev m, float4* vel, const float4* __restrict__ fb, int4* pos, int drift) {
+  if (aborted(m.err)) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += (long long)gridDim.x * blockDim.x) {
     float4 v = vel[i], a = fb[i], b = m.fdpd[i];
     float h = 0.5f * m.dt * m.inv_m;

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
 // k_scan_cells: in-place exclusive scan of the cell histogram
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
+  if (aborted(d.err)) return;
   __shared__ long long sh[33];
   __shared__ long long s_excl;
   __shared__ long long s_tile;
@@ -207,6 +208,7 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
 }
 
 __global__ void __launch_bounds__(256) k_scatter(Dev d) {
+  if (aborted(d.err)) return;
   const int4* __restrict__ pos = d.args->pos;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += stride) {
@@ -432,6 +434,7 @@ __device__ __forceinline__ void load_type_masks(const RuleTab& rt, unsigned* s_m
 }
 
 __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+  if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
   const long long r2max = rtp->r2max;
@@ -475,6 +478,7 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __rest
 // Exact path for beads with more than MAXC candidates: count, allocate,
 // write, then sort the bead's list by (d2, partner) in place.
 __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp) {
+  if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
   const long long r2max = rtp->r2max;
@@ -521,6 +525,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
+  if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b;
   const long long N = d.N;
@@ -638,6 +643,7 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
 // k_edit: trials and in-place edit of each bead's own slots
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__ rtp) {
+  if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -782,6 +788,7 @@ __device__ __forceinline__ int owned_new(const Dev& d, long long u, int mode, in
 }
 
 __global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
+  if (aborted(d.err)) return;
   __shared__ long long sh[33];
   __shared__ long long s_excl, s_tile;
   const long long N = d.N;
@@ -884,6 +891,7 @@ __device__ void block_tile_bases(const int* count, int R, int per_tile, int* bas
 }
 
 __global__ void k_tiles(Dev d, int mode) {
+  if (aborted(d.err)) return;
   if (mode == 0) {
     block_tile_bases(d.n_ang, d.R, PURGE_TILE, d.tb_ang, nullptr);
     __syncthreads();
@@ -906,6 +914,7 @@ __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
 }
 
 __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) {
+  if (aborted(d.err)) return;
   __shared__ long long s_excl, s_tile;
   __shared__ int s_tot;
   __shared__ int s_cnt[PURGE_PER_THREAD][32];
@@ -1102,6 +1111,7 @@ struct WriteEmit {
 };
 
 __global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new) {
+  if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   __shared__ long long sh[33];
   __shared__ long long s_excl, s_tile;
@@ -1169,6 +1179,7 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
 // Per-replica list counts and statistics after the call, then the force tile
 // bases of the final lists (one block).
 __global__ void __launch_bounds__(1024) k_finalize(Dev d) {
+  if (aborted(d.err)) return;
   for (int r = threadIdx.x; r < d.R; r += blockDim.x) {
     long long* st = d.stats + (long long)r * NSTAT;
     int na = d.kept_ang[r] + d.added_ang[r], nd = d.kept_dih[r] + d.added_dih[r];

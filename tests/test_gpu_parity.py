@@ -269,3 +269,28 @@ def test_autotuned_and_fixed_geometries_give_identical_results():
             assert np.array_equal(x, y)
     info = ctxs[0].autotune(torch.from_numpy(s.snapshot(4)).cuda())
     assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.5, 2.0, 3.0)
+
+
+def test_bounded_wait_gives_up_with_a_status_and_leaves_the_device_usable():
+    """With every device-side wait limited to one poll, some wait (a look-back
+    or the matching's grid barrier) gives up; the kernel records ETIMEOUT,
+    every later kernel of the call returns at once, the host reports the
+    status, and the CUDA context stays usable for new work."""
+    D = dynbond()
+    s = W.config2()
+    pos = torch.from_numpy(s.snapshot(0)).cuda()
+    status = None
+    try:
+        ctx = D.Context(s, params=dict(spin_limit=1), flags=D.FLAG_NO_AUTOTUNE)
+        ctx.step(pos, 0, stats=True)
+    except D.DynbondError as e:
+        status = e.status
+    assert status == 5
+    if "ctx" in locals():
+        with pytest.raises(D.DynbondError):
+            ctx.step(pos, 1)
+    assert torch.ones(1000, device="cuda").sum().item() == 1000.0
+    s1 = W.config1()
+    ok = D.Context(s1)
+    st = ok.step(torch.from_numpy(s1.snapshot(0)).cuda(), 0, stats=True)
+    assert st[0, 12] > 0
