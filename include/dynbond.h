@@ -103,9 +103,11 @@ typedef struct dynbond_rule {
 } dynbond_rule;
 
 enum {
-  DYNBOND_FLAG_NO_GRAPH = 1,  /* launch kernels one by one instead of replaying a CUDA graph */
-  DYNBOND_FLAG_PROFILE = 2,   /* record CUDA events between phases (dynbond_phase_times) */
-  DYNBOND_FLAG_NO_AUTOTUNE = 4 /* with cell_scale 0: use cells as wide as the reach, never autotune */
+  DYNBOND_FLAG_NO_GRAPH = 1,    /* launch kernels one by one instead of replaying a CUDA graph */
+  DYNBOND_FLAG_PROFILE = 2,     /* record CUDA events between phases (dynbond_phase_times) */
+  DYNBOND_FLAG_NO_AUTOTUNE = 4, /* with cell_scale 0: use cells as wide as the reach, never autotune */
+  DYNBOND_FLAG_NO_PDL = 8       /* launch each kernel only after the previous one ends (no programmatic
+                                   dependent launch); results are identical either way */
 };
 
 /*

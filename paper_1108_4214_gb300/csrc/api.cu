@@ -31,9 +31,10 @@ struct dynbond_ctx {
   std::vector<void*> allocs;
   cudaGraphExec_t g_step = nullptr, g_forces = nullptr;
   bool use_graph = true;
+  bool pdl = true;  // programmatic dependent launch between the kernels of a call
   int block = 256;
-  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_nb = 0, grid_seg = 0, grid_force = 0;
-  long long st_scan_n = 0, st_nb_n = 0, st_pa_n = 0, st_pd_n = 0, st_rb_n = 0;
+  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_seg = 0, grid_force = 0, grid_edit = 0;
+  long long st_scan_n = 0;
   void* small = nullptr;
   size_t small_bytes = 0;
   void* status_all = nullptr;
@@ -244,6 +245,30 @@ void mark(dynbond_ctx* c, std::vector<cudaEvent_t>& ev, size_t k) {
   if (c->profile && k < ev.size()) cudaEventRecord(ev[k], c->stream);
 }
 
+// Launch on the context's stream, with programmatic stream serialization
+// unless the context disables it (every kernel waits for its predecessor with
+// griddepcontrol.wait before touching memory) or profiles (events between
+// phases would measure the overlap, not the phases).
+#define E(x)                              \
+  do {                                    \
+    cudaError_t e_ = (x);                 \
+    if (e_ != cudaSuccess) return e_;     \
+  } while (0)
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = c->pdl && !c->profile ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_match(dynbond_ctx* c) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->grid_match);
@@ -259,45 +284,39 @@ cudaError_t launch_match(dynbond_ctx* c) {
 
 cudaError_t enqueue_step(dynbond_ctx* c) {
   const Dev& d = c->d;
-  cudaStream_t s = c->stream;
   size_t k = 0;
   mark(c, c->ev_step, k++);
-  k_setup<<<c->nsm * 2, 1024, 0, s>>>(d);
+  E(launch(c, k_setup, c->nsm * 2, 1024, d));
   mark(c, c->ev_step, k++);
-  k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
+  E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   mark(c, c->ev_step, k++);
-  k_scan_cells<<<c->grid_scan, 256, 0, s>>>(d);
-  k_scatter<<<c->grid_bead, 256, 0, s>>>(d);
+  E(launch(c, k_scan_cells, c->grid_scan, 256, d));
+  E(launch(c, k_scatter, c->grid_bead, 256, d));
   mark(c, c->ev_step, k++);
-  k_candidates<<<c->grid_cand, 256, 0, s>>>(d, c->d_rt);
-  k_cand_overflow<<<c->nsm, 128, 0, s>>>(d, c->d_rt);
+  E(launch(c, k_candidates, c->grid_cand, 256, d, c->d_rt));
+  E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   mark(c, c->ev_step, k++);
-  cudaError_t e = launch_match(c);
-  if (e != cudaSuccess) return e;
+  E(launch_match(c));
   mark(c, c->ev_step, k++);
-  k_edit<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
+  E(launch(c, k_edit, c->grid_edit, 256, d, c->d_rt));
   mark(c, c->ev_step, k++);
-  k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 0);
-  k_tiles<<<1, 1024, 0, s>>>(d, 1);
+  E(launch(c, k_purge, c->nsm * 2, PURGE_TILE / 8, d));
+  E(launch(c, k_fill, c->nsm * 4, FILL_TILE, d));
   mark(c, c->ev_step, k++);
-  k_purge<<<c->nsm * 2, PURGE_TILE / 8, 0, s>>>(d);
-  mark(c, c->ev_step, k++);
-  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->d_rt, 0);
-  k_finalize<<<1, 1024, 0, s>>>(d);
+  E(launch(c, k_rebuild, c->grid_seg, 256, d, c->d_rt, 0));
   mark(c, c->ev_step, k++);
   return cudaGetLastError();
 }
 
 cudaError_t enqueue_forces(dynbond_ctx* c) {
   const Dev& d = c->d;
-  cudaStream_t s = c->stream;
   size_t k = 0;
   mark(c, c->ev_forces, k++);
-  k_bond_forces<<<c->grid_force, 256, 0, s>>>(d, c->ff);
+  E(launch(c, k_bond_forces, c->grid_force, 256, d, c->ff));
   mark(c, c->ev_forces, k++);
-  k_angle_dihedral_forces<<<c->grid_force, 256, 0, s>>>(d, c->ff);
+  E(launch(c, k_angle_dihedral_forces, c->grid_force, 256, d, c->ff));
   mark(c, c->ev_forces, k++);
-  k_ev_out<<<1, 256, 0, s>>>(d);
+  E(launch(c, k_ev_out, 1, 256, d));
   return cudaGetLastError();
 }
 
@@ -412,13 +431,12 @@ dynbond_status capture_graphs(dynbond_ctx* c) {
 // only, so it can be timed repeatedly without changing the topology.
 cudaError_t enqueue_front(dynbond_ctx* c) {
   const Dev& d = c->d;
-  cudaStream_t s = c->stream;
-  k_setup<<<c->nsm * 2, 1024, 0, s>>>(d);
-  k_bead<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
-  k_scan_cells<<<c->grid_scan, 256, 0, s>>>(d);
-  k_scatter<<<c->grid_bead, 256, 0, s>>>(d);
-  k_candidates<<<c->grid_cand, 256, 0, s>>>(d, c->d_rt);
-  k_cand_overflow<<<c->nsm, 128, 0, s>>>(d, c->d_rt);
+  E(launch(c, k_setup, c->nsm * 2, 1024, d));
+  E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
+  E(launch(c, k_scan_cells, c->grid_scan, 256, d));
+  E(launch(c, k_scatter, c->grid_bead, 256, d));
+  E(launch(c, k_candidates, c->grid_cand, 256, d, c->d_rt));
+  E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   return cudaGetLastError();
 }
 
@@ -476,6 +494,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->stream = (cudaStream_t)stream;
   c->profile = (params->flags & DYNBOND_FLAG_PROFILE) != 0;
   c->use_graph = (params->flags & DYNBOND_FLAG_NO_GRAPH) == 0;
+  c->pdl = (params->flags & DYNBOND_FLAG_NO_PDL) == 0;
   if (params->max_rounds < 0 || params->prob_mode < 0 || params->prob_mode > 1 || params->cell_scale < 0)
     return (fail(c, DYNBOND_EINVAL, "bad max_rounds, prob_mode or cell_scale"));
   dynbond_status st = build_rules(c, rules, n_rules);
@@ -611,18 +630,21 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.rem, N);
   ALLOC(d.newp, N);
   ALLOC(d.nbl, 2 * N + 1);
-  ALLOC(d.nbl_first, R);
+  ALLOC(d.rm_ang, 6 * N);
+  ALLOC(d.rm_dih, 18 * N);
+  ALLOC(d.pr_ang, 6 * N);
+  ALLOC(d.pr_dih, 18 * N);
   ALLOC(d.tb_ang, R + 1);
   ALLOC(d.tb_dih, R + 1);
-  ALLOC(d.tb_nb, R + 1);
+  ALLOC(d.tb_fill, R + 1);
   ALLOC(d.tb_beads, R + 1);
   ALLOC(d.tb_fang, R + 1);
   ALLOC(d.tb_fdih, R + 1);
   ALLOC(d.ev_acc, 7 * R);
-  // per-call counters zeroed together: kept/added counts, new-bond counts,
-  // round flags, statistics
+  // per-call counters zeroed together: removed / added counts, k_fill
+  // counters and items, round flags, statistics
   {
-    size_t ints = 5 * (size_t)R + 2 * (size_t)R;
+    size_t ints = 11 * (size_t)R;
     size_t bytes = ((ints * sizeof(int) + 15) / 16) * 16 + (size_t)R * NSTAT * sizeof(long long);
     char* base;
     ALLOC(base, bytes);
@@ -631,21 +653,18 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     d.small = (int*)base;
     d.small_words = (long long)(bytes / sizeof(int));
     int* ip = (int*)base;
-    d.kept_ang = ip;
-    d.kept_dih = ip + R;
+    d.m_ang = ip;
+    d.m_dih = ip + R;
     d.added_ang = ip + 2 * R;
     d.added_dih = ip + 3 * R;
-    d.nbl_count = ip + 4 * R;
-    d.round_hit = ip + 5 * R;
+    d.fill_items = ip + 4 * R;
+    d.round_hit = ip + 5 * R;  // 2R
+    d.fillc = ip + 7 * R;      // 4R
     d.stats = (long long*)(base + ((ints * sizeof(int) + 15) / 16) * 16);
   }
   {
     c->st_scan_n = c->n_cells / (256 * 32) + 2;
-    c->st_nb_n = N / (256 * 64) + 2;
-    c->st_pa_n = 6 * N / PURGE_TILE + R + 2;
-    c->st_pd_n = 18 * N / PURGE_TILE + R + 2;
-    c->st_rb_n = 2 * N / REBUILD_TILE + R + 2;
-    long long tot = c->st_scan_n + c->st_nb_n + c->st_pa_n + c->st_pd_n + c->st_rb_n;
+    long long tot = c->st_scan_n;
     unsigned long long* base;
     ALLOC(base, tot);
     c->status_all = base;
@@ -653,10 +672,6 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     d.status_all = base;
     d.status_words = tot;
     d.st_scan = base;
-    d.st_nb = d.st_scan + c->st_scan_n;
-    d.st_pa = d.st_nb + c->st_nb_n;
-    d.st_pd = d.st_pa + c->st_pa_n;
-    d.st_rb = d.st_pd + c->st_pd_n;
   }
   ALLOC(c->h2d_pos, N);
   ALLOC(c->d2h_force, N);
@@ -705,6 +720,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemcpyAsync(d.n_bonds, nb_rep.data(), 8 * R, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(d.tb_beads, tbeads.data(), 4 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
+  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_dirty, d.bm_new})
+    CUDA_TRY(c, cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)c->W, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_ang, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_dih, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.args, 0, sizeof(CallArgs), s));
@@ -712,10 +729,10 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   // ---- launch geometry
   c->grid_bead = bounded_grid(N, 256, c->nsm * 8);
   c->grid_force = bounded_grid(N, 256, c->nsm * 8);
+  c->grid_edit = bounded_grid((c->W + 7) / 8, 8, c->nsm * 8);  // a warp per 8 bitmap words
   c->tuning.bead_blocks_per_sm = 8;
   c->tuning.candidate_blocks_per_sm = 8;
   c->grid_cand = bounded_grid(N, 256, c->nsm * 8);
-  c->grid_nb = bounded_grid(N, 256 * 64, c->nsm * 4);
   c->grid_seg = c->nsm * 4;
   // one 1024-thread block per SM: full latency hiding with few barrier arrivals
   c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 1024, 1),
@@ -725,10 +742,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s));
   CUDA_TRY(c, cudaMemsetAsync(c->small, 0, c->small_bytes, s));
   CUDA_TRY(c, cudaMemsetAsync(c->status_all, 0, c->status_bytes, s));
-  k_newbonds<<<c->grid_nb, 256, 0, s>>>(d, 1);
-  k_tiles<<<1, 1024, 0, s>>>(d, 1);
-  k_rebuild<<<c->grid_seg, REBUILD_TILE, 0, s>>>(d, c->d_rt, 1);
-  k_finalize<<<1, 1024, 0, s>>>(d);
+  k_allbonds<<<c->grid_bead, 256, 0, s>>>(d);
+  k_rebuild<<<c->grid_seg, 256, 0, s>>>(d, c->d_rt, 1);
   CUDA_TRY(c, cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * R, s));
   CUDA_TRY(c, cudaGetLastError());
   st = device_status(c);
@@ -736,7 +751,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
 
   // ---- profiling events and graphs
   if (c->profile) {
-    c->names_step = {"setup", "bead", "cells", "candidates", "match", "edit", "newbonds", "purge", "rebuild"};
+    c->names_step = {"setup", "bead", "cells", "candidates", "match", "edit", "purge", "rebuild"};
     c->names_forces = {"bond_forces", "angle_dihedral_forces"};
     c->ev_step.resize(c->names_step.size() + 1);
     c->ev_forces.resize(c->names_forces.size() + 1);

@@ -80,6 +80,7 @@ struct Counters {
   int n_nbl;
   int n_ovf;
   int ticket[8];
+  int done[4];                 // blocks finished (last-block hand-off)
   unsigned bar[2];
   int rounds_done;
   int round_matched[MAX_ROUNDS];
@@ -108,10 +109,16 @@ struct Dev {
   int4* dih;                   // replica r owns [18*off[r], 18*off[r+1]); w = d | type << 28
   int* n_ang;                  // [R]
   int* n_dih;                  // [R]
-  int* kept_ang;               // [R]
-  int* kept_dih;               // [R]
-  int* added_ang;              // [R]
+  int* m_ang;                  // [R] records removed in this call
+  int* m_dih;                  // [R]
+  int* added_ang;              // [R] records added in this call
   int* added_dih;              // [R]
+  int* fillc;                  // [4R] hole / mover arrival counters of k_fill
+  int* fill_items;             // [R]
+  int* rm_ang;                 // [6N] positions of removed records (replica regions as ang)
+  int* rm_dih;                 // [18N]
+  int* pr_ang;                 // [6N] rendezvous words of k_fill
+  int* pr_dih;                 // [18N]
   long long* n_bonds;          // [R]
   // per-call scratch
   Counters* cnt;
@@ -141,12 +148,10 @@ struct Dev {
   int* round_hit;              // [2*R]
   int4* rem;                   // [N] partners whose bond was removed or retyped
   int2* newp;                  // [N] formed partner, retyped partner
-  int4* nbl;                   // new-bond list (u, v, replica, 0), u < v
-  int* nbl_count;              // [R]
-  int* nbl_first;              // [R]
-  int* tb_ang;                 // [R+1] tile bases
+  int4* nbl;                   // new-bond list (u, v, replica, 0), u < v, unordered
+  int* tb_ang;                 // [R+1] purge tile bases
   int* tb_dih;                 // [R+1]
-  int* tb_nb;                  // [R+1]
+  int* tb_fill;                // [R+1] k_fill tile bases
   int* tb_beads;               // [R+1] (static)
   int* tb_fang;                // [R+1] force tile bases of the final lists
   int* tb_fdih;                // [R+1]
@@ -155,11 +160,7 @@ struct Dev {
   long long small_words;
   unsigned long long* status_all;  // all look-back status words, zeroed by k_setup
   long long status_words;
-  unsigned long long* st_scan; // look-back status words
-  unsigned long long* st_nb;
-  unsigned long long* st_pa;
-  unsigned long long* st_pd;
-  unsigned long long* st_rb;
+  unsigned long long* st_scan; // look-back status words of the cell scan
   long long* stats;            // [R*NSTAT]
   double* ev_acc;              // [R*7]
 };
@@ -242,6 +243,20 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // Once any device error is recorded (a bounded wait gave up, a capacity or
 // consistency check failed, a bad position), every later kernel of the call
 // returns at once, so no kernel consumes half-built data.
+// Programmatic dependent launch.  Kernels of a call are launched with
+// programmatic stream serialization, so the next kernel's blocks may be
+// scheduled while this one drains.  Every kernel first waits for its
+// predecessor to complete and flush (griddepcontrol.wait returns at once for
+// a kernel launched without the attribute), then lets its own successor be
+// scheduled; the successor's blocks only take resources this kernel's
+// blocks leave free, and they wait in turn before touching memory, so each
+// kernel still sees everything all earlier kernels wrote.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ bool aborted(const unsigned* err) { return *(const volatile unsigned*)err != 0u; }
 
 // ---------------------------------------------------------------------------

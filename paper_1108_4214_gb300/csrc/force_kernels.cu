@@ -134,6 +134,7 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
 constexpr int BEAD_PER_THREAD = BEAD_TILE / 256;
 
 __global__ void __launch_bounds__(256) k_bond_forces(Dev d, FF ff) {
+  pdl_enter();
   if (aborted(d.err)) return;
   const int4* __restrict__ pos = d.args->pos;
   float4* __restrict__ force = d.args->force;
@@ -212,6 +213,7 @@ constexpr int DIH_PER_THREAD = FORCE_TILE / 256;
 // Angles and dihedrals in one launch: items [0, tb_fang[R]) are angle tiles,
 // the rest dihedral tiles; both add their forces with float4 atomics.
 __global__ void __launch_bounds__(256) k_angle_dihedral_forces(Dev d, FF ff) {
+  pdl_enter();
   if (aborted(d.err)) return;
   const int4* __restrict__ pos = d.args->pos;
   float4* force = d.args->force;
@@ -356,6 +358,7 @@ __global__ void __launch_bounds__(256) k_angle_dihedral_forces(Dev d, FF ff) {
 // copy the reduced energy / virial out and clear the accumulators for the
 // next force call
 __global__ void k_ev_out(Dev d) {
+  pdl_enter();
   if (aborted(d.err)) return;
   double* out = d.args->ev;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 7 * d.R; k += gridDim.x * blockDim.x) {

@@ -7,7 +7,7 @@
 namespace dynbond {
 
 constexpr int PURGE_TILE = 4096;   // 512 threads x 8 records
-constexpr int REBUILD_TILE = 256;  // new bonds per tile, one per thread
+constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
 constexpr int BEAD_TILE = 512;     // beads per force work item (2 per thread)
 
@@ -23,11 +23,10 @@ __global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_match(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_edit(Dev d, const RuleTab* __restrict__ rtp);
-__global__ void k_newbonds(Dev d, int mode);
-__global__ void k_tiles(Dev d, int mode);
+__global__ void k_allbonds(Dev d);
 __global__ void k_purge(Dev d);
+__global__ void k_fill(Dev d);
 __global__ void k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new);
-__global__ void k_finalize(Dev d);
 __global__ void k_setup(Dev d);
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
                            int set_pos, int set_force);

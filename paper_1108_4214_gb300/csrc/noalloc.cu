@@ -41,9 +41,6 @@ __device__ __forceinline__ float3 na_rel(const int4& a, const int4& b, int L) {
                      (float)wrap_dx(a.z - b.z, L) * q);
 }
 __device__ __forceinline__ float na_dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 na_cross(float3 a, float3 b) {
-  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
 
 // Per-lane FP64 accumulation of one replica's energy and virial; flushed
 // with atomics to the scratch when the lane moves to another replica.

@@ -10,13 +10,12 @@
 //   k_match       rounds of mutual nomination for creation and breakage at
 //                 once (step 4), cooperative launch with a bounded barrier
 //   k_edit        trials, kill / break / convert / form applied to each
-//                 bead's own bond slots (steps 5, 7, 8)
-//   k_newbonds    ordered list of the bonds formed or retyped
-//   k_tiles       per-replica tile bases of the segmented passes
-//   k_purge       in-place ordered compaction of the angle / dihedral lists,
-//                 dropping records on removed or retyped bonds (step 6)
-//   k_rebuild     typed records of every path through a new bond (step 9)
-//   k_finalize    per-replica counts and statistics (step 10)
+//                 bead's own bond slots (steps 5, 7, 8); lists the new bonds
+//   k_purge       positions of the angle / dihedral records on removed or
+//                 retyped bonds (step 6)
+//   k_fill        surviving tail records moved into the holes: dense lists
+//   k_rebuild     typed records of every path through a new bond (step 9);
+//                 per-replica counts and statistics (step 10)
 #include "common.cuh"
 #include "kernels.h"
 
@@ -25,7 +24,6 @@ namespace dynbond {
 constexpr int PURGE_PER_THREAD = 8;  // records per thread; PURGE_TILE / 8 threads per block
 constexpr int SCAN_PER_THREAD = 32;  // cells per thread in the histogram scan
 constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
-constexpr int NB_WORDS = 2;  // bitmap words (64 beads) per thread in the new-bond list
 
 __device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
   if (v) atomicAdd((unsigned long long*)&d.stats[(long long)r * NSTAT + k], (unsigned long long)v);
@@ -46,6 +44,7 @@ __device__ __forceinline__ int warp_alloc(int* counter, int want) {
 // k_bead
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
   const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
@@ -136,6 +135,7 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
 // k_scan_cells: in-place exclusive scan of the cell histogram
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
+  pdl_enter();
   if (aborted(d.err)) return;
   __shared__ long long sh[33];
   __shared__ long long s_excl;
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
 }
 
 __global__ void __launch_bounds__(256) k_scatter(Dev d) {
+  pdl_enter();
   if (aborted(d.err)) return;
   const int4* __restrict__ pos = d.args->pos;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -434,6 +435,7 @@ __device__ __forceinline__ void load_type_masks(const RuleTab& rt, unsigned* s_m
 }
 
 __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
   if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
@@ -478,6 +480,7 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __rest
 // Exact path for beads with more than MAXC candidates: count, allocate,
 // write, then sort the bead's list by (d2, partner) in place.
 __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
   if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
@@ -525,6 +528,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_wait();  // cooperative: its successor is scheduled only when it ends
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b;
@@ -640,227 +644,207 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// k_edit: trials and in-place edit of each bead's own slots
+// k_edit: trials and in-place edit of each bead's own slots.  Each warp owns
+// EDIT_WORDS bitmap words (32 beads each), compacts the beads marked
+// creation- or breakage-active there and edits only those, 32 at a time.
 // ---------------------------------------------------------------------------
+constexpr int EDIT_WORDS = 8;
+
+// position of the n-th (from 0) set bit of m; n < popc(m)
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    unsigned lo = m & ((1u << w) - 1u);
+    int c = __popc(lo);
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = lo;
+    }
+  }
+  return pos;
+}
+
+struct EditOut {
+  bool dirty = false, fresh = false;
+  int form_hi = -1, conv_hi = -1;
+  unsigned n_killed = 0, n_broken = 0, n_conv = 0, n_formed = 0;
+};
+
+__device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long long i, int r, bool ca, bool ba,
+                                          EditOut& o) {
+  const long long N = d.N;
+  uint4 s = d.slots[i];
+  unsigned removed = 0, changed = 0;
+  int conv_partner = -1, form_partner = -1, form_type = 0;
+  if (ba) {
+    removed = d.killmask[i];
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q)
+      if ((removed >> q) & 1u) o.n_killed += s_partner(s_get(s, q)) > i;
+    int j = d.brk_len[i] ? d.mate[N + i] : -1;
+    if (j >= 0) {
+      int4 ent = d.brk[4 * i + d.ptr[N + i]];
+      int k = ent.y;
+      int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
+      if (trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k])) {
+        int q = 0;
+        while (q < SLOTS && s_partner(s_get(s, q)) != j) ++q;
+        bool killed = q < SLOTS && ((removed >> q) & 1u);
+        if (q == SLOTS) {
+          atomicOr(d.err, ERR_INTERNAL);
+        } else if (rt.kind[k] == DYNBOND_BREAKBOND) {
+          removed |= 1u << q;
+          o.n_broken += !killed && j > i;
+        } else if (!killed) {
+          changed |= 1u << q;
+          s_set(s, q, ((unsigned)j << 4) | (unsigned)rt.type2[k]);
+          conv_partner = j;
+          o.n_conv += j > i;
+        }
+      }
+    }
+  }
+  if (ca) {
+    int j = d.mate[i];
+    if (j >= 0) {
+      int4 ent = d.cand[d.cand_start[i] + d.ptr[i]];
+      int k = ent.y & 0xFF;
+      int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
+      if (trial(d, rt, a, b, r, TAG_FORM, d.T_form[(long long)r * MAXR + k])) {
+        form_partner = j;
+        form_type = (ent.y >> 8) & 15;
+        o.n_formed += j > i;
+      }
+    }
+  }
+  if (!(removed | changed | (unsigned)(form_partner >= 0))) return;
+  uint4 ns = make_uint4(0, 0, 0, 0);
+  int4 rp = make_int4(-1, -1, -1, -1);
+  int nk = 0, nr = 0;
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    unsigned v = s_get(s, q);
+    if (!v) continue;
+    if (((removed | changed) >> q) & 1u) {
+      if (nr == 0) rp.x = s_partner(v);
+      else if (nr == 1) rp.y = s_partner(v);
+      else if (nr == 2) rp.z = s_partner(v);
+      else rp.w = s_partner(v);
+      ++nr;
+      if ((removed >> q) & 1u) continue;
+    }
+    s_set(ns, nk++, v);
+  }
+  if (form_partner >= 0) {
+    if (nk >= SLOTS) atomicOr(d.err, ERR_SLOTS);
+    else s_set(ns, nk++, ((unsigned)form_partner << 4) | (unsigned)form_type);
+  }
+  d.slots[i] = ns;
+  o.dirty = (removed | changed) != 0;
+  o.fresh = form_partner >= 0 || conv_partner >= 0;
+  if (o.dirty) d.rem[i] = rp;
+  if (o.fresh) d.newp[i] = make_int2(form_partner, conv_partner);
+  if (form_partner > i) o.form_hi = form_partner;
+  if (conv_partner > i) o.conv_hi = conv_partner;
+}
+
 __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
-  const long long N = d.N;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long W = d.W;
   const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
-    long long i = base + threadIdx.x;
-    bool valid = i < N;
-    bool dirty = false, fresh = false;
-    int r = 0;
-    unsigned n_killed = 0, n_broken = 0, n_conv = 0, n_formed = 0;
-    if (valid) {
-      unsigned wca = d.bm_ca[i >> 5], wba = d.bm_ba[i >> 5];
-      bool ca = (wca >> (i & 31)) & 1u, ba = (wba >> (i & 31)) & 1u;
-      if (ca || ba) {
+  const long long nchunks = (W + EDIT_WORDS - 1) / EDIT_WORDS;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long ch = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += wstride) {
+    const long long w0 = ch * EDIT_WORDS;
+    // lane k < EDIT_WORDS holds word w0 + k of both activity bitmaps
+    unsigned wca = 0, wba = 0;
+    if (lane < EDIT_WORDS && w0 + lane < W) {
+      // only bits of beads below N: the last word may extend past the end
+      const long long b0 = 32 * (w0 + lane);
+      const unsigned vmask = b0 + 32 <= d.N ? FULL : (b0 >= d.N ? 0u : (1u << (d.N - b0)) - 1u);
+      wca = d.bm_ca[w0 + lane] & vmask;
+      wba = d.bm_ba[w0 + lane] & vmask;
+    }
+    const unsigned act = wca | wba;
+    const int cnt = __popc(act);
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(FULL, incl, 31);
+    unsigned out_dirty = 0, out_new = 0;  // lane k: output word w0 + k
+    for (int r0 = 0; r0 < total; r0 += 32) {
+      // lane takes active bead number r0 + lane of the chunk
+      const int want = r0 + lane;
+      int k = 0;
+#pragma unroll
+      for (int q = 0; q < EDIT_WORDS; ++q) k += __shfl_sync(FULL, incl, q) <= want;
+      const unsigned a_k = __shfl_sync(FULL, act, k & (EDIT_WORDS - 1));
+      const unsigned ca_k = __shfl_sync(FULL, wca, k & (EDIT_WORDS - 1));
+      const unsigned ba_k = __shfl_sync(FULL, wba, k & (EDIT_WORDS - 1));
+      const int prev = __shfl_sync(FULL, incl, (k - 1) & (EDIT_WORDS - 1));  // every lane shuffles
+      const int before = k ? prev : 0;
+      EditOut o;
+      int r = 0, bit = 0;
+      long long i = 0;
+      bool valid = want < total;
+      if (valid) {
+        bit = nth_set_bit(a_k, want - before);
+        i = 32 * (w0 + k) + bit;
+        if (i >= d.N) {  // cannot happen with the masked words; never touch memory past N
+          atomicOr(d.err, ERR_INTERNAL);
+          valid = false;
+        }
+      }
+      if (valid) {
         r = d.rep[i];
-        uint4 s = d.slots[i];
-        unsigned removed = 0, changed = 0;
-        int conv_partner = -1, form_partner = -1, form_type = 0;
-        if (ba) {
-          removed = d.killmask[i];
-#pragma unroll
-          for (int q = 0; q < SLOTS; ++q)
-            if ((removed >> q) & 1u) n_killed += s_partner(s_get(s, q)) > i;
-          int j = d.brk_len[i] ? d.mate[N + i] : -1;
-          if (j >= 0) {
-            int4 ent = d.brk[4 * i + d.ptr[N + i]];
-            int k = ent.y;
-            int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
-            if (trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k])) {
-              int q = 0;
-              while (q < SLOTS && s_partner(s_get(s, q)) != j) ++q;
-              bool killed = q < SLOTS && ((removed >> q) & 1u);
-              if (q == SLOTS) {
-                atomicOr(d.err, ERR_INTERNAL);
-              } else if (rt.kind[k] == DYNBOND_BREAKBOND) {
-                removed |= 1u << q;
-                n_broken += !killed && j > i;
-              } else if (!killed) {
-                changed |= 1u << q;
-                s_set(s, q, ((unsigned)j << 4) | (unsigned)rt.type2[k]);
-                conv_partner = j;
-                n_conv += j > i;
-              }
-            }
+        edit_bead(d, rt, i, r, (ca_k >> bit) & 1u, (ba_k >> bit) & 1u, o);
+      }
+      stat_add_warp(d.stats, r, ST_KILLED, o.n_killed);
+      stat_add_warp(d.stats, r, ST_BROKEN, o.n_broken);
+      stat_add_warp(d.stats, r, ST_CONVERTED, o.n_conv);
+      stat_add_warp(d.stats, r, ST_FORMED, o.n_formed);
+      {
+        int dv = (int)o.n_formed - (int)o.n_broken - (int)o.n_killed;
+        if (__ballot_sync(FULL, dv != 0)) {
+          unsigned grp = __match_any_sync(FULL, r);
+          if (grp == FULL) {
+            int sum = (int)__reduce_add_sync(FULL, (unsigned)dv);
+            if (lane == 0 && sum) atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)sum);
+          } else if (dv) {
+            atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)dv);
           }
-        }
-        if (ca) {
-          int j = d.mate[i];
-          if (j >= 0) {
-            int4 ent = d.cand[d.cand_start[i] + d.ptr[i]];
-            int k = ent.y & 0xFF;
-            int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
-            if (trial(d, rt, a, b, r, TAG_FORM, d.T_form[(long long)r * MAXR + k])) {
-              form_partner = j;
-              form_type = (ent.y >> 8) & 15;
-              n_formed += j > i;
-            }
-          }
-        }
-        if (removed | changed | (unsigned)(form_partner >= 0)) {
-          uint4 ns = make_uint4(0, 0, 0, 0);
-          int4 rp = make_int4(-1, -1, -1, -1);
-          int nk = 0, nr = 0;
-#pragma unroll
-          for (int q = 0; q < SLOTS; ++q) {
-            unsigned v = s_get(s, q);
-            if (!v) continue;
-            if ((removed >> q) & 1u) {
-              if (nr == 0) rp.x = s_partner(v);
-              else if (nr == 1) rp.y = s_partner(v);
-              else if (nr == 2) rp.z = s_partner(v);
-              else rp.w = s_partner(v);
-              ++nr;
-              continue;
-            }
-            if ((changed >> q) & 1u) {
-              if (nr == 0) rp.x = s_partner(v);
-              else if (nr == 1) rp.y = s_partner(v);
-              else if (nr == 2) rp.z = s_partner(v);
-              else rp.w = s_partner(v);
-              ++nr;
-            }
-            s_set(ns, nk++, v);
-          }
-          if (form_partner >= 0) {
-            if (nk >= SLOTS) atomicOr(d.err, ERR_SLOTS);
-            else s_set(ns, nk++, ((unsigned)form_partner << 4) | (unsigned)form_type);
-          }
-          d.slots[i] = ns;
-          dirty = (removed | changed) != 0;
-          fresh = form_partner >= 0 || conv_partner >= 0;
-          if (dirty) d.rem[i] = rp;
-          if (fresh) d.newp[i] = make_int2(form_partner, conv_partner);
         }
       }
-    }
-    stat_add_warp(d.stats, r, ST_KILLED, n_killed);
-    stat_add_warp(d.stats, r, ST_BROKEN, n_broken);
-    stat_add_warp(d.stats, r, ST_CONVERTED, n_conv);
-    stat_add_warp(d.stats, r, ST_FORMED, n_formed);
-    {
-      int dv = (int)n_formed - (int)n_broken - (int)n_killed;
-      if (__ballot_sync(FULL, dv != 0)) {
-        unsigned grp = __match_any_sync(FULL, r);
-        if (grp == FULL) {
-          int sum = (int)__reduce_add_sync(FULL, (unsigned)dv);
-          if (lane == 0 && sum) atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)sum);
-        } else if (dv) {
-          atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)dv);
+      // output bitmap words: OR of the bits of the lanes in each word
+      const unsigned bit_i = valid ? 1u << (i & 31) : 0u;
+#pragma unroll
+      for (int q = 0; q < EDIT_WORDS; ++q) {
+        unsigned dq = __reduce_or_sync(FULL, (k == q && o.dirty) ? bit_i : 0u);
+        unsigned nq = __reduce_or_sync(FULL, (k == q && o.fresh) ? bit_i : 0u);
+        if (lane == q) {
+          out_dirty |= dq;
+          out_new |= nq;
         }
       }
+      // new-bond list for the rebuild: bonds formed or retyped, listed by
+      // their lower end
+      int nb_form = o.form_hi >= 0, nb_conv = o.conv_hi >= 0;
+      int at = warp_alloc(&d.cnt->n_nbl, nb_form + nb_conv);
+      if (nb_form) d.nbl[at++] = make_int4((int)i, o.form_hi, r, 0);
+      if (nb_conv) d.nbl[at] = make_int4((int)i, o.conv_hi, r, 0);
     }
-    unsigned md = __ballot_sync(FULL, dirty), mn = __ballot_sync(FULL, fresh);
-    if (lane == 0 && valid) {
-      d.bm_dirty[i >> 5] = md;
-      d.bm_new[i >> 5] = mn;
+    if (lane < EDIT_WORDS && w0 + lane < W) {
+      d.bm_dirty[w0 + lane] = out_dirty;
+      d.bm_new[w0 + lane] = out_new;
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_newbonds: ordered list of new bonds (u < v).  mode 0: bonds formed or
-// retyped in this call; mode 1: every bond (initial typing of the system).
-// ---------------------------------------------------------------------------
-// Owned new bonds of bead u: partners above u (mode 0: formed / retyped in
-// this call; mode 1: every bond).
-__device__ __forceinline__ int owned_new(const Dev& d, long long u, int mode, int* out) {
-  int n = 0;
-  if (mode == 0) {
-    int2 np = d.newp[u];
-    if (np.x > u) out[n++] = np.x;
-    if (np.y > u) out[n++] = np.y;
-  } else {
-    uint4 s = d.slots[u];
-#pragma unroll
-    for (int q = 0; q < SLOTS; ++q) {
-      int v = s_partner(s_get(s, q));
-      if (v > u) out[n++] = v;
-    }
-  }
-  return n;
-}
-
-__global__ void __launch_bounds__(256) k_newbonds(Dev d, int mode) {
-  if (aborted(d.err)) return;
-  __shared__ long long sh[33];
-  __shared__ long long s_excl, s_tile;
-  const long long N = d.N;
-  const long long W = (N + 31) / 32;
-  const long long words_per_tile = (long long)blockDim.x * NB_WORDS;
-  const long long ntiles = (W + words_per_tile - 1) / words_per_tile;
-  while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[1], 1);
-    __syncthreads();
-    long long t = s_tile;
-    if (t >= ntiles) break;
-    long long w0 = t * words_per_tile + (long long)threadIdx.x * NB_WORDS;
-    unsigned bits[NB_WORDS];
-    long long cnt = 0;
-#pragma unroll
-    for (int k = 0; k < NB_WORDS; ++k) {
-      long long w = w0 + k;
-      bits[k] = 0;
-      if (w >= W) continue;
-      if (mode == 0) {
-        bits[k] = d.bm_new[w];
-      } else {
-        long long hi = min(32ll, N - 32 * w);
-        bits[k] = hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
-      }
-      unsigned b = bits[k];
-      while (b) {
-        int l = __ffs(b) - 1;
-        b &= b - 1;
-        int tmp[SLOTS];
-        cnt += owned_new(d, 32 * w + l, mode, tmp);
-      }
-    }
-    long long tot;
-    long long ex = block_excl_scan(cnt, sh, &tot);
-    if (threadIdx.x < 32) {
-      long long x = lookback(d.st_nb, t, 0, (unsigned long long)tot, d.spin_limit, d.err);
-      if (threadIdx.x == 0) s_excl = x;
-    }
-    __syncthreads();
-    if (s_excl < 0) return;
-    long long at = s_excl + ex;
-    int r0 = w0 < W ? d.rep[32 * w0] : 0;
-    unsigned n0 = 0;
-#pragma unroll
-    for (int k = 0; k < NB_WORDS; ++k) {
-      unsigned b = bits[k];
-      while (b) {
-        int l = __ffs(b) - 1;
-        b &= b - 1;
-        long long u = 32 * (w0 + k) + l;
-        int tmp[SLOTS];
-        int nr = owned_new(d, u, mode, tmp);
-        if (!nr) continue;
-        int r = d.rep[u];
-        for (int q = 0; q < nr; ++q) d.nbl[at++] = make_int4((int)u, tmp[q], r, 0);
-        if (r == r0) n0 += nr;
-        else atomicAdd(&d.nbl_count[r], nr);
-      }
-    }
-    count_add_warp(d.nbl_count, r0, n0);
-    if (t == ntiles - 1 && threadIdx.x == blockDim.x - 1) d.cnt->n_nbl = (int)at;
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// k_tiles: per-replica tile bases (one block)
-//   mode 0: purge tiles of the angle / dihedral lists
-//   mode 1: first index and tiles of each replica's new bonds
-//   mode 2: force tiles of the angle / dihedral lists
-// ---------------------------------------------------------------------------
+// per-replica tile bases: base[r] = tiles of replicas before r, base[R] = all
 __device__ void block_tile_bases(const int* count, int R, int per_tile, int* base, int* first) {
   __shared__ long long sh[33];
   __shared__ long long carry, carry2;
@@ -890,21 +874,69 @@ __device__ void block_tile_bases(const int* count, int R, int per_tile, int* bas
   if (threadIdx.x == 0) base[R] = (int)carry;
 }
 
-__global__ void k_tiles(Dev d, int mode) {
+// ---------------------------------------------------------------------------
+// Interaction-list maintenance (Appendix steps 6 and 9).  The order of the
+// records inside a replica's angle / dihedral list carries no meaning (the
+// exported topology is sorted), so the lists stay dense without any ordered
+// scan or look-back chain:
+//   k_allbonds  every bond (u, v), u < v, of the initial graph (creation)
+//   k_purge     lists the position of every record holding a bond removed or
+//               retyped in this call: m of the replica's n records go
+//   k_fill      moves the surviving records of the tail [n - m, n) into the
+//               holes below n - m; the i-th hole and the i-th mover to arrive
+//               meet at rendezvous word i, and the second one moves the record
+//   k_rebuild   appends the typed records of every path through a new bond
+//               after the n - m kept ones; its last block finalizes the
+//               counts, the statistics and the force tiles
+// New bonds are listed by k_edit (or k_allbonds) as (u, v, replica, 0).
+// ---------------------------------------------------------------------------
+
+// One slot per lane that wants one, one atomic per warp (all lanes active).
+__device__ __forceinline__ int warp_alloc1(int* counter, bool want) {
+  const int lane = threadIdx.x & 31;
+  unsigned m = __ballot_sync(FULL, want);
+  int base = 0;
+  if (lane == 0 && m) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(FULL, base, 0);
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
+// Last block of the grid to get here (after all its threads' writes are
+// visible device-wide); the caller then finishes the per-replica work alone.
+__device__ __forceinline__ bool last_block(int* done) {
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+__global__ void __launch_bounds__(256) k_allbonds(Dev d) {
+  pdl_enter();
   if (aborted(d.err)) return;
-  if (mode == 0) {
-    block_tile_bases(d.n_ang, d.R, PURGE_TILE, d.tb_ang, nullptr);
-    __syncthreads();
-    block_tile_bases(d.n_dih, d.R, PURGE_TILE, d.tb_dih, nullptr);
-  } else if (mode == 1) {
-    block_tile_bases(d.nbl_count, d.R, REBUILD_TILE, d.tb_nb, d.nbl_first);
+  const long long N = d.N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
+    long long u = base + threadIdx.x;
+    int out[SLOTS], n = 0, r = 0;
+    if (u < N) {
+      uint4 su = d.slots[u];
+      r = d.rep[u];
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        int v = s_partner(s_get(su, q));
+        if (v > u) out[n++] = v;
+      }
+    }
+    int at = warp_alloc(&d.cnt->n_nbl, n);
+    for (int q = 0; q < n; ++q) d.nbl[at + q] = make_int4((int)u, out[q], r, 0);
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_purge: drop every angle / dihedral containing a bond removed or retyped
-// in this call (Appendix step 6); ordered, in place, segment per replica.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ bool is_dirty(const Dev& d, int x) { return (d.bm_dirty[x >> 5] >> (x & 31)) & 1u; }
 
 __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
@@ -913,88 +945,113 @@ __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
   return rp.x == b || rp.y == b || rp.z == b || rp.w == b;
 }
 
+// Does the record hold a bond removed or retyped in this call (step 6)?
+__device__ __forceinline__ bool record_gone(const Dev& d, const int4& v, bool dih) {
+  if (!dih) return bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z);
+  return bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z) || bond_gone(d, v.z, v.w & 0x0FFFFFFF);
+}
+
 __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) {
+  pdl_enter();
   if (aborted(d.err)) return;
-  __shared__ long long s_excl, s_tile;
-  __shared__ int s_tot;
-  __shared__ int s_cnt[PURGE_PER_THREAD][32];
-  __shared__ int s_off[PURGE_PER_THREAD][32];
   const int R = d.R;
   const int na_tiles = d.tb_ang[R];
   const int ntiles = na_tiles + d.tb_dih[R];
-  const int nw = blockDim.x >> 5;
-  while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[2], 1);
-    __syncthreads();
-    int tg = (int)s_tile;
-    if (tg >= ntiles) break;
-    // tiles [0, na_tiles) compact the angle lists, the rest the dihedral lists
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int tg = blockIdx.x; tg < ntiles; tg += gridDim.x) {
+    // tiles [0, na_tiles) scan the angle lists, the rest the dihedral lists
     const bool dih = tg >= na_tiles;
     const int t = dih ? tg - na_tiles : tg;
-    int4* recs = dih ? d.dih : d.ang;
     const int* tb = dih ? d.tb_dih : d.tb_ang;
-    unsigned long long* status = dih ? d.st_pd : d.st_pa;
-    int r = find_seg(tb, R, t);
-    int lt = t - tb[r];
-    long long base = (dih ? 18 : 6) * d.off[r];
-    int n = (dih ? d.n_dih : d.n_ang)[r];
-    int beg = lt * PURGE_TILE + threadIdx.x;
+    const int r = find_seg(tb, R, t);
+    const long long base = (dih ? 18 : 6) * d.off[r];
+    const int4* recs = (dih ? d.dih : d.ang) + base;
+    const int n = (dih ? d.n_dih : d.n_ang)[r];
+    const int beg = (t - tb[r]) * PURGE_TILE + threadIdx.x;
     int4 v[PURGE_PER_THREAD];
-    unsigned keep = 0;
 #pragma unroll
     for (int k = 0; k < PURGE_PER_THREAD; ++k) {
       int idx = beg + k * (int)blockDim.x;
-      if (idx >= n) continue;
-      v[k] = recs[base + idx];
-      bool gone;
-      if (!dih) {
-        gone = bond_gone(d, v[k].x, v[k].y) || bond_gone(d, v[k].y, v[k].z);
-      } else {
-        int dd = v[k].w & 0x0FFFFFFF;
-        gone = bond_gone(d, v[k].x, v[k].y) || bond_gone(d, v[k].y, v[k].z) || bond_gone(d, v[k].z, dd);
-      }
-      if (!gone) keep |= 1u << k;
+      if (idx < n) v[k] = recs[idx];
     }
-    // ordered compaction: records are numbered k-major within the tile
-    // (index = k * blockDim + thread), so scan over that order
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned bal[PURGE_PER_THREAD];
+    int tot = 0;
 #pragma unroll
     for (int k = 0; k < PURGE_PER_THREAD; ++k) {
-      bal[k] = __ballot_sync(FULL, (keep >> k) & 1u);
-      if (lane == 0) s_cnt[k][wid] = __popc(bal[k]);
+      int idx = beg + k * (int)blockDim.x;
+      bal[k] = __ballot_sync(FULL, idx < n && record_gone(d, v[k], dih));
+      tot += __popc(bal[k]);
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      // warp 0: exclusive offsets over (k, warp) order, then the look-back
-      int acc = 0;
-      for (int k = 0; k < PURGE_PER_THREAD; ++k) {
-        int c = lane < nw ? s_cnt[k][lane] : 0;
-        int inc = warp_incl_scan(c);
-        if (lane < nw) s_off[k][lane] = acc + inc - c;
-        acc += __shfl_sync(FULL, inc, 31);
-      }
-      long long x = lookback(status, t, tb[r], (unsigned long long)acc, d.spin_limit, d.err);
-      if (lane == 0) {
-        s_tot = acc;
-        s_excl = x;
-        if (x >= 0 && lt == tb[r + 1] - tb[r] - 1) (dih ? d.kept_dih : d.kept_ang)[r] = (int)(x + acc);
-      }
-    }
-    __syncthreads();
-    if (s_excl < 0) return;
-    long long excl = s_excl;
-    // nothing moves when no record before or inside this tile was dropped
-    bool full = excl == (long long)lt * PURGE_TILE && s_tot == min(PURGE_TILE, n - lt * PURGE_TILE);
-    if (!full) {
+    if (!tot) continue;
+    int wbase = 0;
+    if (lane == 0) wbase = atomicAdd((dih ? d.m_dih : d.m_ang) + r, tot);
+    wbase = __shfl_sync(FULL, wbase, 0);
+    int* rm = (dih ? d.rm_dih : d.rm_ang) + base;
+    int* pr = (dih ? d.pr_dih : d.pr_ang) + base;
 #pragma unroll
-      for (int k = 0; k < PURGE_PER_THREAD; ++k) {
-        if (!((keep >> k) & 1u)) continue;
-        int rank = s_off[k][wid] + __popc(bal[k] & ((1u << lane) - 1));
-        recs[base + excl + rank] = v[k];
+    for (int k = 0; k < PURGE_PER_THREAD; ++k) {
+      if ((bal[k] >> lane) & 1u) {
+        int at = wbase + __popc(bal[k] & lt_mask);
+        rm[at] = beg + k * (int)blockDim.x;
+        pr[at] = 0;  // rendezvous word of k_fill
+      }
+      wbase += __popc(bal[k]);
+    }
+  }
+  // the last block sizes k_fill: per replica, m holes-or-not and m tail
+  // positions of each list
+  if (!last_block(&d.cnt->done[0])) return;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) d.fill_items[r] = 2 * (ld_cg(d.m_ang + r) + ld_cg(d.m_dih + r));
+  __syncthreads();
+  block_tile_bases(d.fill_items, R, FILL_TILE, d.tb_fill, nullptr);
+}
+
+__global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  const int R = d.R;
+  const int ntiles = d.tb_fill[R];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int r = find_seg(d.tb_fill, R, t);
+    const int k = (t - d.tb_fill[r]) * FILL_TILE + threadIdx.x;
+    const int ma = d.m_ang[r], md = d.m_dih[r];
+    // item k: [0, ma) removed angles, [ma, 2 ma) the angle tail, then the
+    // same for the dihedrals
+    const bool dih = k >= 2 * ma;
+    const int kk = dih ? k - 2 * ma : k;
+    const int m = dih ? md : ma;
+    const long long base = (dih ? 18 : 6) * d.off[r];
+    int4* recs = (dih ? d.dih : d.ang) + base;
+    const int keep = (dih ? d.n_dih : d.n_ang)[r] - m;
+    int role = -1, pos = 0;  // role 0 / 1: angle hole / mover, 2 / 3: dihedral
+    if (kk < m) {
+      int p = (dih ? d.rm_dih : d.rm_ang)[base + kk];
+      if (p < keep) {
+        role = dih ? 2 : 0;
+        pos = p;
+      }
+    } else if (kk < 2 * m) {
+      int p = keep + (kk - m);
+      if (!record_gone(d, recs[p], dih)) {
+        role = dih ? 3 : 1;
+        pos = p;
       }
     }
-    __syncthreads();
+    int at = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int a = warp_alloc1(&d.fillc[4 * r + q], role == q);
+      if (role == q) at = a;
+    }
+    if (role < 0) continue;
+    int code = (role & 1) ? -(pos + 1) : pos + 1;
+    int other = atomicExch((dih ? d.pr_dih : d.pr_ang) + base + at, code);
+    if (other != 0) {  // both ends arrived: move the tail record into the hole
+      int hole = code > 0 ? code - 1 : other - 1;
+      int mover = code < 0 ? -code - 1 : -other - 1;
+      recs[hole] = recs[mover];
+    }
   }
 }
 
@@ -1110,57 +1167,85 @@ struct WriteEmit {
   }
 };
 
-__global__ void __launch_bounds__(REBUILD_TILE) k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new) {
-  if (aborted(d.err)) return;
-  const RuleTab& rt = *rtp;
-  __shared__ long long sh[33];
-  __shared__ long long s_excl, s_tile;
-  const int R = d.R;
-  const int ntiles = d.tb_nb[R];
-  Rebuild rb{d, rt, all_new};
-  while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&d.cnt->ticket[4], 1);
-    __syncthreads();
-    int t = (int)s_tile;
-    if (t >= ntiles) break;
-    int r = find_seg(d.tb_nb, R, t);
-    int lt = t - d.tb_nb[r];
-    int idx = lt * REBUILD_TILE + threadIdx.x;
-    bool valid = idx < d.nbl_count[r];
-    int4 e = valid ? d.nbl[d.nbl_first[r] + idx] : make_int4(0, 0, 0, 0);
-    CountEmit ce;
-    if (valid) rb.run(e.x, e.y, ce);
-    long long packed = (long long)ce.na | ((long long)ce.nd << 32);
-    long long tot;
-    long long ex = block_excl_scan(packed, sh, &tot);
-    if (threadIdx.x < 32) {
-      long long x = lookback(d.st_rb, t, d.tb_nb[r], (unsigned long long)tot, d.spin_limit, d.err);
-      if (threadIdx.x == 0) {
-        s_excl = x;
-        if (x >= 0 && lt == d.tb_nb[r + 1] - d.tb_nb[r] - 1) {
-          long long all = x + tot;
-          d.added_ang[r] = (int)(all & 0xFFFFFFFFll);
-          d.added_dih[r] = (int)(all >> 32);
-        }
+// Room for (na, nd) records after the kept ones of replica r: one atomic pair
+// per group of lanes with the same replica; offsets in lane order.
+__device__ __forceinline__ void reserve(const Dev& d, int r, int na, int nd, int* oa, int* od) {
+  const int lane = threadIdx.x & 31;
+  unsigned grp = __match_any_sync(FULL, r);
+  int pa = 0, pd = 0, ta = 0, td = 0;
+  for (int l = 0; l < 32; ++l) {
+    int a = __shfl_sync(FULL, na, l), b = __shfl_sync(FULL, nd, l);
+    if ((grp >> l) & 1u) {
+      ta += a;
+      td += b;
+      if (l < lane) {
+        pa += a;
+        pd += b;
       }
     }
-    __syncthreads();
-    if (s_excl < 0) return;
+  }
+  int leader = __ffs(grp) - 1;
+  int ba = 0, bd = 0;
+  if (lane == leader && r >= 0) {
+    if (ta) ba = atomicAdd(d.added_ang + r, ta);
+    if (td) bd = atomicAdd(d.added_dih + r, td);
+  }
+  *oa = __shfl_sync(FULL, ba, leader) + pa;
+  *od = __shfl_sync(FULL, bd, leader) + pd;
+}
+
+__global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  const RuleTab& rt = *rtp;
+  const Rebuild rb{d, rt, all_new};
+  const int n = d.cnt->n_nbl;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int i = base + threadIdx.x;
+    const bool valid = i < n;
+    int4 e = valid ? d.nbl[i] : make_int4(0, 0, -1, 0);
+    CountEmit ce;
+    if (valid) rb.run(e.x, e.y, ce);
+    int oa, od;
+    reserve(d, e.z, ce.na, ce.nd, &oa, &od);
     if (valid && (ce.na || ce.nd)) {
-      long long pre = s_excl + ex;
-      WriteEmit we{d.ang + 6 * d.off[r] + d.kept_ang[r] + (pre & 0xFFFFFFFFll),
-                   d.dih + 18 * d.off[r] + d.kept_dih[r] + (pre >> 32), d.ang + 6 * d.off[r + 1],
+      const int r = e.z;
+      WriteEmit we{d.ang + 6 * d.off[r] + (d.n_ang[r] - d.m_ang[r]) + oa,
+                   d.dih + 18 * d.off[r] + (d.n_dih[r] - d.m_dih[r]) + od, d.ang + 6 * d.off[r + 1],
                    d.dih + 18 * d.off[r + 1], d.err};
       rb.run(e.x, e.y, we);
     }
-    __syncthreads();
   }
+  // the last block: per-replica counts and statistics (step 10), then the
+  // force tiles of the final lists
+  if (!last_block(&d.cnt->done[1])) return;
+  for (int r = threadIdx.x; r < d.R; r += blockDim.x) {
+    long long* st = d.stats + (long long)r * NSTAT;
+    int ma = ld_cg(d.m_ang + r), md = ld_cg(d.m_dih + r);
+    int aa = ld_cg(d.added_ang + r), ad = ld_cg(d.added_dih + r);
+    int na = d.n_ang[r] - ma + aa, nd = d.n_dih[r] - md + ad;
+    st[ST_ANG_REMOVED] = ma;
+    st[ST_DIH_REMOVED] = md;
+    st[ST_ANG_ADDED] = aa;
+    st[ST_DIH_ADDED] = ad;
+    d.n_ang[r] = na;
+    d.n_dih[r] = nd;
+    st[ST_NBONDS] = __ldcg(d.n_bonds + r);
+    st[ST_NANGLES] = na;
+    st[ST_NDIHEDRALS] = nd;
+  }
+  __syncthreads();
+  block_tile_bases(d.n_ang, d.R, FORCE_TILE, d.tb_fang, nullptr);
+  __syncthreads();
+  block_tile_bases(d.n_dih, d.R, FORCE_TILE, d.tb_fdih, nullptr);
 }
 
 // Per-call setup (one launch): zero the counters, the cell histogram, the
 // creation-active bitmap, the per-replica scratch and the look-back status
 // words; block 0 also computes the purge tile bases from the list counts.
 __global__ void __launch_bounds__(1024) k_setup(Dev d) {
+  pdl_enter();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   int* cnt = reinterpret_cast<int*>(d.cnt);
@@ -1174,29 +1259,6 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
     __syncthreads();
     block_tile_bases(d.n_dih, d.R, PURGE_TILE, d.tb_dih, nullptr);
   }
-}
-
-// Per-replica list counts and statistics after the call, then the force tile
-// bases of the final lists (one block).
-__global__ void __launch_bounds__(1024) k_finalize(Dev d) {
-  if (aborted(d.err)) return;
-  for (int r = threadIdx.x; r < d.R; r += blockDim.x) {
-    long long* st = d.stats + (long long)r * NSTAT;
-    int na = d.kept_ang[r] + d.added_ang[r], nd = d.kept_dih[r] + d.added_dih[r];
-    st[ST_ANG_REMOVED] = d.n_ang[r] - d.kept_ang[r];
-    st[ST_DIH_REMOVED] = d.n_dih[r] - d.kept_dih[r];
-    st[ST_ANG_ADDED] = d.added_ang[r];
-    st[ST_DIH_ADDED] = d.added_dih[r];
-    d.n_ang[r] = na;
-    d.n_dih[r] = nd;
-    st[ST_NBONDS] = d.n_bonds[r];
-    st[ST_NANGLES] = na;
-    st[ST_NDIHEDRALS] = nd;
-  }
-  __syncthreads();
-  block_tile_bases(d.n_ang, d.R, FORCE_TILE, d.tb_fang, nullptr);
-  __syncthreads();
-  block_tile_bases(d.n_dih, d.R, FORCE_TILE, d.tb_fdih, nullptr);
 }
 
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,

@@ -188,14 +188,41 @@ def test_batched_ladder_parity_and_replica_independence():
     assert np.array_equal(mapped[np.lexsort(mapped.T[::-1])], bs)
 
 
-def test_graph_and_direct_launches_agree():
+@pytest.mark.parametrize("flags", ["NO_GRAPH", "NO_PDL", "NO_GRAPH|NO_PDL"])
+def test_graph_and_direct_launches_agree(flags):
     s = W.config1()
     D = dynbond()
+    f = 0
+    for name in flags.split("|"):
+        f |= getattr(D, "FLAG_" + name)
     a = D.Context(s)
-    b = D.Context(s, flags=D.FLAG_NO_GRAPH)
+    b = D.Context(s, flags=f)
     for k in range(3):
         p = torch.from_numpy(s.snapshot(k)).cuda()
         assert np.array_equal(a.step(p, k, stats=True), b.step(p, k, stats=True))
+    for x, y in zip(a.topology(), b.topology()):
+        assert np.array_equal(x, y)
+
+
+def test_dependent_launch_overlap_changes_nothing_at_scale():
+    """Programmatic dependent launch lets each kernel's blocks be scheduled
+    while its predecessor drains; on the 1M-bead system (multi-wave grids,
+    look-back chains, the cooperative matching) every call must give the
+    same topology, statistics and forces as strictly serialized launches."""
+    s = W.config2()
+    D = dynbond()
+    a = D.Context(s, params=dict(cell_scale=1.0))
+    b = D.Context(s, params=dict(cell_scale=1.0), flags=D.FLAG_NO_PDL)
+    for k in range(4):
+        p = torch.from_numpy(s.snapshot(k)).cuda()
+        assert np.array_equal(a.step(p, k, stats=True), b.step(p, k, stats=True))
+        fa, eva = a.forces(p)
+        fb, evb = b.forces(p)
+        torch.testing.assert_close(fa, fb, rtol=1e-5, atol=1e-4)
+        # record order and atomic order differ between runs: energy and
+        # virial agree to the reduction's rounding, not bit for bit
+        ea, eb = eva.cpu().numpy(), evb.cpu().numpy()
+        assert np.abs(ea - eb).max() <= 1e-9 * np.abs(ea).max()
     for x, y in zip(a.topology(), b.topology()):
         assert np.array_equal(x, y)
 
@@ -212,7 +239,10 @@ def test_host_buffer_entry_point_matches_device_path():
         f_d, ev_d = b.forces(p)
         assert np.array_equal(st_h, st_d)
         assert np.allclose(f_h, f_d.cpu().numpy(), rtol=1e-5, atol=1e-4)
-        assert np.allclose(ev_h, ev_d.cpu().numpy(), rtol=1e-9)
+        # the two contexts hold their records in different (unordered) list
+        # positions, so the FP32 partial sums group differently
+        ev_d = ev_d.cpu().numpy()
+        assert np.abs(ev_h - ev_d).max() <= 1e-7 * np.abs(ev_d).max()
 
 
 def test_position_outside_box_is_reported_and_sticks():
