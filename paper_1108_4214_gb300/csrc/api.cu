@@ -316,7 +316,7 @@ cudaError_t enqueue_forces(dynbond_ctx* c) {
   mark(c, c->ev_forces, k++);
   E(launch(c, k_angle_dihedral_forces, c->grid_force, 256, d, c->ff));
   mark(c, c->ev_forces, k++);
-  E(launch(c, k_ev_out, 1, 256, d));
+  E(launch(c, k_ev_out, bounded_grid(7ll * c->R, 256, c->nsm), 256, d));
   return cudaGetLastError();
 }
 
@@ -612,14 +612,13 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.cand, d.cand_cap);
   ALLOC(d.cand_start, N);
   ALLOC(d.cand_len, N);
-  ALLOC(d.act_c, N);
   ALLOC(d.ovf, N);
   ALLOC(d.brk, 4 * N);
   ALLOC(d.brk_len, N);
   ALLOC(d.killmask, N);
-  ALLOC(d.act_b, N);
   ALLOC(d.bm_ca, c->W);
   ALLOC(d.bm_ba, c->W);
+  ALLOC(d.bm_bn, c->W);
   ALLOC(d.bm_dirty, c->W);
   ALLOC(d.bm_new, c->W);
   ALLOC(d.live[0], 2 * N);
@@ -640,7 +639,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.tb_beads, R + 1);
   ALLOC(d.tb_fang, R + 1);
   ALLOC(d.tb_fdih, R + 1);
-  ALLOC(d.ev_acc, 7 * R);
+  ALLOC(d.ev_acc, 7 * (size_t)R * EV_COPIES);
   // per-call counters zeroed together: removed / added counts, k_fill
   // counters and items, round flags, statistics
   {
@@ -720,7 +719,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemcpyAsync(d.n_bonds, nb_rep.data(), 8 * R, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(d.tb_beads, tbeads.data(), 4 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
-  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_dirty, d.bm_new})
+  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_bn, d.bm_dirty, d.bm_new})
     CUDA_TRY(c, cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)c->W, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_ang, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_dih, 0, 4 * R, s));
@@ -744,7 +743,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemsetAsync(c->status_all, 0, c->status_bytes, s));
   k_allbonds<<<c->grid_bead, 256, 0, s>>>(d);
   k_rebuild<<<c->grid_seg, 256, 0, s>>>(d, c->d_rt, 1);
-  CUDA_TRY(c, cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * R, s));
+  CUDA_TRY(c, cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * (size_t)R * EV_COPIES, s));
   CUDA_TRY(c, cudaGetLastError());
   st = device_status(c);
   if (st) return (st);

@@ -75,8 +75,6 @@ struct CallArgs {
 struct Counters {
   int n_sorted;
   int cand_used;
-  int n_act_c;
-  int n_act_b;
   int n_nbl;
   int n_ovf;
   int ticket[8];
@@ -131,14 +129,13 @@ struct Dev {
   long long cand_cap;
   int* cand_start;             // [N]
   int* cand_len;               // [N]
-  int* act_c;                  // [N]
   int* ovf;                    // [N] sorted indices of beads with more than MAXC candidates
   int4* brk;                   // [N*4] (partner, rule, key lo, key hi), key = -d2
   unsigned char* brk_len;      // [N]
   unsigned char* killmask;     // [N]
-  int* act_b;                  // [N]
   unsigned* bm_ca;             // [W] creation-active beads
   unsigned* bm_ba;             // [W] breakage/kill-active beads
+  unsigned* bm_bn;             // [W] beads nominating a breakage partner
   unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
   unsigned* bm_new;            // [W] beads with a formed or retyped bond
   int* live[2];                // [2*N] each: active (system << 31 | bead) entries between rounds
@@ -162,7 +159,7 @@ struct Dev {
   long long status_words;
   unsigned long long* st_scan; // look-back status words of the cell scan
   long long* stats;            // [R*NSTAT]
-  double* ev_acc;              // [R*7]
+  double* ev_acc;              // [R * EV_COPIES * 7] striped energy / virial sums
 };
 
 // ---------------------------------------------------------------------------
@@ -485,6 +482,189 @@ __device__ __forceinline__ void count_add_warp(int* counts, int r, unsigned v) {
     if (lane == 0) atomicAdd(&counts[r], (int)sum);
   } else if (v) {
     atomicAdd(&counts[r], (int)v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block-aggregated counters.  Atomics on one address from every warp of a
+// launch serialize in L2 (a few ns each, thousands per launch), so list
+// appends and per-replica counts are combined per block first.
+// ---------------------------------------------------------------------------
+
+// Exclusive prefix of `want` over the block, then one atomicAdd on `counter`
+// for the block total (none if it is 0); returns this thread's first slot.
+// Every thread of the block must call it.
+__device__ __forceinline__ int block_alloc(int* counter, int want) {
+  __shared__ int s_off[32];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const int incl = warp_incl_scan(want);
+  if (lane == 31) s_off[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < nw ? s_off[lane] : 0;
+    int inc = warp_incl_scan(v);
+    if (lane < nw) s_off[lane] = inc - v;
+    if (lane == 31) s_base = inc ? atomicAdd(counter, inc) : 0;
+  }
+  __syncthreads();
+  const int at = s_base + s_off[wid] + incl - want;
+  __syncthreads();
+  return at;
+}
+
+__device__ __forceinline__ long long warp_sum64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Address of per-replica counter k: base[k] + r * stride[k].
+template <int K>
+struct CountTargets {
+  long long* base[K];
+  int stride[K];
+  __device__ unsigned long long* at(int r, int k) const {
+    return (unsigned long long*)(base[k] + (long long)r * stride[k]);
+  }
+};
+
+// Per-thread partial sums of K per-replica counters.  A thread keeps the
+// replica it last counted for and flushes with atomics when that changes
+// (rare: threads walk beads in id order, replicas are contiguous in id);
+// flush_block() adds the partials of the whole block with one atomic per
+// counter when they all belong to one replica, else one per thread.
+template <int K>
+struct ReplicaCounts {
+  int r = -1;
+  long long v[K];
+  __device__ ReplicaCounts() {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0;
+  }
+  __device__ void flush_thread(const CountTargets<K>& t) {
+    if (r >= 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        if (v[k]) atomicAdd(t.at(r, k), (unsigned long long)v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = 0;
+  }
+  __device__ void add(const CountTargets<K>& t, int rr, int k, long long x) {
+    if (!x) return;
+    if (rr != r) {
+      flush_thread(t);
+      r = rr;
+    }
+    v[k] += x;
+  }
+  // every thread of the block must call it
+  __device__ void flush_block(const CountTargets<K>& t) {
+    __shared__ int s_lo, s_hi;
+    __shared__ long long s_sum[K];
+    if (threadIdx.x == 0) {
+      s_lo = 0x7FFFFFFF;
+      s_hi = -1;
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_sum[k] = 0;
+    }
+    __syncthreads();
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) any |= v[k] != 0;
+    if (any) {
+      atomicMin(&s_lo, r);
+      atomicMax(&s_hi, r);
+    }
+    __syncthreads();
+    const int lo = s_lo, hi = s_hi;
+    if (hi >= 0 && lo == hi) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        long long x = warp_sum64(v[k]);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd((unsigned long long*)&s_sum[k], (unsigned long long)x);
+        v[k] = 0;
+      }
+      __syncthreads();
+      if (threadIdx.x < K && s_sum[threadIdx.x]) atomicAdd(t.at(lo, threadIdx.x), (unsigned long long)s_sum[threadIdx.x]);
+    } else if (hi >= 0) {
+      flush_thread(t);
+    }
+    __syncthreads();
+  }
+};
+
+// Visit the beads whose bit is set in bitmap a or b (words [0, W), bits of
+// beads below N) over the chunks [c_begin, c_end) of 8 words.  Loops are
+// block-uniform: each warp compacts one chunk and its lanes take the set
+// bits 32 at a time; fn(valid, i, in_a, in_b) is called by every thread of
+// the block the same number of times (valid = false for idle lanes), so fn
+// may use block-wide collectives.
+constexpr int CHUNK_WORDS = 8;
+
+// position of the n-th (from 0) set bit of m; n < popc(m)
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    unsigned lo = m & ((1u << w) - 1u);
+    int c = __popc(lo);
+    if (n >= c) {
+      n -= c;
+      m >>= w;
+      pos += w;
+    } else {
+      m = lo;
+    }
+  }
+  return pos;
+}
+
+template <class F>
+__device__ __forceinline__ void for_bits_block(const unsigned* a, const unsigned* b, long long W, long long N,
+                                               long long c_begin, long long c_end, F&& fn) {
+  __shared__ int s_rounds;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (long long c0 = c_begin; c0 < c_end; c0 += nwarps) {
+    const long long ch = c0 + warp;
+    const long long w0 = ch * CHUNK_WORDS;
+    unsigned wa = 0, wb = 0;
+    if (ch < c_end && lane < CHUNK_WORDS && w0 + lane < W) {
+      const long long b0 = 32 * (w0 + lane);  // the last word may extend past N
+      const unsigned vmask = b0 + 32 <= N ? FULL : (b0 >= N ? 0u : (1u << (N - b0)) - 1u);
+      if (a) wa = a[w0 + lane] & vmask;
+      if (b) wb = b[w0 + lane] & vmask;
+    }
+    const unsigned act = wa | wb;
+    const int incl = warp_incl_scan(__popc(act));
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (threadIdx.x == 0) s_rounds = 0;
+    __syncthreads();
+    if (lane == 0 && total) atomicMax(&s_rounds, (total + 31) >> 5);
+    __syncthreads();
+    const int rounds = s_rounds;
+    __syncthreads();
+    for (int rr = 0; rr < rounds; ++rr) {
+      const int want = rr * 32 + lane;
+      int k = 0;
+#pragma unroll
+      for (int q = 0; q < CHUNK_WORDS; ++q) k += __shfl_sync(FULL, incl, q) <= want;
+      const int ks = k & (CHUNK_WORDS - 1);
+      const unsigned act_k = __shfl_sync(FULL, act, ks);
+      const unsigned wa_k = __shfl_sync(FULL, wa, ks);
+      const unsigned wb_k = __shfl_sync(FULL, wb, ks);
+      const int prev = __shfl_sync(FULL, incl, (k - 1) & (CHUNK_WORDS - 1));
+      bool valid = want < total;
+      long long i = 0;
+      int bit = 0;
+      if (valid) {
+        bit = nth_set_bit(act_k, want - (k ? prev : 0));
+        i = 32 * (w0 + k) + bit;
+        valid = i < N;
+      }
+      fn(valid, i, valid && ((wa_k >> bit) & 1u), valid && ((wb_k >> bit) & 1u));
+    }
   }
 }
 

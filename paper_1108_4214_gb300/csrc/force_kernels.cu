@@ -124,7 +124,9 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
   if (threadIdx.x < 7) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
-    atomicAdd(&d.ev_acc[r * 7 + threadIdx.x], s);
+    // striped: blocks add to one of EV_COPIES copies, so the FP64 atomics
+    // of a launch do not all meet at the same seven addresses
+    atomicAdd(&d.ev_acc[((long long)r * EV_COPIES + blockIdx.x % EV_COPIES) * 7 + threadIdx.x], s);
   }
   __syncthreads();
 }
@@ -355,15 +357,21 @@ __global__ void __launch_bounds__(256) k_angle_dihedral_forces(Dev d, FF ff) {
   if (racc >= 0) flush_ev(d, acc, racc);
 }
 
-// copy the reduced energy / virial out and clear the accumulators for the
-// next force call
+// sum the striped copies of the energy / virial, write them out and clear
+// the accumulators for the next force call
 __global__ void k_ev_out(Dev d) {
   pdl_enter();
   if (aborted(d.err)) return;
   double* out = d.args->ev;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 7 * d.R; k += gridDim.x * blockDim.x) {
-    out[k] = d.ev_acc[k];
-    d.ev_acc[k] = 0.0;
+    const int r = k / 7, c = k % 7;
+    double s = 0.0;
+    for (int q = 0; q < EV_COPIES; ++q) {
+      double* p = d.ev_acc + ((long long)r * EV_COPIES + q) * 7 + c;
+      s += *p;
+      *p = 0.0;
+    }
+    out[k] = s;
   }
 }
 

@@ -10,6 +10,7 @@ constexpr int PURGE_TILE = 4096;   // 512 threads x 8 records
 constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
 constexpr int BEAD_TILE = 512;     // beads per force work item (2 per thread)
+constexpr int EV_COPIES = 32;      // striped copies of each replica's energy / virial sums
 
 // bonded force-field tables in FP32 (kernel parameter space)
 struct FF {

@@ -50,6 +50,8 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
+  const CountTargets<1> tg{{d.stats + ST_BREAK_CANDIDATES}, {NSTAT}};
+  ReplicaCounts<1> cnt;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     long long i = base + threadIdx.x;
     bool valid = i < N;
@@ -123,12 +125,14 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
         }
       }
     }
-    unsigned m = __ballot_sync(FULL, ba);
-    if (lane == 0 && valid) d.bm_ba[i >> 5] = m;
-    int slot = warp_alloc(&d.cnt->n_act_b, nbrk > 0 ? 1 : 0);
-    if (nbrk > 0) d.act_b[slot] = (int)i;
-    stat_add_warp(d.stats, r, ST_BREAK_CANDIDATES, (unsigned)ncand_b);
+    unsigned m = __ballot_sync(FULL, ba), mn = __ballot_sync(FULL, nbrk > 0);
+    if (lane == 0 && valid) {
+      d.bm_ba[i >> 5] = m;
+      d.bm_bn[i >> 5] = mn;
+    }
+    if (valid) cnt.add(tg, r, 0, ncand_b);
   }
+  cnt.flush_block(tg);
 }
 
 // ---------------------------------------------------------------------------
@@ -442,6 +446,8 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __rest
   const long long r2max = rtp->r2max;
   const int n = d.cnt->n_sorted;
   const int stride = gridDim.x * blockDim.x;
+  const CountTargets<1> tg{{d.stats + ST_CANDIDATES}, {NSTAT}};
+  ReplicaCounts<1> pairs;
   for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     int e = base + threadIdx.x;
     int i = -1, r = 0;
@@ -459,7 +465,7 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __rest
     int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
     if (ll.overflow) d.ovf[oslot] = e;
     int cnt = ll.overflow ? 0 : ll.cnt;
-    int at = warp_alloc(&d.cnt->cand_used, cnt);
+    int at = block_alloc(&d.cnt->cand_used, cnt);
     if (cnt > 0) {
       if ((long long)at + cnt > d.cand_cap) {
         atomicOr(d.err, ERR_CAND_CAP);
@@ -471,10 +477,9 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __rest
         activate_creator(d, i, at, cnt);
       }
     }
-    int slot = warp_alloc(&d.cnt->n_act_c, cnt > 0 ? 1 : 0);
-    if (cnt > 0) d.act_c[slot] = i;
-    stat_add_warp(d.stats, r, ST_CANDIDATES, ll.overflow ? 0u : (unsigned)ll.pairs);
+    if (e < n && !ll.overflow) pairs.add(tg, r, 0, ll.pairs);
   }
+  pairs.flush_block(tg);
 }
 
 // Exact path for beads with more than MAXC candidates: count, allocate,
@@ -516,7 +521,6 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
       lst[b] = x;
     }
     activate_creator(d, i, at, cv.cnt);
-    d.act_c[atomicAdd(&d.cnt->n_act_c, 1)] = i;
     stat_add(d, d.rep[i], ST_CANDIDATES, pairs);
   }
 }
@@ -527,100 +531,133 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
 // or max_rounds rounds.  Per-bead lists are sorted, so a bead's nominee is
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
+// Flag replica r (-1: none) in flags; one store per block when every thread
+// of the block names the same replica.  Every thread of the block must call it.
+__device__ __forceinline__ void block_flag(int* flags, int r) {
+  __shared__ int s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    s_lo = 0x7FFFFFFF;
+    s_hi = -1;
+  }
+  __syncthreads();
+  if (r >= 0) {
+    atomicMin(&s_lo, r);
+    atomicMax(&s_hi, r);
+  }
+  __syncthreads();
+  const int lo = s_lo, hi = s_hi;
+  if (hi >= 0) {
+    if (lo == hi) {
+      if (threadIdx.x == 0) flags[lo] = 1;
+    } else if (r >= 0) {
+      flags[r] = 1;
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_wait();  // cooperative: its successor is scheduled only when it ends
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
-  const int na_c = d.cnt->n_act_c, na_b = d.cnt->n_act_b;
   const long long N = d.N;
-  const int stride = gridDim.x * blockDim.x;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  // round 0 reads the two activation lists; later rounds read the compacted
-  // list of beads that were still unmatched and nominated someone
-  int n = na_c + na_b;
-  int round = 0;
-  // once few beads remain, block 0 finishes the rounds alone with block
-  // barriers instead of grid barriers
+  const int R = d.R;
+  const CountTargets<2> tg{{d.stats + ST_CREATE_MATCHED, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
+  ReplicaCounts<2> matched_pairs;
+  // round 0 enumerates the nominators from the activity bitmaps; later rounds
+  // read the compacted list of beads that were still unmatched and nominated
+  // someone.  Once few remain, block 0 finishes the rounds alone with block
+  // barriers instead of grid barriers.
+  int n = 0, round = 0;
   bool solo = false;
-  int gg = g, st = stride;
+  int nb = gridDim.x, bi = blockIdx.x;  // participating blocks, this block's rank
   while (true) {
     const int* src = round ? d.live[(round - 1) & 1] : nullptr;
     int* dst = d.live[round & 1];
-    // nomination: first list entry whose partner is still unmatched (round 0
-    // was written by the list producers)
-    for (int idx = round ? gg : n; idx < n; idx += st) {
-      int sys, i;
-      if (src) {
-        int e = src[idx];
-        sys = (unsigned)e >> 31;
-        i = e & 0x7FFFFFFF;
-      } else {
-        sys = idx >= na_c;
-        i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
-      }
-      long long o = sys ? N : 0;
-      int p = d.ptr[o + i];
-      int len = sys ? d.brk_len[i] : d.cand_len[i];
-      const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
-      int j = -1;
-      while (p < len) {
-        int q = lst[p].x;
-        if (ld_cg(d.mate + o + q) == -1) {
-          j = q;
-          break;
+    int hits = 0;            // pairs (i < j) this thread matched in this round
+    int hr[2] = {-1, -1};    // replica of those pairs, per system
+    // a mutual nomination is a match; an unmatched nominator carries over
+    auto match_one = [&](int sys, int i, bool& keep) {
+      const long long o = sys ? N : 0;
+      const int j = d.nom[o + i];
+      if (j >= 0 && ld_cg(d.nom + o + j) == i) {
+        d.mate[o + i] = j;
+        if (i < j) {
+          const int r = d.rep[i];
+          ++hits;
+          matched_pairs.add(tg, r, sys, 1);
+          if (hr[sys] != r) {
+            if (hr[sys] >= 0) d.round_hit[sys * R + hr[sys]] = 1;
+            hr[sys] = r;
+          }
         }
-        ++p;
+      } else {
+        keep = j >= 0;
       }
-      d.ptr[o + i] = p;
-      d.nom[o + i] = j;
-    }
-    if (round) {
+    };
+    if (round == 0) {
+      // nominations were written by the list producers
+      const long long nchunks = (d.W + CHUNK_WORDS - 1) / CHUNK_WORDS;
+      const long long cpb = (nchunks + nb - 1) / nb;
+      const long long c0 = (long long)bi * cpb, c1 = min(nchunks, c0 + cpb);
+      for_bits_block(d.bm_ca, d.bm_bn, d.W, N, c0, c1, [&](bool valid, long long i, bool ca, bool bn) {
+        bool k0 = false, k1 = false;
+        if (ca) match_one(0, (int)i, k0);
+        if (bn) match_one(1, (int)i, k1);
+        int at = block_alloc(&d.cnt->round_live[0], (int)k0 + (int)k1);
+        if (k0) dst[at++] = (int)i;
+        if (k1) dst[at] = (int)(1u << 31 | (unsigned)i);
+        (void)valid;
+      });
+    } else {
+      // nomination: first list entry whose partner is still unmatched
+      for (int base = bi * blockDim.x; base < n; base += nb * blockDim.x) {
+        const int idx = base + threadIdx.x;
+        if (idx >= n) continue;
+        const int e = src[idx];
+        const int sys = (unsigned)e >> 31, i = e & 0x7FFFFFFF;
+        const long long o = sys ? N : 0;
+        int p = d.ptr[o + i];
+        const int len = sys ? d.brk_len[i] : d.cand_len[i];
+        const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
+        int j = -1;
+        while (p < len) {
+          int q = lst[p].x;
+          if (ld_cg(d.mate + o + q) == -1) {
+            j = q;
+            break;
+          }
+          ++p;
+        }
+        d.ptr[o + i] = p;
+        d.nom[o + i] = j;
+      }
       if (solo) __syncthreads();
       else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
-    }
-    // mutual nominations are matched; unmatched nominators carry over
-    for (int base = gg - lane; base < n; base += st) {
-      int idx = base + lane;
-      int sys = 0, r = 0, i = -1;
-      bool hit = false, keep = false;
-      if (idx < n) {
-        if (src) {
-          int e = src[idx];
-          sys = (unsigned)e >> 31;
-          i = e & 0x7FFFFFFF;
-        } else {
-          sys = idx >= na_c;
-          i = sys ? d.act_b[idx - na_c] : d.act_c[idx];
+      for (int base = bi * blockDim.x; base < n; base += nb * blockDim.x) {
+        const int idx = base + threadIdx.x;
+        bool keep = false;
+        int e = 0;
+        if (idx < n) {
+          e = src[idx];
+          match_one((unsigned)e >> 31, e & 0x7FFFFFFF, keep);
         }
-        long long o = sys ? N : 0;
-        int j = d.nom[o + i];
-        if (j >= 0 && ld_cg(d.nom + o + j) == i) {
-          d.mate[o + i] = j;
-          if (i < j) {
-            r = d.rep[i];
-            hit = true;
-            d.round_hit[sys * d.R + r] = 1;
-          }
-        } else {
-          keep = j >= 0;
-        }
+        int at = block_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
+        if (keep) dst[at] = e;
       }
-      unsigned m = __ballot_sync(FULL, hit);
-      if (lane == 0 && m) atomicAdd(&d.cnt->round_matched[round], __popc(m));
-      stat_add_warp(d.stats, r, ST_CREATE_MATCHED, hit && !sys);
-      stat_add_warp(d.stats, r, ST_BREAK_MATCHED, hit && sys);
-      int at = warp_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
-      if (keep) dst[at] = (int)((unsigned)sys << 31 | (unsigned)i);
     }
+    // per block: pairs matched in the round, replicas that matched any
+    block_alloc(&d.cnt->round_matched[round], hits);
+    block_flag(d.round_hit, hr[0]);
+    block_flag(d.round_hit + R, hr[1]);
     if (solo) __syncthreads();
     else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
-    int matched = ld_cg(&d.cnt->round_matched[round]);
+    const int matched = ld_cg(&d.cnt->round_matched[round]);
     if (blockIdx.x == 0) {
-      for (int k = threadIdx.x; k < 2 * d.R; k += blockDim.x) {
+      for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) {
         if (ld_cg(d.round_hit + k)) {
-          int r = k % d.R;
-          d.stats[(long long)r * NSTAT + (k < d.R ? ST_CREATE_ROUNDS : ST_BREAK_ROUNDS)] += 1;
+          int r = k % R;
+          d.stats[(long long)r * NSTAT + (k < R ? ST_CREATE_ROUNDS : ST_BREAK_ROUNDS)] += 1;
           d.round_hit[k] = 0;
         }
       }
@@ -630,44 +667,27 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
     if (matched == 0 || n == 0) break;
     if (rt.max_rounds && round >= rt.max_rounds) break;
     if (round >= MAX_ROUNDS) {
-      if (g == 0) atomicOr(d.err, ERR_ROUNDS);
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(d.err, ERR_ROUNDS);
       break;
     }
     if (!solo && n <= SOLO_LIVE) {
-      if (blockIdx.x != 0) return;
+      if (blockIdx.x != 0) {
+        matched_pairs.flush_block(tg);
+        return;
+      }
       solo = true;
-      gg = threadIdx.x;
-      st = blockDim.x;
+      nb = 1;
+      bi = 0;
     }
   }
-  if (g == 0) d.cnt->rounds_done = round;
+  matched_pairs.flush_block(tg);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->rounds_done = round;
 }
 
 // ---------------------------------------------------------------------------
-// k_edit: trials and in-place edit of each bead's own slots.  Each warp owns
-// EDIT_WORDS bitmap words (32 beads each), compacts the beads marked
-// creation- or breakage-active there and edits only those, 32 at a time.
+// k_edit: trials and in-place edit of each bead's own slots.  Only beads
+// marked creation- or breakage-active are visited (bitmap compaction).
 // ---------------------------------------------------------------------------
-constexpr int EDIT_WORDS = 8;
-
-// position of the n-th (from 0) set bit of m; n < popc(m)
-__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
-  int pos = 0;
-#pragma unroll
-  for (int w = 16; w > 0; w >>= 1) {
-    unsigned lo = m & ((1u << w) - 1u);
-    int c = __popc(lo);
-    if (n >= c) {
-      n -= c;
-      m >>= w;
-      pos += w;
-    } else {
-      m = lo;
-    }
-  }
-  return pos;
-}
-
 struct EditOut {
   bool dirty = false, fresh = false;
   int form_hi = -1, conv_hi = -1;
@@ -756,92 +776,35 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__
   pdl_enter();
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
-  const long long W = d.W;
-  const int lane = threadIdx.x & 31;
-  const long long nchunks = (W + EDIT_WORDS - 1) / EDIT_WORDS;
-  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long ch = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunks; ch += wstride) {
-    const long long w0 = ch * EDIT_WORDS;
-    // lane k < EDIT_WORDS holds word w0 + k of both activity bitmaps
-    unsigned wca = 0, wba = 0;
-    if (lane < EDIT_WORDS && w0 + lane < W) {
-      // only bits of beads below N: the last word may extend past the end
-      const long long b0 = 32 * (w0 + lane);
-      const unsigned vmask = b0 + 32 <= d.N ? FULL : (b0 >= d.N ? 0u : (1u << (d.N - b0)) - 1u);
-      wca = d.bm_ca[w0 + lane] & vmask;
-      wba = d.bm_ba[w0 + lane] & vmask;
+  const CountTargets<5> tg{{d.stats + ST_KILLED, d.stats + ST_BROKEN, d.stats + ST_CONVERTED, d.stats + ST_FORMED,
+                            d.n_bonds},
+                           {NSTAT, NSTAT, NSTAT, NSTAT, 1}};
+  ReplicaCounts<5> counts;
+  const long long nchunks = (d.W + CHUNK_WORDS - 1) / CHUNK_WORDS;
+  const long long cpb = (nchunks + gridDim.x - 1) / gridDim.x;
+  const long long c0 = (long long)blockIdx.x * cpb, c1 = min(nchunks, c0 + cpb);
+  for_bits_block(d.bm_ca, d.bm_ba, d.W, d.N, c0, c1, [&](bool valid, long long i, bool ca, bool ba) {
+    EditOut o;
+    int r = 0;
+    if (valid) {
+      r = d.rep[i];
+      edit_bead(d, rt, i, r, ca, ba, o);
+      counts.add(tg, r, 0, o.n_killed);
+      counts.add(tg, r, 1, o.n_broken);
+      counts.add(tg, r, 2, o.n_conv);
+      counts.add(tg, r, 3, o.n_formed);
+      counts.add(tg, r, 4, (long long)o.n_formed - (long long)o.n_broken - (long long)o.n_killed);
+      if (o.dirty) atomicOr(&d.bm_dirty[i >> 5], 1u << (i & 31));
+      if (o.fresh) atomicOr(&d.bm_new[i >> 5], 1u << (i & 31));
     }
-    const unsigned act = wca | wba;
-    const int cnt = __popc(act);
-    const int incl = warp_incl_scan(cnt);
-    const int total = __shfl_sync(FULL, incl, 31);
-    unsigned out_dirty = 0, out_new = 0;  // lane k: output word w0 + k
-    for (int r0 = 0; r0 < total; r0 += 32) {
-      // lane takes active bead number r0 + lane of the chunk
-      const int want = r0 + lane;
-      int k = 0;
-#pragma unroll
-      for (int q = 0; q < EDIT_WORDS; ++q) k += __shfl_sync(FULL, incl, q) <= want;
-      const unsigned a_k = __shfl_sync(FULL, act, k & (EDIT_WORDS - 1));
-      const unsigned ca_k = __shfl_sync(FULL, wca, k & (EDIT_WORDS - 1));
-      const unsigned ba_k = __shfl_sync(FULL, wba, k & (EDIT_WORDS - 1));
-      const int prev = __shfl_sync(FULL, incl, (k - 1) & (EDIT_WORDS - 1));  // every lane shuffles
-      const int before = k ? prev : 0;
-      EditOut o;
-      int r = 0, bit = 0;
-      long long i = 0;
-      bool valid = want < total;
-      if (valid) {
-        bit = nth_set_bit(a_k, want - before);
-        i = 32 * (w0 + k) + bit;
-        if (i >= d.N) {  // cannot happen with the masked words; never touch memory past N
-          atomicOr(d.err, ERR_INTERNAL);
-          valid = false;
-        }
-      }
-      if (valid) {
-        r = d.rep[i];
-        edit_bead(d, rt, i, r, (ca_k >> bit) & 1u, (ba_k >> bit) & 1u, o);
-      }
-      stat_add_warp(d.stats, r, ST_KILLED, o.n_killed);
-      stat_add_warp(d.stats, r, ST_BROKEN, o.n_broken);
-      stat_add_warp(d.stats, r, ST_CONVERTED, o.n_conv);
-      stat_add_warp(d.stats, r, ST_FORMED, o.n_formed);
-      {
-        int dv = (int)o.n_formed - (int)o.n_broken - (int)o.n_killed;
-        if (__ballot_sync(FULL, dv != 0)) {
-          unsigned grp = __match_any_sync(FULL, r);
-          if (grp == FULL) {
-            int sum = (int)__reduce_add_sync(FULL, (unsigned)dv);
-            if (lane == 0 && sum) atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)sum);
-          } else if (dv) {
-            atomicAdd((unsigned long long*)&d.n_bonds[r], (unsigned long long)(long long)dv);
-          }
-        }
-      }
-      // output bitmap words: OR of the bits of the lanes in each word
-      const unsigned bit_i = valid ? 1u << (i & 31) : 0u;
-#pragma unroll
-      for (int q = 0; q < EDIT_WORDS; ++q) {
-        unsigned dq = __reduce_or_sync(FULL, (k == q && o.dirty) ? bit_i : 0u);
-        unsigned nq = __reduce_or_sync(FULL, (k == q && o.fresh) ? bit_i : 0u);
-        if (lane == q) {
-          out_dirty |= dq;
-          out_new |= nq;
-        }
-      }
-      // new-bond list for the rebuild: bonds formed or retyped, listed by
-      // their lower end
-      int nb_form = o.form_hi >= 0, nb_conv = o.conv_hi >= 0;
-      int at = warp_alloc(&d.cnt->n_nbl, nb_form + nb_conv);
-      if (nb_form) d.nbl[at++] = make_int4((int)i, o.form_hi, r, 0);
-      if (nb_conv) d.nbl[at] = make_int4((int)i, o.conv_hi, r, 0);
-    }
-    if (lane < EDIT_WORDS && w0 + lane < W) {
-      d.bm_dirty[w0 + lane] = out_dirty;
-      d.bm_new[w0 + lane] = out_new;
-    }
-  }
+    // new-bond list for the rebuild: bonds formed or retyped, listed by
+    // their lower end
+    const bool nf = o.form_hi >= 0, nv = o.conv_hi >= 0;
+    int at = block_alloc(&d.cnt->n_nbl, (int)nf + (int)nv);
+    if (nf) d.nbl[at++] = make_int4((int)i, o.form_hi, r, 0);
+    if (nv) d.nbl[at] = make_int4((int)i, o.conv_hi, r, 0);
+  });
+  counts.flush_block(tg);
 }
 
 // per-replica tile bases: base[r] = tiles of replicas before r, base[R] = all
@@ -890,16 +853,6 @@ __device__ void block_tile_bases(const int* count, int R, int per_tile, int* bas
 //               counts, the statistics and the force tiles
 // New bonds are listed by k_edit (or k_allbonds) as (u, v, replica, 0).
 // ---------------------------------------------------------------------------
-
-// One slot per lane that wants one, one atomic per warp (all lanes active).
-__device__ __forceinline__ int warp_alloc1(int* counter, bool want) {
-  const int lane = threadIdx.x & 31;
-  unsigned m = __ballot_sync(FULL, want);
-  int base = 0;
-  if (lane == 0 && m) base = atomicAdd(counter, __popc(m));
-  base = __shfl_sync(FULL, base, 0);
-  return base + __popc(m & ((1u << lane) - 1u));
-}
 
 // Last block of the grid to get here (after all its threads' writes are
 // visible device-wide); the caller then finishes the per-replica work alone.
@@ -983,9 +936,8 @@ __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) 
       bal[k] = __ballot_sync(FULL, idx < n && record_gone(d, v[k], dih));
       tot += __popc(bal[k]);
     }
-    if (!tot) continue;
-    int wbase = 0;
-    if (lane == 0) wbase = atomicAdd((dih ? d.m_dih : d.m_ang) + r, tot);
+    // one atomic per tile (the tile lies in one replica)
+    int wbase = block_alloc((dih ? d.m_dih : d.m_ang) + r, lane == 0 ? tot : 0);
     wbase = __shfl_sync(FULL, wbase, 0);
     int* rm = (dih ? d.rm_dih : d.rm_ang) + base;
     int* pr = (dih ? d.pr_dih : d.pr_ang) + base;
@@ -1040,8 +992,8 @@ __global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
     }
     int at = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int a = warp_alloc1(&d.fillc[4 * r + q], role == q);
+    for (int q = 0; q < 4; ++q) {  // the tile lies in one replica
+      int a = block_alloc(&d.fillc[4 * r + q], role == q ? 1 : 0);
       if (role == q) at = a;
     }
     if (role < 0) continue;
@@ -1251,7 +1203,11 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
   int* cnt = reinterpret_cast<int*>(d.cnt);
   for (long long k = g; k < (long long)(sizeof(Counters) / sizeof(int)); k += stride) cnt[k] = 0;
   for (long long k = g; k <= d.n_cells; k += stride) d.cell_start[k] = 0;
-  for (long long k = g; k < d.W; k += stride) d.bm_ca[k] = 0;
+  for (long long k = g; k < d.W; k += stride) {
+    d.bm_ca[k] = 0;
+    d.bm_dirty[k] = 0;
+    d.bm_new[k] = 0;
+  }
   for (long long k = g; k < d.small_words; k += stride) d.small[k] = 0;
   for (long long k = g; k < d.status_words; k += stride) d.status_all[k] = 0ull;
   if (blockIdx.x == 0) {
