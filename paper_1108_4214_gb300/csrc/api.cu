@@ -220,6 +220,16 @@ dynbond_status build_rules(dynbond_ctx* c, const dynbond_rule* rules, int n) {
   rt.prob_mode = p.prob_mode;
   rt.key0 = (uint32_t)p.seed;
   rt.key1 = (uint32_t)(p.seed >> 32);
+  // one cell-list class per creation-capable type (binned by k_bead)
+  rt.n_cls = 0;
+  for (int t = 0; t < 16; ++t)
+    rt.cls_of[t] = (rt.role_store[t] && ((rt.reactive >> t) & 1u)) ? rt.n_cls++ : -1;
+  for (int t = 0; t < 16; ++t) {
+    rt.cls_mask[t] = 0;
+    for (int u = 0; u < 16; ++u)
+      if (rt.pair_rules[t][u] && rt.cls_of[u] >= 0) rt.cls_mask[t] |= 1u << rt.cls_of[u];
+  }
+  if (rt.n_cls == 0) rt.n_cls = 1;  // nothing is binned; keep the arrays non-empty
   return DYNBOND_OK;
 }
 
@@ -399,9 +409,12 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale) {
     cb[r + 1] = cb[r] + n * n * n;
   }
   if (c->max_cells && cb[R] > c->max_cells) return fail(c, DYNBOND_EINVAL, "cell geometry larger than allocated");
+  if (cb[R] * c->rt.n_cls >= 0x7FFFFFFFll)
+    return fail(c, DYNBOND_EINVAL, "cell grid too large: boxes over 2^31 cell keys (cell classes x cells)");
   c->n_cells = cb[R];
   c->d.n_cells = c->n_cells;
-  c->grid_scan = bounded_grid(c->n_cells, 256 * 32, c->nsm * 4);
+  c->d.n_keys = c->n_cells * c->rt.n_cls;
+  c->grid_scan = bounded_grid(c->d.n_keys, 256 * 32, c->nsm * 4);
   if (c->d_nc) {
     CUDA_TRY(c, cudaMemcpyAsync(c->d_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cb, cb.data(), 8 * (R + 1), cudaMemcpyHostToDevice, c->stream));
@@ -604,12 +617,14 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.n_bonds, R);
   ALLOC(d.cnt, 1);
   ALLOC(d.err, 1);
-  ALLOC(d.cell_start, c->n_cells + 1);
+  ALLOC(d.cell_start, c->n_cells * c->rt.n_cls + 1);
   ALLOC(d.bead_cell, N);
   ALLOC(d.bead_rank, N);
   ALLOC(d.sorted, N);
-  d.cand_cap = 2 * N + 65536;
-  ALLOC(d.cand, d.cand_cap);
+  d.cand_fixed = N * CAND_FAST;
+  d.cand_pool = 2 * N + 65536;
+  if (d.cand_fixed + d.cand_pool >= 0x7FFFFFFFll) return fail(c, DYNBOND_EINVAL, "too many beads for one context");
+  ALLOC(d.cand, d.cand_fixed + d.cand_pool);
   ALLOC(d.cand_start, N);
   ALLOC(d.cand_len, N);
   ALLOC(d.ovf, N);
@@ -662,7 +677,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     d.stats = (long long*)(base + ((ints * sizeof(int) + 15) / 16) * 16);
   }
   {
-    c->st_scan_n = c->n_cells / (256 * 32) + 2;
+    c->st_scan_n = c->n_cells * c->rt.n_cls / (256 * 32) + 2;
     long long tot = c->st_scan_n;
     unsigned long long* base;
     ALLOC(base, tot);

@@ -14,6 +14,7 @@ namespace dynbond {
 constexpr int SLOTS = DYNBOND_SLOTS;
 constexpr int MAXR = DYNBOND_MAX_RULES;
 constexpr int MAXC = DYNBOND_MAX_CANDIDATES;
+constexpr int CAND_FAST = 8;  // candidate slots of each sorted entry (longer lists use the pool)
 constexpr int MAX_ROUNDS = DYNBOND_MAX_ROUNDS;
 constexpr int NSTAT = 17;
 constexpr unsigned FULL = 0xffffffffu;
@@ -61,6 +62,11 @@ struct RuleTab {
   uint32_t role_store[16];      // bond types a bead of type t could store under some creation rule
   int bk_start[17];             // breakbond / convertbond / killbond rules of bond type t:
   int bk_list[MAXR];            //   bk_list[bk_start[t] .. bk_start[t+1]) in list order
+  // cell-list classes: creation-capable bead types are binned apart, and a
+  // bead searches only the classes of the types it can pair with
+  int n_cls;
+  int cls_of[16];               // class of bead type t, -1 if never binned
+  uint32_t cls_mask[16];        // classes holding partner types of bead type t
 };
 
 // Arguments that change from call to call, read from device memory so that a
@@ -94,7 +100,8 @@ struct Dev {
   const long long* box;        // [R]
   const int* nc;               // [R] cells per axis
   const long long* cell_base;  // [R+1]
-  long long n_cells;
+  long long n_cells;            // cells of one class (all replicas)
+  long long n_keys;             // n_cls * n_cells binned keys
   const int* rep;              // [N]
   const unsigned char* type;   // [N]
   const unsigned* stream;      // [R]
@@ -121,12 +128,14 @@ struct Dev {
   // per-call scratch
   Counters* cnt;
   unsigned* err;               // sticky error word
-  int* cell_start;             // [n_cells + 1]
+  int* cell_start;             // [n_keys + 1], key = class * n_cells + cell
   int* bead_cell;              // [N]
   int* bead_rank;              // [N]
   int4* sorted;                // [N] (x, y, z, gid << 4 | type)
-  int4* cand;                  // [cand_cap] (partner, rule | mytype << 8, d2 lo, d2 hi)
-  long long cand_cap;
+  int4* cand;                  // (partner, rule | mytype << 8, d2 lo, d2 hi): CAND_FAST slots per
+                               // sorted entry, then a pool of cand_pool entries for longer lists
+  long long cand_fixed;        // N * CAND_FAST
+  long long cand_pool;
   int* cand_start;             // [N]
   int* cand_len;               // [N]
   int* ovf;                    // [N] sorted indices of beads with more than MAXC candidates
@@ -197,6 +206,18 @@ __device__ __forceinline__ int wrap_dx(int dx, int L) {
   else if (dx <= -half_up) dx += L;
   return dx;
 }
+// Cell of coordinate x in [0, L) on an axis of nc cells: floor(x nc / L)
+// exactly.  The FP32 estimate is within one of the true quotient (relative
+// error below 2^-22 on a value below 1024), and one integer-exact comparison
+// step corrects it.
+__device__ __forceinline__ int cell_of(int x, int nc, int L, float nc_over_L) {
+  int q = min(max((int)((float)x * nc_over_L), 0), nc - 1);
+  const long long p = (long long)x * nc;
+  if ((long long)q * L > p) --q;
+  else if ((long long)(q + 1) * L <= p) ++q;
+  return q;
+}
+
 __device__ __forceinline__ long long dist2(const int4& a, const int4& b, int L) {
   long long x = wrap_dx(a.x - b.x, L), y = wrap_dx(a.y - b.y, L), z = wrap_dx(a.z - b.z, L);
   return x * x + y * y + z * z;

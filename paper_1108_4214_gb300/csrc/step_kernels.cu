@@ -23,6 +23,7 @@ namespace dynbond {
 
 constexpr int PURGE_PER_THREAD = 8;  // records per thread; PURGE_TILE / 8 threads per block
 constexpr int SCAN_PER_THREAD = 32;  // cells per thread in the histogram scan
+constexpr int SCAN_BATCH = 2;  // candidate entries loaded together
 constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
 
 __device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
@@ -70,8 +71,9 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
         // creation: eligible beads are binned (Appendix step 2 searches them)
         if (creation_eligible(rt, bt, s)) {
           int nc = d.nc[r];
-          long long cx = (long long)p.x * nc / L, cy = (long long)p.y * nc / L, cz = (long long)p.z * nc / L;
-          long long c = d.cell_base[r] + (cx * nc + cy) * nc + cz;
+          const float f = (float)nc / (float)L;
+          long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f), cz = cell_of(p.z, nc, L, f);
+          long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nc + cz;
           d.bead_rank[i] = atomicAdd(&d.cell_start[c], 1);
           d.bead_cell[i] = (int)c;
         } else {
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
   __shared__ long long sh[33];
   __shared__ long long s_excl;
   __shared__ long long s_tile;
-  const long long n = d.n_cells;
+  const long long n = d.n_keys;
   const long long per_tile = (long long)blockDim.x * SCAN_PER_THREAD;
   const long long ntiles = (n + per_tile - 1) / per_tile;
   while (true) {
@@ -308,25 +310,27 @@ __device__ __noinline__ void cand_slow(const uint4* __restrict__ slots, const Ru
 }
 
 // Visit every creation candidate of eligible bead i (sorted entry `me`):
-// entries of the 27 neighbouring cells (distinct cells when a replica has
-// fewer than 3 per axis) whose bead type can pair with this one and that lie
-// within the largest creation distance are collected first; the rule and
-// graph-distance tests then run on them after the scan, so the lanes of a
-// warp take the rare path together instead of one after another.
-__device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned tmask,
+// for each cell-list class holding partner types of bead i, the entries of
+// the 27 neighbouring cells (distinct cells when a replica has fewer than 3
+// per axis) within the largest creation distance are collected first; the
+// rule and graph-distance tests then run on them after the scan, so the
+// lanes of a warp take the rare path together instead of one after another.
+__device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned cmask,
                                                 long long r2max, const int4& me, int i, LocalList* ll, int mode,
                                                 int4** out) {
-  int ti = me.w & 15;
-  int r = d.rep[i];
-  int L = (int)d.box[r], nc = d.nc[r];
-  long long cb = d.cell_base[r];
-  int cx = (int)((long long)me.x * nc / L), cy = (int)((long long)me.y * nc / L), cz = (int)((long long)me.z * nc / L);
+  const int ti = me.w & 15;
+  const int r = d.rep[i];
+  const int L = (int)d.box[r], nc = d.nc[r];
+  // cell keys fit in 32 bits (n_cls * n_cells < 2^31 is checked on the host)
+  const int cb = (int)d.cell_base[r], ncl = (int)d.n_cells;
+  const float f = (float)nc / (float)L;
+  const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f), cz = cell_of(me.z, nc, L, f);
   // x and y: the distinct neighbouring columns; z: the three neighbouring
   // cells of a column are contiguous in cell order, so each column is one or
   // two contiguous runs of the sorted array
-  int noff = nc >= 3 ? 3 : nc;
-  int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
-  int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
+  const int noff = nc >= 3 ? 3 : nc;
+  const int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
+  const int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
   int z0, z1, w0 = 0, w1 = -1;  // main run [z0, z1], wrapped run [w0, w1]
   if (nc >= 3) {
     z0 = cz - 1;
@@ -346,48 +350,54 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   long long pd[MAXC];
   int np = 0;
   bool more = false;
-  // all column ranges first (independent loads in flight together)
-  int rq0[9], rq1[9];
+  // entries of the 9 column runs [q0, q0 + len), fetched SCAN_BATCH at a
+  // time with independent loads (runs are short, most are empty)
+  auto scan_runs = [&](int lo, int hi, int cbk) {
+    int q0[9], ex[10];  // run starts; exclusive prefix of the run lengths
+    ex[0] = 0;
 #pragma unroll
-  for (int ab = 0; ab < 9; ++ab) {
-    int a = ab / 3, b = ab % 3;
-    rq0[ab] = rq1[ab] = 0;
-    if (a < noff && b < noff) {
-      long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
-      rq0[ab] = d.cell_start[row + z0];
-      rq1[ab] = d.cell_start[row + z1 + 1];
-    }
-  }
-  for (int ab = 0; ab < 9; ++ab) {
-    int a = ab / 3, b = ab % 3;
-    if (a >= noff || b >= noff) continue;
-    long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
-    for (int run = 0; run < 2; ++run) {
-      int q0, q1;
-      if (run == 0) {
-        q0 = rq0[ab];
-        q1 = rq1[ab];
-      } else {
-        if (w1 < w0) continue;
-        q0 = d.cell_start[row + w0];
-        q1 = d.cell_start[row + w1 + 1];
+    for (int ab = 0; ab < 9; ++ab) {
+      const int a = ab / 3, b = ab % 3;
+      int len = 0;
+      q0[ab] = 0;
+      if (a < noff && b < noff) {
+        const int row = cbk + (xs[a] * nc + ys[b]) * nc;
+        q0[ab] = d.cell_start[row + lo];
+        len = d.cell_start[row + hi + 1] - q0[ab];
       }
-      {
-        for (int q = q0; q < q1; ++q) {
-          int4 o = d.sorted[q];
-          if (!((tmask >> (o.w & 15)) & 1u)) continue;
-          long long dd = dist2(me, o, L);
-          if (dd > r2max || (o.w >> 4) == i) continue;
-          if (np < MAXC) {
-            pj[np] = o.w;
-            pd[np] = dd;
-            ++np;
-          } else {
-            more = true;
-          }
+      ex[ab + 1] = ex[ab] + len;
+    }
+    const int total = ex[9];
+    for (int k0 = 0; k0 < total; k0 += SCAN_BATCH) {
+      int4 o[SCAN_BATCH];
+#pragma unroll
+      for (int v = 0; v < SCAN_BATCH; ++v) {
+        const int k = k0 + v;
+        int q = -1;
+#pragma unroll
+        for (int u = 0; u < 9; ++u)
+          if (k >= ex[u] && k < ex[u + 1]) q = q0[u] + (k - ex[u]);
+        if (q >= 0) o[v] = d.sorted[q];
+      }
+#pragma unroll
+      for (int v = 0; v < SCAN_BATCH; ++v) {
+        if (k0 + v >= total) break;
+        const long long dd = dist2(me, o[v], L);
+        if (dd > r2max || (o[v].w >> 4) == i) continue;
+        if (np < MAXC) {
+          pj[np] = o[v].w;
+          pd[np] = dd;
+          ++np;
+        } else {
+          more = true;
         }
       }
     }
+  };
+  for (unsigned cm = cmask; cm; cm &= cm - 1) {
+    const int cbk = (__ffs(cm) - 1) * ncl + cb;  // this class's cells of the replica
+    scan_runs(z0, z1, cbk);
+    if (w1 >= w0) scan_runs(w0, w1, cbk);  // next to a periodic boundary in z
   }
   if (more && mode == 0) {
     ll->overflow = true;  // finished exactly by k_cand_overflow
@@ -395,23 +405,24 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   }
   if (more) {  // counting / writing passes of the overflow path: rescan without a buffer
     uint4 si = d.slots[i];
-    for (int a = 0; a < noff; ++a)
-      for (int b = 0; b < noff; ++b) {
-        long long row = cb + ((long long)xs[a] * nc + ys[b]) * nc;
-        for (int run = 0; run < 2; ++run) {
-          int lo = run ? w0 : z0, hi = run ? w1 : z1;
-          if (hi < lo) continue;
-          int q0 = d.cell_start[row + lo], q1 = d.cell_start[row + hi + 1];
-          for (int q = q0; q < q1; ++q) {
-            int4 o = d.sorted[q];
-            int tj = o.w & 15;
-            if (!((tmask >> tj) & 1u)) continue;
-            long long dd = dist2(me, o, L);
-            if (dd > r2max || (o.w >> 4) == i) continue;
-            cand_slow(d.slots, rtp, i, o.w >> 4, ti, tj, dd, si, ll, mode, out);
+    for (unsigned cm = cmask; cm; cm &= cm - 1) {
+      const int cbk = (__ffs(cm) - 1) * ncl + cb;
+      for (int a = 0; a < noff; ++a)
+        for (int b = 0; b < noff; ++b) {
+          const int row = cbk + (xs[a] * nc + ys[b]) * nc;
+          for (int run = 0; run < 2; ++run) {
+            int lo = run ? w0 : z0, hi = run ? w1 : z1;
+            if (hi < lo) continue;
+            int q0 = d.cell_start[row + lo], q1 = d.cell_start[row + hi + 1];
+            for (int q = q0; q < q1; ++q) {
+              int4 o = d.sorted[q];
+              long long dd = dist2(me, o, L);
+              if (dd > r2max || (o.w >> 4) == i) continue;
+              cand_slow(d.slots, rtp, i, o.w >> 4, ti, o.w & 15, dd, si, ll, mode, out);
+            }
           }
         }
-      }
+    }
     return;
   }
   if (np == 0) return;
@@ -428,17 +439,13 @@ __device__ __forceinline__ void activate_creator(const Dev& d, int i, int start,
   atomicOr(&d.bm_ca[i >> 5], 1u << (i & 31));
 }
 
-// bit tj of the mask of bead type ti: some creation rule pairs ti with tj
+// per bead type: the cell-list classes holding its partner types
 __device__ __forceinline__ void load_type_masks(const RuleTab& rt, unsigned* s_mask) {
-  if (threadIdx.x < 16) {
-    unsigned m = 0;
-    for (int b = 0; b < 16; ++b) m |= (rt.pair_rules[threadIdx.x][b] != 0) << b;
-    s_mask[threadIdx.x] = m;
-  }
+  if (threadIdx.x < 16) s_mask[threadIdx.x] = rt.cls_mask[threadIdx.x];
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+__global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
   if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
@@ -464,17 +471,24 @@ __global__ void __launch_bounds__(256) k_candidates(Dev d, const RuleTab* __rest
     // beads with more than MAXC candidates are finished by k_cand_overflow
     int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
     if (ll.overflow) d.ovf[oslot] = e;
+    // lists of up to CAND_FAST entries go to the sorted entry's own slots;
+    // longer ones (rare) take room from the shared pool behind them
     int cnt = ll.overflow ? 0 : ll.cnt;
-    int at = block_alloc(&d.cnt->cand_used, cnt);
     if (cnt > 0) {
-      if ((long long)at + cnt > d.cand_cap) {
-        atomicOr(d.err, ERR_CAND_CAP);
-        cnt = 0;
-      } else {
+      long long at = (long long)e * CAND_FAST;
+      if (cnt > CAND_FAST) {
+        const int a = atomicAdd(&d.cnt->cand_used, cnt);
+        at = d.cand_fixed + a;
+        if ((long long)a + cnt > d.cand_pool) {
+          atomicOr(d.err, ERR_CAND_CAP);
+          cnt = 0;
+        }
+      }
+      if (cnt > 0) {
         for (int q = 0; q < cnt; ++q)
           d.cand[at + q] =
               make_int4(ll.kp[q], ll.ki[q], (int)(unsigned)(unsigned long long)ll.kd[q], (int)(ll.kd[q] >> 32));
-        activate_creator(d, i, at, cnt);
+        activate_creator(d, i, (int)at, cnt);
       }
     }
     if (e < n && !ll.overflow) pairs.add(tg, r, 0, ll.pairs);
@@ -498,11 +512,12 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     cv.cnt = cv.pairs = 0;
     cv.me = i;
     scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 1, nullptr);
-    int at = atomicAdd(&d.cnt->cand_used, cv.cnt);
-    if ((long long)at + cv.cnt > d.cand_cap) {
+    const int a = atomicAdd(&d.cnt->cand_used, cv.cnt);
+    if ((long long)a + cv.cnt > d.cand_pool) {
       atomicOr(d.err, ERR_CAND_CAP);
       continue;
     }
+    const long long at = d.cand_fixed + a;
     int pairs = cv.pairs;
     int4* w = d.cand + at;
     scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 2, &w);
@@ -520,7 +535,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
       }
       lst[b] = x;
     }
-    activate_creator(d, i, at, cv.cnt);
+    activate_creator(d, i, (int)at, cv.cnt);
     stat_add(d, d.rep[i], ST_CANDIDATES, pairs);
   }
 }
@@ -1202,7 +1217,7 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   int* cnt = reinterpret_cast<int*>(d.cnt);
   for (long long k = g; k < (long long)(sizeof(Counters) / sizeof(int)); k += stride) cnt[k] = 0;
-  for (long long k = g; k <= d.n_cells; k += stride) d.cell_start[k] = 0;
+  for (long long k = g; k <= d.n_keys; k += stride) d.cell_start[k] = 0;
   for (long long k = g; k < d.W; k += stride) {
     d.bm_ca[k] = 0;
     d.bm_dirty[k] = 0;
