@@ -275,6 +275,10 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Replica of bead i: the common single-system case needs no load, so later
+// loads that depend on the replica (box, offsets, streams) are not delayed.
+__device__ __forceinline__ int rep_of(const Dev& d, long long i) { return d.R == 1 ? 0 : d.rep[i]; }
+
 __device__ __forceinline__ bool aborted(const unsigned* err) { return *(const volatile unsigned*)err != 0u; }
 
 // ---------------------------------------------------------------------------
@@ -580,6 +584,70 @@ struct ReplicaCounts {
     }
     v[k] += x;
   }
+  // Barrier-free variant for kernels whose warps finish at different times:
+  // begin_block() (every thread, once, before any end_warp) clears the shared
+  // partials; end_warp() (every lane of a warp, once) adds the warp's partials
+  // there, and the last warp of the block to finish adds them to the
+  // counters.  Partials of a replica other than the block's first are added
+  // directly.
+  struct Shared {
+    long long sum[K];
+    int r, done;
+  };
+  __device__ static Shared& shared() {
+    __shared__ Shared sh;
+    return sh;
+  }
+  __device__ static void begin_block() {
+    Shared& sh = shared();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) sh.sum[k] = 0;
+      sh.r = -1;
+      sh.done = 0;
+    }
+    __syncthreads();
+  }
+  __device__ void end_warp(const CountTargets<K>& t) {
+    Shared& sh = shared();
+    const int lane = threadIdx.x & 31;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) any |= v[k] != 0;
+    const int rr = any ? r : -1;
+    const unsigned have = __ballot_sync(FULL, any);
+    const int wr = __shfl_sync(FULL, rr, have ? __ffs(have) - 1 : 0);
+    // warp-uniform: every lane with partials counts for replica wr
+    const bool uniform = __all_sync(FULL, !any || rr == wr) && have;
+    bool local = false;  // this warp's partials go to the shared sums
+    if (uniform) {
+      int cur = 0;
+      if (lane == 0) {
+        cur = atomicCAS(&sh.r, -1, wr);
+        cur = cur == -1 ? wr : cur;
+      }
+      local = __shfl_sync(FULL, cur, 0) == wr;
+    }
+    if (local) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const long long x = warp_sum64(v[k]);
+        if (lane == 0 && x) atomicAdd((unsigned long long*)&sh.sum[k], (unsigned long long)x);
+        v[k] = 0;
+      }
+    } else {
+      flush_thread(t);
+    }
+    __threadfence_block();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&sh.done, 1) == (int)(blockDim.x >> 5) - 1;
+    last = __shfl_sync(FULL, last, 0);
+    if (last && lane < K) {
+      const long long x = *(volatile long long*)&sh.sum[lane];
+      const int br = *(volatile int*)&sh.r;
+      if (x && br >= 0) atomicAdd(t.at(br, lane), (unsigned long long)x);
+    }
+  }
   // every thread of the block must call it
   __device__ void flush_block(const CountTargets<K>& t) {
     __shared__ int s_lo, s_hi;
@@ -615,6 +683,31 @@ struct ReplicaCounts {
     __syncthreads();
   }
 };
+
+// Flag replica r (-1: none) in flags; one store per block when every thread
+// of the block names the same replica.  Every thread of the block must call it.
+__device__ __forceinline__ void block_flag(int* flags, int r) {
+  __shared__ int s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    s_lo = 0x7FFFFFFF;
+    s_hi = -1;
+  }
+  __syncthreads();
+  if (r >= 0) {
+    atomicMin(&s_lo, r);
+    atomicMax(&s_hi, r);
+  }
+  __syncthreads();
+  const int lo = s_lo, hi = s_hi;
+  if (hi >= 0) {
+    if (lo == hi) {
+      if (threadIdx.x == 0) flags[lo] = 1;
+    } else if (r >= 0) {
+      flags[r] = 1;
+    }
+  }
+  __syncthreads();
+}
 
 // Visit the beads whose bit is set in bitmap a or b (words [0, W), bits of
 // beads below N) over the chunks [c_begin, c_end) of 8 words.  Loops are

@@ -51,15 +51,16 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  const CountTargets<1> tg{{d.stats + ST_BREAK_CANDIDATES}, {NSTAT}};
-  ReplicaCounts<1> cnt;
+  const CountTargets<2> tg{{d.stats + ST_BREAK_CANDIDATES, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
+  ReplicaCounts<2> cnt;
+  int hit_r = -1;  // replica of the breakage pairs this thread matched (settled pairs, below)
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     long long i = base + threadIdx.x;
     bool valid = i < N;
     int nbrk = 0, ncand_b = 0, r = 0;
-    bool ba = false;
+    bool ba = false, nominates = false;
     if (valid) {
-      r = d.rep[i];
+      r = rep_of(d, i);
       int bt = d.type[i];
       uint4 s = d.slots[i];
       int4 p = pos[i];
@@ -84,13 +85,18 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
         if (rt.breakish && has_bit(rt.reactive, bt)) {
           unsigned km = 0;
           int4 ent[SLOTS];
+          int nbt = 0;        // slots of i holding a type named by break / convert / kill rules
+          uint4 sj_one = s;   // slots of the partner (meaningful when nbrk == 1)
 #pragma unroll
           for (int q = 0; q < SLOTS; ++q) {
             unsigned v = s_get(s, q);
             if (!v || !has_bit(rt.breakish, s_type(v))) continue;
+            ++nbt;
             int bty = s_type(v), j = s_partner(v);
             if (!has_bit(rt.reactive, d.type[j])) continue;
-            if (s_type_to(d.slots[j], (int)i) != bty) continue;
+            const uint4 sj = d.slots[j];
+            if (s_type_to(sj, (int)i) != bty) continue;
+            sj_one = sj;
             long long dd = dist2(p, pos[j], L);
             int rule = -1;
             for (int q2 = rt.bk_start[bty], q3 = rt.bk_start[bty + 1]; q2 < q3; ++q2) {
@@ -113,21 +119,50 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
             ++nbrk;
             ncand_b += j > i;
           }
-          if (km || nbrk) {
+          // A settled pair: both ends hold exactly one bond of a type named by
+          // break / convert / kill rules -- each other.  They nominate each
+          // other in round 0 and nobody else can nominate either, so they
+          // match there whatever else happens; the trial (step 5) is drawn
+          // now and only a successful one reaches the edit.
+          bool settled = false;
+          if (nbrk == 1 && nbt == 1) {
+            int nbt_j = 0;
+#pragma unroll
+            for (int q = 0; q < SLOTS; ++q) {
+              unsigned v = s_get(sj_one, q);
+              nbt_j += v && has_bit(rt.breakish, s_type(v));
+            }
+            settled = nbt_j == 1;
+          }
+          bool broken = false;
+          if (settled) {
+            const int j = ent[0].x, k = ent[0].y;
+            const int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
+            broken = trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k]);
+            if (j > i) {
+              cnt.add(tg, r, 1, 1);  // the pair matched in round 0
+              if (hit_r != r) {
+                if (hit_r >= 0) d.round_hit[d.R + hit_r] = 1;
+                hit_r = r;
+              }
+            }
+          }
+          if (km || (nbrk && !settled) || broken) {
             ba = true;
             d.killmask[i] = (unsigned char)km;
             d.brk_len[i] = (unsigned char)nbrk;
             for (int q = 0; q < nbrk; ++q) d.brk[4 * i + q] = ent[q];
             if (nbrk) {
-              d.mate[N + i] = -1;
+              d.mate[N + i] = broken ? ent[0].x : -1;
               d.ptr[N + i] = 0;
               d.nom[N + i] = ent[0].x;  // round 0 nomination: the most distant partner
             }
           }
+          nominates = nbrk > 0 && !settled;
         }
       }
     }
-    unsigned m = __ballot_sync(FULL, ba), mn = __ballot_sync(FULL, nbrk > 0);
+    unsigned m = __ballot_sync(FULL, ba), mn = __ballot_sync(FULL, nominates);
     if (lane == 0 && valid) {
       d.bm_ba[i >> 5] = m;
       d.bm_bn[i >> 5] = mn;
@@ -135,6 +170,8 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
     if (valid) cnt.add(tg, r, 0, ncand_b);
   }
   cnt.flush_block(tg);
+  // settled pairs count as round-0 breakage matches of their replica
+  block_flag(d.round_hit + d.R, hit_r);
 }
 
 // ---------------------------------------------------------------------------
@@ -319,7 +356,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
                                                 long long r2max, const int4& me, int i, LocalList* ll, int mode,
                                                 int4** out) {
   const int ti = me.w & 15;
-  const int r = d.rep[i];
+  const int r = rep_of(d, i);
   const int L = (int)d.box[r], nc = d.nc[r];
   // cell keys fit in 32 bits (n_cls * n_cells < 2^31 is checked on the host)
   const int cb = (int)d.cell_base[r], ncl = (int)d.n_cells;
@@ -455,6 +492,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
   const int stride = gridDim.x * blockDim.x;
   const CountTargets<1> tg{{d.stats + ST_CANDIDATES}, {NSTAT}};
   ReplicaCounts<1> pairs;
+  ReplicaCounts<1>::begin_block();
   for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     int e = base + threadIdx.x;
     int i = -1, r = 0;
@@ -464,7 +502,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
     if (e < n) {
       int4 me = d.sorted[e];
       i = me.w >> 4;
-      r = d.rep[i];
+      r = rep_of(d, i);
       ll.me = i;
       scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &ll, 0, nullptr);
     }
@@ -493,7 +531,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
     }
     if (e < n && !ll.overflow) pairs.add(tg, r, 0, ll.pairs);
   }
-  pairs.flush_block(tg);
+  pairs.end_warp(tg);
 }
 
 // Exact path for beads with more than MAXC candidates: count, allocate,
@@ -536,7 +574,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
       lst[b] = x;
     }
     activate_creator(d, i, (int)at, cv.cnt);
-    stat_add(d, d.rep[i], ST_CANDIDATES, pairs);
+    stat_add(d, rep_of(d, i), ST_CANDIDATES, pairs);
   }
 }
 
@@ -546,31 +584,6 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
 // or max_rounds rounds.  Per-bead lists are sorted, so a bead's nominee is
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
-// Flag replica r (-1: none) in flags; one store per block when every thread
-// of the block names the same replica.  Every thread of the block must call it.
-__device__ __forceinline__ void block_flag(int* flags, int r) {
-  __shared__ int s_lo, s_hi;
-  if (threadIdx.x == 0) {
-    s_lo = 0x7FFFFFFF;
-    s_hi = -1;
-  }
-  __syncthreads();
-  if (r >= 0) {
-    atomicMin(&s_lo, r);
-    atomicMax(&s_hi, r);
-  }
-  __syncthreads();
-  const int lo = s_lo, hi = s_hi;
-  if (hi >= 0) {
-    if (lo == hi) {
-      if (threadIdx.x == 0) flags[lo] = 1;
-    } else if (r >= 0) {
-      flags[r] = 1;
-    }
-  }
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_wait();  // cooperative: its successor is scheduled only when it ends
   if (aborted(d.err)) return;
@@ -598,7 +611,7 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
       if (j >= 0 && ld_cg(d.nom + o + j) == i) {
         d.mate[o + i] = j;
         if (i < j) {
-          const int r = d.rep[i];
+          const int r = rep_of(d, i);
           ++hits;
           matched_pairs.add(tg, r, sys, 1);
           if (hr[sys] != r) {
@@ -802,7 +815,7 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__
     EditOut o;
     int r = 0;
     if (valid) {
-      r = d.rep[i];
+      r = rep_of(d, i);
       edit_bead(d, rt, i, r, ca, ba, o);
       counts.add(tg, r, 0, o.n_killed);
       counts.add(tg, r, 1, o.n_broken);
@@ -893,7 +906,7 @@ __global__ void __launch_bounds__(256) k_allbonds(Dev d) {
     int out[SLOTS], n = 0, r = 0;
     if (u < N) {
       uint4 su = d.slots[u];
-      r = d.rep[u];
+      r = rep_of(d, u);
 #pragma unroll
       for (int q = 0; q < SLOTS; ++q) {
         int v = s_partner(s_get(su, q));
