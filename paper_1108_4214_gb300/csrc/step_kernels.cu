@@ -309,26 +309,23 @@ struct LocalList {
   bool overflow;
 };
 
-// Rare path of the neighbour scan, kept out of line so the hot loop stays
-// small: last matching creation rule, graph-distance exclusion, sorted
-// insertion (mode 0: into the local list; 1: count; 2: write to `out`).
-__device__ __noinline__ void cand_slow(const uint4* __restrict__ slots, const RuleTab* __restrict__ rtp, int i, int j,
-                                       int ti, int tj, long long dd, uint4 si, LocalList* ll, int mode, int4** out) {
+// Rule and graph-distance tests of a pair within the largest creation
+// distance: the last matching creation rule and the type bead i would store
+// (code = rule | stored type << 8), or -1.  Kept out of line so the scan
+// loops stay small.
+__device__ __noinline__ int eval_pair(const uint4* __restrict__ slots, const RuleTab* __restrict__ rtp, int i, int j,
+                                      int ti, int tj, long long dd, uint4 si) {
   const RuleTab& rt = *rtp;
   uint4 sj = slots[j];
   int sta, stb, k;
   if (i < j) k = creation_rule(rt, ti, tj, si, sj, dd, &sta, &stb);
   else k = creation_rule(rt, tj, ti, sj, si, dd, &stb, &sta);
-  if (k < 0 || !pair_eligible(slots, rt, i, j, si, sj)) return;
-  ll->pairs += j > i;
-  if (mode == 2) {
-    *(*out)++ = make_int4(j, k | (sta << 8), (int)(unsigned)(unsigned long long)dd, (int)(dd >> 32));
-    return;
-  }
-  if (mode == 1) {
-    ++ll->cnt;
-    return;
-  }
+  if (k < 0 || !pair_eligible(slots, rt, i, j, si, sj)) return -1;
+  return k | (sta << 8);
+}
+
+// insert (dd, j, code) into the bead's list, sorted by (d2, partner)
+__device__ __forceinline__ void list_insert(LocalList* ll, long long dd, int j, int code) {
   if (ll->cnt == MAXC) {
     ll->overflow = true;
     return;
@@ -342,8 +339,20 @@ __device__ __noinline__ void cand_slow(const uint4* __restrict__ slots, const Ru
   }
   ll->kd[at] = dd;
   ll->kp[at] = j;
-  ll->ki[at] = k | (sta << 8);
+  ll->ki[at] = code;
   ++ll->cnt;
+}
+
+// The overflow passes: mode 1 counts the bead's candidates, mode 2 writes
+// them to *out (sorted afterwards).
+__device__ __forceinline__ void cand_slow(const uint4* __restrict__ slots, const RuleTab* __restrict__ rtp, int i,
+                                          int j, int ti, int tj, long long dd, uint4 si, LocalList* ll, int mode,
+                                          int4** out) {
+  const int code = eval_pair(slots, rtp, i, j, ti, tj, dd, si);
+  if (code < 0) return;
+  ll->pairs += j > i;
+  if (mode == 2) *(*out)++ = make_int4(j, code, (int)(unsigned)(unsigned long long)dd, (int)(dd >> 32));
+  else ++ll->cnt;
 }
 
 // Visit every creation candidate of eligible bead i (sorted entry `me`):
@@ -354,7 +363,7 @@ __device__ __noinline__ void cand_slow(const uint4* __restrict__ slots, const Ru
 // lanes of a warp take the rare path together instead of one after another.
 __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned cmask,
                                                 long long r2max, const int4& me, int i, LocalList* ll, int mode,
-                                                int4** out) {
+                                                int4** out, int* pj, long long* pd, int* np_out) {
   const int ti = me.w & 15;
   const int r = rep_of(d, i);
   const int L = (int)d.box[r], nc = d.nc[r];
@@ -383,8 +392,6 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
     z0 = 0;
     z1 = nc - 1;
   }
-  int pj[MAXC];
-  long long pd[MAXC];
   int np = 0;
   bool more = false;
   // entries of the 9 column runs [q0, q0 + len), fetched SCAN_BATCH at a
@@ -436,8 +443,9 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
     scan_runs(z0, z1, cbk);
     if (w1 >= w0) scan_runs(w0, w1, cbk);  // next to a periodic boundary in z
   }
-  if (more && mode == 0) {
-    ll->overflow = true;  // finished exactly by k_cand_overflow
+  if (mode == 0) {  // survivors go back to the caller; the warp tests them together
+    ll->overflow = more;  // finished exactly by k_cand_overflow
+    *np_out = more ? 0 : np;
     return;
   }
   if (more) {  // counting / writing passes of the overflow path: rescan without a buffer
@@ -467,6 +475,59 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   for (int k = 0; k < np; ++k) cand_slow(d.slots, rtp, i, pj[k] >> 4, ti, pj[k] & 15, pd[k], si, ll, mode, out);
 }
 
+// The rule and graph-distance tests of the survivors of a whole warp: the
+// lanes' survivors are queued in shared memory and tested 32 at a time, so
+// a lane with many survivors does not hold the warp for each of them; the
+// results go back to the owners' sorted lists.  Every lane must call it.
+constexpr int SURV_CAP = 64;  // queued survivors per warp (more: each lane tests its own)
+struct SurvQueue {
+  int j[SURV_CAP], code[SURV_CAP];
+  long long dd[SURV_CAP];
+  unsigned char owner[SURV_CAP];
+};
+__device__ __forceinline__ void warp_survivors(const Dev& d, const RuleTab* __restrict__ rtp, int i, int ti,
+                                               const uint4& si, const int* pj, const long long* pd, int np,
+                                               LocalList* ll, SurvQueue& q) {
+  const int lane = threadIdx.x & 31;
+  const int incl = warp_incl_scan(np);
+  const int total = __shfl_sync(FULL, incl, 31);
+  if (total == 0) return;
+  if (total > SURV_CAP) {
+    for (int k = 0; k < np; ++k) {
+      const int code = eval_pair(d.slots, rtp, i, pj[k] >> 4, ti, pj[k] & 15, pd[k], si);
+      if (code < 0) continue;
+      ll->pairs += (pj[k] >> 4) > i;
+      list_insert(ll, pd[k], pj[k] >> 4, code);
+    }
+    return;
+  }
+  const int off = incl - np;
+  for (int k = 0; k < np; ++k) {
+    q.j[off + k] = pj[k];
+    q.dd[off + k] = pd[k];
+    q.owner[off + k] = (unsigned char)lane;
+  }
+  __syncwarp();
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int t = t0 + lane;
+    const bool valid = t < total;
+    const int o = valid ? q.owner[t] : lane;
+    const int oi = __shfl_sync(FULL, i, o), oti = __shfl_sync(FULL, ti, o);
+    const uint4 osi = make_uint4(__shfl_sync(FULL, si.x, o), __shfl_sync(FULL, si.y, o), __shfl_sync(FULL, si.z, o),
+                                 __shfl_sync(FULL, si.w, o));
+    if (valid) q.code[t] = eval_pair(d.slots, rtp, oi, q.j[t] >> 4, oti, q.j[t] & 15, q.dd[t], osi);
+  }
+  __syncwarp();
+  for (int k = 0; k < np; ++k) {
+    const int code = q.code[off + k];
+    if (code < 0) continue;
+    const int j = pj[k] >> 4;
+    ll->pairs += j > i;
+    list_insert(ll, pd[k], j, code);
+  }
+  __syncwarp();
+}
+
 __device__ __forceinline__ void activate_creator(const Dev& d, int i, int start, int len) {
   d.cand_start[i] = start;
   d.cand_len[i] = len;
@@ -493,19 +554,26 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
   const CountTargets<1> tg{{d.stats + ST_CANDIDATES}, {NSTAT}};
   ReplicaCounts<1> pairs;
   ReplicaCounts<1>::begin_block();
+  __shared__ SurvQueue s_q[8];  // one per warp (256 threads)
   for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     int e = base + threadIdx.x;
-    int i = -1, r = 0;
+    int i = -1, r = 0, ti = 0, np = 0;
+    int pj[MAXC];
+    long long pd[MAXC];
+    uint4 si = make_uint4(0, 0, 0, 0);
     LocalList ll;
     ll.cnt = ll.pairs = 0;
     ll.overflow = false;
     if (e < n) {
       int4 me = d.sorted[e];
       i = me.w >> 4;
+      ti = me.w & 15;
       r = rep_of(d, i);
       ll.me = i;
-      scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &ll, 0, nullptr);
+      scan_candidates(d, rtp, s_mask[ti], r2max, me, i, &ll, 0, nullptr, pj, pd, &np);
+      if (np) si = d.slots[i];
     }
+    warp_survivors(d, rtp, i, ti, si, pj, pd, np, &ll, s_q[threadIdx.x >> 5]);
     // beads with more than MAXC candidates are finished by k_cand_overflow
     int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
     if (ll.overflow) d.ovf[oslot] = e;
@@ -549,7 +617,9 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     LocalList cv;
     cv.cnt = cv.pairs = 0;
     cv.me = i;
-    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 1, nullptr);
+    int pj[MAXC], np = 0;
+    long long pd[MAXC];
+    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 1, nullptr, pj, pd, &np);
     const int a = atomicAdd(&d.cnt->cand_used, cv.cnt);
     if ((long long)a + cv.cnt > d.cand_pool) {
       atomicOr(d.err, ERR_CAND_CAP);
@@ -558,7 +628,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     const long long at = d.cand_fixed + a;
     int pairs = cv.pairs;
     int4* w = d.cand + at;
-    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 2, &w);
+    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 2, &w, pj, pd, &np);
     int4* lst = d.cand + at;
     for (int a = 1; a < cv.cnt; ++a) {
       int4 x = lst[a];
@@ -927,8 +997,12 @@ __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
 }
 
 // Does the record hold a bond removed or retyped in this call (step 6)?
+// Every bond of an angle contains its middle bead, every bond of a dihedral
+// one of its two middle beads, so those bitmap bits decide most records.
 __device__ __forceinline__ bool record_gone(const Dev& d, const int4& v, bool dih) {
-  if (!dih) return bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z);
+  if (!dih) return is_dirty(d, v.y) && (bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z));
+  const bool db = is_dirty(d, v.y), dc = is_dirty(d, v.z);
+  if (!db && !dc) return false;
   return bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z) || bond_gone(d, v.z, v.w & 0x0FFFFFFF);
 }
 
