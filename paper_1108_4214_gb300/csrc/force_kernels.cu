@@ -58,11 +58,13 @@ __device__ __forceinline__ float3 axpy(float a, float3 x, float3 y) {
 }
 __device__ __forceinline__ float3 scale(float a, float3 x) { return make_float3(a * x.x, a * x.y, a * x.z); }
 
-// Energy / virial accumulators: each FP32 term is added with an error-free
-// transformation (TwoSum), so a thread's partial sum is a float pair with
-// about twice the FP32 precision; warps combine the pairs the same way, and
-// only the per-warp totals enter FP64 (block sum, then one FP64 atomic per
-// component per block).  FP64 is thus used only where the reduction needs it.
+// Energy / virial accumulators: a thread sums its own few terms (at most a
+// few tens: its beads' bonds or its records over the launch) in plain FP32;
+// warps combine the threads' partials with an error-free transformation
+// (TwoSum), so a warp total is a float pair with about twice the FP32
+// precision, and only the per-warp totals enter FP64 (block sum, then one
+// striped FP64 atomic per component per block).  FP64 is thus used only
+// where the reduction needs it, and a thread holds 7 registers for it.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   float bp = __fsub_rn(s, a);
@@ -71,17 +73,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 struct EV {
-  float hi[7], lo[7];
+  float hi[7];
   __device__ EV() {
 #pragma unroll
-    for (int k = 0; k < 7; ++k) hi[k] = lo[k] = 0.f;
+    for (int k = 0; k < 7; ++k) hi[k] = 0.f;
   }
-  __device__ void add(int k, float x) {
-    float s, e;
-    two_sum(hi[k], x, s, e);
-    hi[k] = s;
-    lo[k] = __fadd_rn(lo[k], e);
-  }
+  __device__ void add(int k, float x) { hi[k] = __fadd_rn(hi[k], x); }
   // W_ab += r_a F_b + q_a G_b, the two terms summed in FP32 first
   __device__ void vir2(float3 r, float3 f, float3 q, float3 g) {
     add(1, r.x * f.x + q.x * g.x);
@@ -108,7 +105,7 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    float h = acc.hi[k], l = acc.lo[k];
+    float h = acc.hi[k], l = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       float h2 = __shfl_down_sync(FULL, h, o), l2 = __shfl_down_sync(FULL, l, o);
@@ -118,7 +115,7 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
       l = __fadd_rn(__fadd_rn(l, l2), e);
     }
     if (lane == 0) sh[k][wid] = (double)h + (double)l;
-    acc.hi[k] = acc.lo[k] = 0.f;
+    acc.hi[k] = 0.f;
   }
   __syncthreads();
   if (threadIdx.x < 7) {
