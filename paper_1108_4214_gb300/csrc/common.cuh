@@ -148,7 +148,7 @@ struct Dev {
   unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
   unsigned* bm_new;            // [W] beads with a formed or retyped bond
   int* live[2];                // [2*N] each: active (system << 31 | bead) entries between rounds
-  int* mate;                   // [2*N] creation / breakage partner, -1 = none
+  long long* mate;             // [2*N] creation / breakage match: partner | round << 32, -1 = none
   int* nom;                    // [2*N]
   int* ptr;                    // [2*N]
   int* round_hit;              // [2*R]
@@ -278,6 +278,10 @@ __device__ __forceinline__ void pdl_enter() {
 // Replica of bead i: the common single-system case needs no load, so later
 // loads that depend on the replica (box, offsets, streams) are not delayed.
 __device__ __forceinline__ int rep_of(const Dev& d, long long i) { return d.R == 1 ? 0 : d.rep[i]; }
+
+// a match of the matching rounds: the partner and the round it was made in
+__device__ __forceinline__ long long mate_pack(int round, int j) { return ((long long)round << 32) | (unsigned)j; }
+__device__ __forceinline__ int mate_partner(long long m) { return m < 0 ? -1 : (int)(unsigned)m; }
 
 __device__ __forceinline__ bool aborted(const unsigned* err) { return *(const volatile unsigned*)err != 0u; }
 

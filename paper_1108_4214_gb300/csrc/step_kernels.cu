@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
             d.brk_len[i] = (unsigned char)nbrk;
             for (int q = 0; q < nbrk; ++q) d.brk[4 * i + q] = ent[q];
             if (nbrk) {
-              d.mate[N + i] = broken ? ent[0].x : -1;
+              d.mate[N + i] = broken ? mate_pack(0, ent[0].x) : -1;
               d.ptr[N + i] = 0;
               d.nom[N + i] = ent[0].x;  // round 0 nomination: the most distant partner
             }
@@ -654,6 +654,21 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
 // or max_rounds rounds.  Per-bead lists are sorted, so a bead's nominee is
 // its first entry whose partner is still unmatched.
 // ---------------------------------------------------------------------------
+// First entry, from position p on, of bead i's list (system sys) whose
+// partner was unmatched when round `round` began; p is left at it (or at the
+// list's end, returning -1).
+__device__ __forceinline__ int first_open(const Dev& d, int sys, int i, int& p, int round) {
+  const long long o = sys ? d.N : 0;
+  const int len = sys ? d.brk_len[i] : d.cand_len[i];
+  const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
+  for (; p < len; ++p) {
+    const int q = lst[p].x;
+    const long long m = __ldcg(d.mate + o + q);
+    if (m < 0 || (m >> 32) == round) return q;
+  }
+  return -1;
+}
+
 __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_wait();  // cooperative: its successor is scheduled only when it ends
   if (aborted(d.err)) return;
@@ -679,7 +694,7 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
       const long long o = sys ? N : 0;
       const int j = d.nom[o + i];
       if (j >= 0 && ld_cg(d.nom + o + j) == i) {
-        d.mate[o + i] = j;
+        d.mate[o + i] = mate_pack(0, j);
         if (i < j) {
           const int r = rep_of(d, i);
           ++hits;
@@ -708,37 +723,41 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
         (void)valid;
       });
     } else {
-      // nomination: first list entry whose partner is still unmatched
-      for (int base = bi * blockDim.x; base < n; base += nb * blockDim.x) {
-        const int idx = base + threadIdx.x;
-        if (idx >= n) continue;
-        const int e = src[idx];
-        const int sys = (unsigned)e >> 31, i = e & 0x7FFFFFFF;
-        const long long o = sys ? N : 0;
-        int p = d.ptr[o + i];
-        const int len = sys ? d.brk_len[i] : d.cand_len[i];
-        const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
-        int j = -1;
-        while (p < len) {
-          int q = lst[p].x;
-          if (ld_cg(d.mate + o + q) == -1) {
-            j = q;
-            break;
-          }
-          ++p;
-        }
-        d.ptr[o + i] = p;
-        d.nom[o + i] = j;
-      }
-      if (solo) __syncthreads();
-      else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+      // One phase per round: a live bead's nominee is its first list entry
+      // that was unmatched when the round began (a match stamped with this
+      // round does not count yet), and the nominee's own nominee is found
+      // the same way from the nominee's list; a mutual pair is a match.  The
+      // two ends decide alike, so a round needs a single barrier.
       for (int base = bi * blockDim.x; base < n; base += nb * blockDim.x) {
         const int idx = base + threadIdx.x;
         bool keep = false;
         int e = 0;
         if (idx < n) {
           e = src[idx];
-          match_one((unsigned)e >> 31, e & 0x7FFFFFFF, keep);
+          const int sys = (unsigned)e >> 31, i = e & 0x7FFFFFFF;
+          const long long o = sys ? N : 0;
+          int p = ld_cg(d.ptr + o + i);  // written in an earlier round, maybe on another SM
+          const int j = first_open(d, sys, i, p, round);
+          d.ptr[o + i] = p;
+          if (j >= 0) {
+            // the nominee's pointer only ever skips partners matched before
+            // this round, whichever value is read
+            int pj = ld_cg(d.ptr + o + j);
+            if (first_open(d, sys, j, pj, round) == i) {
+              d.mate[o + i] = mate_pack(round, j);
+              if (i < j) {
+                const int r = rep_of(d, i);
+                ++hits;
+                matched_pairs.add(tg, r, sys, 1);
+                if (hr[sys] != r) {
+                  if (hr[sys] >= 0) d.round_hit[sys * R + hr[sys]] = 1;
+                  hr[sys] = r;
+                }
+              }
+            } else {
+              keep = true;
+            }
+          }
         }
         int at = block_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
         if (keep) dst[at] = e;
@@ -803,7 +822,7 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
 #pragma unroll
     for (int q = 0; q < SLOTS; ++q)
       if ((removed >> q) & 1u) o.n_killed += s_partner(s_get(s, q)) > i;
-    int j = d.brk_len[i] ? d.mate[N + i] : -1;
+    int j = d.brk_len[i] ? mate_partner(d.mate[N + i]) : -1;
     if (j >= 0) {
       int4 ent = d.brk[4 * i + d.ptr[N + i]];
       int k = ent.y;
@@ -827,7 +846,7 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
     }
   }
   if (ca) {
-    int j = d.mate[i];
+    int j = mate_partner(d.mate[i]);
     if (j >= 0) {
       int4 ent = d.cand[d.cand_start[i] + d.ptr[i]];
       int k = ent.y & 0xFF;
