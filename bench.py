@@ -51,6 +51,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest of the ranks' values (the slowest rank's time); x itself
+    when the job has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(beads_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Bead-updates/s of the whole job: every rank updates its own system of
+    beads_per_rank beads per step (weak scaling); seconds is the slowest
+    rank's time for the steps."""
+    return beads_per_rank * steps * world / seconds
+
+
 def workload(rank: int):
     from paper_1108_4214_gb300 import workloads as W
     s = W.config2()
@@ -232,11 +251,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(times)), dev)
     # per-phase device times from a second context that records events
     # between the phases (events inside the replayed work serialize the
     # kernels, so the headline above is timed without them)
@@ -256,7 +271,7 @@ def run_gpu(args):
     stats = {n: int(st[:, j].sum()) for j, n in enumerate(dynbond.STAT_NAMES)}
     ctx.forces(snaps[-1], force, ev)
     ctx.sync()
-    value = N * K * world / (total_ms / 1e3)
+    value = whole_job_value(N, K, world, total_ms / 1e3)
     result = dict(value=value, ms=total_ms / K, N=N, R=R, phases={k: float(np.mean(v)) for k, v in phases.items()},
                   stats=stats, na_before=na_before, nd_before=nd_before, clocks=clk.summary(), rank=rank,
                   world=world, name=s.name, tuning=tuning)
@@ -277,11 +292,8 @@ def run_gpu(args):
         t0 = time.perf_counter()
         ctx_h.run_host(pin_pos, k, pin_f, pin_ev)
         e2e_s += time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    result["e2e"] = dict(value=N * K * world / e2e_s, unit=UNIT, h2d_bytes_per_step=16 * N,
+    e2e_s = max_over_ranks(e2e_s, dev)
+    result["e2e"] = dict(value=whole_job_value(N, K, world, e2e_s), unit=UNIT, h2d_bytes_per_step=16 * N,
                          d2h_bytes_per_step=16 * N + 56 * R)
     ctx_h.close()
     ctx.close()
@@ -333,6 +345,12 @@ def run_batched(steps: int, warmup: int):
         ctx.step(pos_all[k], k)
         ctx.forces(pos_all[k], f, ev)
     t_b = timed(batched_call)
+    # one more (untimed) call for the algorithmic byte count of a call
+    topo = ctx.topology()
+    na0, nd0 = topo[1].shape[0], topo[2].shape[0]
+    st = ctx.step(pos_all[-1], warmup + steps, stats=True)
+    ctx.forces(pos_all[-1], f, ev)
+    stats = {n: int(st[:, j].sum()) for j, n in enumerate(dynbond.STAT_NAMES)}
     ctx.sync()
     ctx.close()
 
@@ -356,10 +374,15 @@ def run_batched(steps: int, warmup: int):
         c.close()
     vb = N * steps / (t_b / 1e3)
     vp = N * steps / (t_p / 1e3)
+    alg = algorithmic_bytes((na0, nd0), stats, N, full.n_replicas)
+    peak, peak_kind = peaks()
+    ach = alg / (t_b / steps * 1e-3) / 1e9
     return dict(workload=full.name, replicas=full.n_replicas, beads=N, steps=steps, warmup=warmup,
                 value=vb, ms_per_step=t_b / steps, plain_value=vp, plain_ms_per_step=t_p / steps,
                 speedup=vb / vp, tuning=tuning, unit=UNIT,
-                plain="one context per replica, called one after another on one stream")
+                plain="one context per replica, called one after another on one stream",
+                step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=ach, peak=peak, unit="GB/s",
+                                   frac=ach / peak, peak_source=peak_kind))
 
 
 def cpu_baseline(seconds: float):
