@@ -147,7 +147,7 @@ def algorithmic_bytes(stats_before, st, N, R):
     na0, nd0 = stats_before
     b = 16 * N + 16 * N  # positions + slots: candidate search / breakage scan
     b += 2 * 16 * c["candidates"] * 2  # edge list (both directions) written and read
-    b += 8 * 2 * c["candidates"] * max(1, c["create_rounds"])  # nominations per round
+    b += 8 * 2 * c["candidates"]  # one nomination per directed candidate (later rounds touch fewer)
     b += 16 * (na0 + nd0)  # purge reads both lists
     b += 16 * (c["angles_added"] + c["dihedrals_added"])  # appended records
     b += 16 * N + 16 * N + 16 * (c["n_angles"] + c["n_dihedrals"]) + 16 * N + 56 * R  # forces
