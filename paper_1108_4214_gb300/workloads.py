@@ -82,6 +82,106 @@ def rules_dna2(p_form: float = 0.5, p_break: float = 0.05, backbone_maxbond: boo
     return rules
 
 
+def rules_dna1_paper() -> List[Dict]:
+    """The paper's own rule list of its 1-bead-per-nucleotide DNA model
+    (Fig. 2 of Sec. 3; bead types A, T, C, G = 1..4; bond types 1 =
+    hybridization, 2 / 3 = the two directions of a backbone bond):
+    complementary beads within 0.6 sigma hybridize with probability 1;
+    a T bead and a C bead within 0.3 sigma ligate with probability 0.1 by a
+    directional backbone bond (the T end stores type 2, the C end type 3);
+    hybridization bonds longer than 1 sigma are killed; every bead holds at
+    most one bond of each of the types 1, 2 and 3 (the Fig. 2 maxbond lines,
+    whose printed argument order is read as max, bead types, bond type); the
+    typing rules 9-14 add backbone and base-pair angles and the dihedrals
+    across and along base pairs.  Run it with paircheck14, one nomination per
+    call and the two-uniform trial (the paper's own semantics)."""
+    star = ALL_BEADS
+    rules = [
+        dict(kind="createbond", btype=HYB, beads=(bit(A), bit(T)), dist=0.6, prob=1.0),
+        dict(kind="createbond", btype=HYB, beads=(bit(C), bit(G)), dist=0.6, prob=1.0),
+        dict(kind="createdirbond", btype=BB3, btype2=BB5, beads=(bit(T), bit(C)), dist=0.3, prob=0.1),
+        dict(kind="killbond", btype=HYB, dist=1.0),
+        dict(kind="maxbond", bonds=bit(HYB), beads=star, max=1),
+        dict(kind="maxbond", bonds=bit(BB3), beads=star, max=1),
+        dict(kind="maxbond", bonds=bit(BB5), beads=star, max=1),
+        dict(kind="createangle", type=1, beads=(star, star, star), bonds=(bit(BB3), bit(BB5))),
+        dict(kind="createangle", type=2, beads=(star, star, star), bonds=(bit(HYB), bit(BB3, BB5))),
+        dict(kind="createdihedral", type=1, beads=(star,) * 4, bonds=(bit(HYB), bit(BB3, BB5), bit(HYB))),
+        dict(kind="createdihedral", type=2, beads=(star,) * 4, bonds=(bit(BB3), bit(HYB), bit(BB5))),
+        dict(kind="createdihedral", type=3, beads=(star,) * 4, bonds=(bit(BB3), bit(HYB), bit(BB3))),
+        dict(kind="createdihedral", type=3, beads=(star,) * 4, bonds=(bit(BB5), bit(HYB), bit(BB5))),
+    ]
+    return rules
+
+
+def dna1_oligo_system(n_motifs: int = 64, template_nt: int = 16, oligo_nt: int = 4, seed: int = 6,
+                      spacing: float = 0.5, rise: float = 0.5, nick: float = 0.25) -> "System":
+    """Oligomers on templates in the paper's 1-bead model (the setting of its
+    oligomer-template examples, Sec. 3): each motif is a straight template
+    strand and template_nt / oligo_nt complementary oligomers lying
+    anti-parallel `rise` sigma beside it, already hybridized; consecutive
+    oligomers meet at a nick of `nick` sigma between a T end and a C end, so
+    ligation can close it.  Motifs sit on a cubic grid 4 sigma apart with
+    random orientations.  Backbone bead k stores type 2 toward bead k+1,
+    which stores type 3 toward bead k."""
+    rng = np.random.default_rng([seed, 61])
+    n_olig = template_nt // oligo_nt
+    per = 2 * template_nt
+    N = n_motifs * per
+    side = int(np.ceil(n_motifs ** (1.0 / 3.0)))
+    box = 4.0 * side + 4.0
+    pos = np.zeros((N, 3))
+    types = np.zeros(N, np.int32)
+    bonds = []
+    for m in range(n_motifs):
+        b0 = m * per
+        seq = rng.integers(1, 5, size=template_nt).astype(np.int32)
+        for j in range(n_olig - 1):  # template under each nick: oligo ends T (over A) and C (over G)
+            seq[template_nt - oligo_nt * (j + 1)] = A
+            seq[template_nt - oligo_nt * (j + 1) - 1] = G
+        types[b0:b0 + template_nt] = seq
+        u = _unit_vectors(rng, 1)[0]
+        w = _unit_vectors(rng, 1)[0]
+        v = w - np.dot(w, u) * u
+        v /= np.linalg.norm(v)
+        o = 2.0 + 4.0 * np.array([m % side, (m // side) % side, m // (side * side)], np.float64)
+        t = np.arange(template_nt)
+        pos[b0:b0 + template_nt] = o + spacing * t[:, None] * u
+        bonds.append(np.stack([b0 + t[:-1], b0 + t[1:], np.full(template_nt - 1, BB3),
+                               np.full(template_nt - 1, BB5)], axis=1))
+        # oligomer beads: oligo j, position k (5' to 3') opposite template bead
+        # template_nt - 1 - (oligo_nt * j + k)
+        for j in range(n_olig):
+            first = b0 + template_nt + oligo_nt * j
+            for k in range(oligo_nt):
+                tb = template_nt - 1 - (oligo_nt * j + k)
+                shift = 0.0
+                if k == 0 and j > 0:
+                    shift = -0.5 * (spacing - nick)  # toward the previous oligomer's last bead
+                if k == oligo_nt - 1 and j < n_olig - 1:
+                    shift = 0.5 * (spacing - nick)
+                pos[first + k] = o + (spacing * tb - shift) * u + rise * v
+                types[first + k] = COMPLEMENT[seq[tb]]
+                bonds.append(np.array([[b0 + tb, first + k, HYB, HYB]]))
+            kk = np.arange(oligo_nt - 1)
+            bonds.append(np.stack([first + kk, first + kk + 1, np.full(oligo_nt - 1, BB3),
+                                   np.full(oligo_nt - 1, BB5)], axis=1))
+    ff = forcefield_dna2()
+    for t_ in (HYB, BB3, BB5):
+        ff["bond_r0"][t_] = 0.6
+    ff["angle_k"][:4] = 2.0
+    ff["dihedral_k"][:4] = 1.0
+    ff["dihedral_d"][:4] = 1
+    return System(
+        name=f"dna1-oligo-{N}", bead_offset=np.array([0, N], np.int64),
+        box_q=np.array([int(np.rint(box * QSCALE))], np.int64), types=types,
+        bonds=np.concatenate(bonds).astype(np.int32), rules=rules_dna1_paper(), pos0=pos, seed=seed,
+        sigma_perturb=0.05,
+        params=dict(default_params(seed), paircheck14=1, max_rounds=1, prob_mode=1),
+        forcefield=ff,
+    )
+
+
 def forcefield_dna2() -> Dict[str, np.ndarray]:
     """Bonded force-field tables (index = type): harmonic bonds E = K (r - r0)^2
     with K = 100, r0 = 1 for bond types 1..4; cosine angles E = K (1 + cos theta)

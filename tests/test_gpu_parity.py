@@ -132,6 +132,20 @@ def test_random_systems_all_rule_kinds(seed):
     run_parity(s, 4)
 
 
+def test_paper_exact_mode_oligomers_on_templates():
+    """The paper's own 1-bead DNA rule list (Fig. 2) in the paper's own
+    semantics -- paircheck14, one nomination per call, the two-uniform trial
+    average -- on oligomers hybridized to templates: ligations across the
+    nicks (createdirbond), kills of stretched hybridization bonds and the
+    typing rules 9-14, bit-exact against the oracle for 12 calls."""
+    s = W.dna1_oligo_system()
+    o, worst = run_parity(s, 12)
+    bonds = o.topology()[0]
+    ligated = int(((bonds[:, 2] == W.BB3) & (bonds[:, 3] == W.BB5)).sum()) - 64 * (16 - 1) - 64 * 4 * 3
+    assert ligated > 0, "no ligation happened"
+    print("ligated", ligated, "max force / ev error", max(w[0] for w in worst), max(w[1] for w in worst))
+
+
 def test_rounds_matching_and_single_nomination():
     pos2 = [[2.0, 2, 2], [2.0, 3.0, 2], [2.5, 2, 2], [2.95, 2.6, 2]]
     rules = [dict(kind="createbond", btype=1, beads=(W.bit(1), W.bit(2)), dist=1.1, prob=1.0),
