@@ -268,6 +268,19 @@ dynbond_status dynbond_run_host(dynbond_ctx* ctx, const int32_t* h_pos, uint64_t
 dynbond_status dynbond_get_topology(dynbond_ctx* ctx, dynbond_topology* topo);
 
 /*
+ * Order-independent 64-bit hash of each replica's topology (not part of the
+ * paper; for logging a long run call by call):
+ *   h_r = sum over bond ends (i stores t toward j) of mix(i << 32 | j << 4 | t)
+ *       + sum over angles (a, b, c, t) of chain(0xA, a, b, c, t)
+ *       + sum over dihedrals (a, b, c, d, t) of chain(0xD, a, b, c, d, t)   (mod 2^64),
+ * bead ids local to the replica, records canonical as exported, mix the
+ * splitmix64 finalizer (Steele, Lea, Flood, OOPSLA 2014) and
+ * chain(x0, x1, ...) = mix(...mix(mix(x0) ^ x1)... ^ xn).
+ * Writes n_replicas values to h_out (host).  Synchronizes.
+ */
+dynbond_status dynbond_topology_hash(dynbond_ctx* ctx, uint64_t* h_out);
+
+/*
  * Autotuning of launch geometry (not part of the paper): the cell edge (1, 1.5,
  * 2 or 3 x the largest creation distance) and the bead-pass grid size (4, 8 or
  * 16 blocks per SM) are chosen by timing the front of a call (cell binning and

@@ -56,6 +56,7 @@ struct dynbond_ctx {
   int* d_nc = nullptr;
   long long* d_cb = nullptr;
   dynbond_tuning tuning{};
+  unsigned long long* d_hash = nullptr;  // per-replica topology hashes
   bool tuned = false;
 };
 
@@ -690,6 +691,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(c->h2d_pos, N);
   ALLOC(c->d2h_force, N);
   ALLOC(c->d2h_ev, 7 * R);
+  ALLOC(c->d_hash, R);
 #undef ALLOC
   d.off = p_off;
   d.box = p_box;
@@ -900,6 +902,21 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
 dynbond_status dynbond_sync(dynbond_ctx* c) {
   if (!c) return DYNBOND_EINVAL;
   if (c->sticky) return c->sticky;
+  return device_status(c);
+}
+
+dynbond_status dynbond_topology_hash(dynbond_ctx* c, uint64_t* h_out) {
+  if (!c || !h_out) return DYNBOND_EINVAL;
+  if (c->sticky) return c->sticky;
+  const int R = c->R;
+  unsigned long long* d_h = c->d_hash;
+  cudaError_t e = cudaMemsetAsync(d_h, 0, 8 * (size_t)R, c->stream);
+  if (e == cudaSuccess) {
+    k_topo_hash<<<c->nsm * 4, 256, 0, c->stream>>>(c->d, d_h);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_h, 8 * (size_t)R, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return fail(c, DYNBOND_ECUDA, std::string("topology hash: ") + cudaGetErrorString(e));
   return device_status(c);
 }
 

@@ -354,6 +354,56 @@ __global__ void __launch_bounds__(256) k_angle_dihedral_forces(Dev d, FF ff) {
   if (racc >= 0) flush_ev(d, acc, racc);
 }
 
+// Order-independent topology hash (see dynbond_topology_hash): per replica,
+// the sum of splitmix64-mixed bond ends and interaction records.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_topo_hash(Dev d, unsigned long long* h) {
+  if (aborted(d.err)) return;
+  const int R = d.R;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += stride) {
+    const int r = rep_of(d, i);
+    const long long o = d.off[r];
+    const uint4 s = d.slots[i];
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      const unsigned v = s_get(s, q);
+      if (!v) continue;
+      const unsigned long long j = (unsigned long long)(s_partner(v) - o);
+      acc += mix64(((unsigned long long)(i - o) << 32) | (j << 4) | (unsigned long long)s_type(v));
+    }
+    if (acc) atomicAdd(h + r, acc);
+  }
+  for (int r = 0; r < R; ++r) {
+    const long long o = d.off[r];
+    const int4* ang = d.ang + 6 * o;
+    const int4* dih = d.dih + 18 * o;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < d.n_ang[r]; k += stride) {
+      const int4 a = ang[k];
+      unsigned long long z = mix64(0xA);
+      z = mix64(z ^ (unsigned long long)(a.x - o));
+      z = mix64(z ^ (unsigned long long)(a.y - o));
+      z = mix64(z ^ (unsigned long long)(a.z - o));
+      atomicAdd(h + r, mix64(z ^ (unsigned long long)a.w));
+    }
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < d.n_dih[r]; k += stride) {
+      const int4 a = dih[k];
+      unsigned long long z = mix64(0xD);
+      z = mix64(z ^ (unsigned long long)(a.x - o));
+      z = mix64(z ^ (unsigned long long)(a.y - o));
+      z = mix64(z ^ (unsigned long long)(a.z - o));
+      z = mix64(z ^ (unsigned long long)((a.w & 0x0FFFFFFF) - o));
+      atomicAdd(h + r, mix64(z ^ (unsigned long long)((unsigned)a.w >> 28)));
+    }
+  }
+}
+
 // sum the striped copies of the energy / virial, write them out and clear
 // the accumulators for the next force call
 __global__ void k_ev_out(Dev d) {

@@ -39,5 +39,6 @@ const uint4* internal_slots(const dynbond_ctx* ctx, long long* n_beads, long lon
 __global__ void k_bond_forces(Dev d, FF ff);
 __global__ void k_angle_dihedral_forces(Dev d, FF ff);
 __global__ void k_ev_out(Dev d);
+__global__ void k_topo_hash(Dev d, unsigned long long* h);
 
 }  // namespace dynbond

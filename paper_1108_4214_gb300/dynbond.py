@@ -29,7 +29,7 @@ STAT_NAMES = [
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
            "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
            "dynbond_forces_noalloc", "dynbond_autotune", "dynbond_md_create", "dynbond_md_advance",
-           "dynbond_md_destroy"]
+           "dynbond_md_destroy", "dynbond_topology_hash"]
 NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
@@ -122,6 +122,8 @@ def load() -> ctypes.CDLL:
     L.dynbond_md_advance.argtypes = [c_p, c_p, c_p, c_i64, c_u64, c_p]
     L.dynbond_md_destroy.restype = None
     L.dynbond_md_destroy.argtypes = [c_p]
+    L.dynbond_topology_hash.restype = c_i32
+    L.dynbond_topology_hash.argtypes = [c_p, c_p]
     L.dynbond_autotune.restype = c_i32
     L.dynbond_autotune.argtypes = [c_p, c_p, c_p]
     L.dynbond_forces_noalloc.restype = c_i32
@@ -293,6 +295,12 @@ class Context:
         t = Tuning()
         self._check(self.L.dynbond_autotune(self.h, c_p(_ptr(pos)), ctypes.byref(t)))
         return {n: getattr(t, n) for n, _ in Tuning._fields_}
+
+    def topology_hash(self) -> np.ndarray:
+        """dynbond_topology_hash: one order-independent 64-bit hash per replica."""
+        h = np.zeros(self.R, np.uint64)
+        self._check(self.L.dynbond_topology_hash(self.h, c_p(h.ctypes.data)))
+        return h
 
     def topology(self):
         """(bonds [nb, 4], angles [na, 4], dihedrals [nd, 5]) canonical and sorted (numpy)."""

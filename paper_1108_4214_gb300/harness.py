@@ -40,6 +40,7 @@ def run_dpd_loop(system: W.System, n_calls: int, md_steps_per_call: int = 10, du
     ev_dev = torch.empty((7,), dtype=torch.float64, device=dev)
     dumps: List[Dump] = []
     counts = []
+    hashes = []  # topology hash after every call (dynbond_topology_hash)
     t_md = t_bond = 0.0
     for c in range(n_calls):
         torch.cuda.synchronize()
@@ -57,11 +58,13 @@ def run_dpd_loop(system: W.System, n_calls: int, md_steps_per_call: int = 10, du
         st = ctx.step(pos, c, stats=True)
         t_bond += time.perf_counter() - t2
         counts.append(st[:, [12, 13, 14]].sum(axis=0))
+        hashes.append(ctx.topology_hash().copy())
         if dump:
             dumps.append(Dump(c, snap, bonds_before, ev, st, ctx.topology()))
     v = vel.cpu().numpy()[:, :3].astype(np.float64)
     kT_measured = float(np.mean(v ** 2))
     md.close()
     ctx.close()
-    return dict(dumps=dumps, counts=np.array(counts), kT=kT_measured, seconds_md=t_md, seconds_step=t_bond,
+    return dict(dumps=dumps, counts=np.array(counts), hashes=np.array(hashes), kT=kT_measured, seconds_md=t_md,
+                seconds_step=t_bond,
                 n_md_steps=n_calls * md_steps_per_call, n_calls=n_calls)

@@ -72,3 +72,43 @@ def ladder_1bead_positions(sep=0.5, spacing=0.5):
         p[k] = (5.0 + spacing * k, 5.0, 5.0)
         p[7 - k] = (5.0 + spacing * k, 5.0 + sep, 5.0)
     return p
+
+
+# ---------------------------------------------------------------------------
+# The topology hash of include/dynbond.h (dynbond_topology_hash), restated
+# from its definition for exported topologies: bond ends, angles and
+# dihedrals mixed with the splitmix64 finalizer and summed mod 2^64.
+# ---------------------------------------------------------------------------
+M64 = (1 << 64) - 1
+
+
+def _mix(z):
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def _chain(first, cols):
+    z = _mix(np.full(len(cols[0]), first, dtype=np.uint64))
+    for c in cols:
+        z = _mix(z ^ np.asarray(c, dtype=np.int64).astype(np.uint64))
+    return z
+
+
+def topology_hash(bonds, angles, dihedrals):
+    """Hash of one replica's topology (bead ids local to the replica)."""
+    b = np.asarray(bonds, np.int64).reshape(-1, 4)
+    u64 = lambda x: np.asarray(x, np.int64).astype(np.uint64)
+    ends = np.concatenate([
+        (u64(b[:, 0]) << np.uint64(32)) | (u64(b[:, 1]) << np.uint64(4)) | u64(b[:, 2]),
+        (u64(b[:, 1]) << np.uint64(32)) | (u64(b[:, 0]) << np.uint64(4)) | u64(b[:, 3])])
+    a = np.asarray(angles, np.int64).reshape(-1, 4)
+    d = np.asarray(dihedrals, np.int64).reshape(-1, 5)
+    total = 0
+    with np.errstate(over="ignore"):
+        for part in (_mix(ends), _chain(0xA, [a[:, k] for k in range(4)]),
+                     _chain(0xD, [d[:, k] for k in range(5)])):
+            total = (total + int(part.sum(dtype=np.uint64))) & M64
+    return total

@@ -9,6 +9,7 @@ import dataclasses
 import numpy as np
 import pytest
 
+from helpers import topology_hash
 from oracle import oracle as O
 from paper_1108_4214_gb300 import workloads as W
 
@@ -29,6 +30,9 @@ def replay(system, res):
         assert np.array_equal(st, d.stats), (d.call, st, d.stats)
         for g, r in zip(d.topology, o.topology()):
             assert np.array_equal(g, r), d.call
+        # the hash logged after that call names the same topology
+        assert int(res["hashes"][d.call][0]) == topology_hash(*o.topology()), d.call
+    assert len(res["hashes"]) == len(res["counts"])
     assert worst_ev <= EV_TOL, worst_ev
     return worst_ev
 
