@@ -618,9 +618,12 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.n_bonds, R);
   ALLOC(d.cnt, 1);
   ALLOC(d.err, 1);
-  ALLOC(d.cell_start, c->n_cells * c->rt.n_cls + 1);
+  // 4 leading ints (16 B, keeping the scan's vector loads aligned): element -1
+  // stays 0, so cell k's range after the scatter is [cell_start[k-1], cell_start[k])
+  ALLOC(d.cell_start, c->n_cells * c->rt.n_cls + 5);
+  CUDA_TRY(c, cudaMemsetAsync(d.cell_start, 0, 4 * (size_t)(c->n_cells * c->rt.n_cls + 5), c->stream));
+  d.cell_start += 4;
   ALLOC(d.bead_cell, N);
-  ALLOC(d.bead_rank, N);
   ALLOC(d.sorted, N);
   d.cand_fixed = N * CAND_FAST;
   d.cand_pool = 2 * N + 65536;

@@ -128,9 +128,9 @@ struct Dev {
   // per-call scratch
   Counters* cnt;
   unsigned* err;               // sticky error word
-  int* cell_start;             // [n_keys + 1], key = class * n_cells + cell
+  int* cell_start;             // [-1, n_keys], key = class * n_cells + cell: counts, then starts
+                               // (exclusive scan), then ends after the scatter; cell_start[-1] = 0
   int* bead_cell;              // [N]
-  int* bead_rank;              // [N]
   int4* sorted;                // [N] (x, y, z, gid << 4 | type)
   int4* cand;                  // (partner, rule | mytype << 8, d2 lo, d2 hi): CAND_FAST slots per
                                // sorted entry, then a pool of cand_pool entries for longer lists

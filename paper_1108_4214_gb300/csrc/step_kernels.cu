@@ -44,130 +44,165 @@ __device__ __forceinline__ int warp_alloc(int* counter, int want) {
 // ---------------------------------------------------------------------------
 // k_bead
 // ---------------------------------------------------------------------------
+// Breakage nomination of bead i (Appendix steps 3 and 5): its symmetric bonds
+// of a type named by breakbond / convertbond / killbond with both ends
+// reactive, sorted by (-d2, partner); killbond marks; settled pairs.
+// Returns the flags of the activity bitmaps (bit 0: active in the edit,
+// bit 1: nominates in the matching).
+__device__ __forceinline__ unsigned bead_breakage(const Dev& d, const RuleTab& rt, const int4* __restrict__ pos,
+                                                  long long i, int r, const CountTargets<2>& tg, ReplicaCounts<2>& cnt,
+                                                  int& hit_r) {
+  const long long N = d.N;
+  const uint4 s = d.slots[i];
+  const int4 p = pos[i];
+  const int L = (int)d.box[r];
+  unsigned km = 0;
+  int4 ent[SLOTS];
+  int nbrk = 0, ncand_b = 0;
+  int nbt = 0;        // slots of i holding a type named by break / convert / kill rules
+  uint4 sj_one = s;   // slots of the partner (meaningful when nbrk == 1)
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    unsigned v = s_get(s, q);
+    if (!v || !has_bit(rt.breakish, s_type(v))) continue;
+    ++nbt;
+    int bty = s_type(v), j = s_partner(v);
+    if (!has_bit(rt.reactive, d.type[j])) continue;
+    const uint4 sj = d.slots[j];
+    if (s_type_to(sj, (int)i) != bty) continue;
+    sj_one = sj;
+    long long dd = dist2(p, pos[j], L);
+    int rule = -1;
+    for (int q2 = rt.bk_start[bty], q3 = rt.bk_start[bty + 1]; q2 < q3; ++q2) {
+      int k = rt.bk_list[q2];
+      int kd = rt.kind[k];
+      if (kd == DYNBOND_KILLBOND && dd > rt.r2[k]) km |= 1u << q;
+      if ((kd == DYNBOND_BREAKBOND && dd > rt.r2[k]) || kd == DYNBOND_CONVERTBOND) rule = k;
+    }
+    if (rule < 0) continue;
+    // insert sorted by (-d2, partner)
+    long long key = -dd;
+    int at = nbrk;
+    while (at > 0) {
+      long long pk = ((long long)(unsigned)ent[at - 1].w << 32) | (unsigned)ent[at - 1].z;
+      if (pk < key || (pk == key && ent[at - 1].x < j)) break;
+      ent[at] = ent[at - 1];
+      --at;
+    }
+    ent[at] = make_int4(j, rule, (int)(unsigned)(unsigned long long)key, (int)(key >> 32));
+    ++nbrk;
+    ncand_b += j > i;
+  }
+  cnt.add(tg, r, 0, ncand_b);
+  // A settled pair: both ends hold exactly one bond of a type named by
+  // break / convert / kill rules -- each other.  They nominate each other in
+  // round 0 and nobody else can nominate either, so they match there
+  // whatever else happens; the trial (step 5) is drawn now and only a
+  // successful one reaches the edit.
+  bool settled = false;
+  if (nbrk == 1 && nbt == 1) {
+    int nbt_j = 0;
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+      unsigned v = s_get(sj_one, q);
+      nbt_j += v && has_bit(rt.breakish, s_type(v));
+    }
+    settled = nbt_j == 1;
+  }
+  bool broken = false;
+  if (settled) {
+    const int j = ent[0].x, k = ent[0].y;
+    const int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
+    broken = trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k]);
+    if (j > i) {
+      cnt.add(tg, r, 1, 1);  // the pair matched in round 0
+      if (hit_r != r) {
+        if (hit_r >= 0) d.round_hit[d.R + hit_r] = 1;
+        hit_r = r;
+      }
+    }
+  }
+  const bool ba = km || (nbrk && !settled) || broken;
+  if (ba) {
+    d.killmask[i] = (unsigned char)km;
+    d.brk_len[i] = (unsigned char)nbrk;
+    for (int q = 0; q < nbrk; ++q) d.brk[4 * i + q] = ent[q];
+    if (nbrk) {
+      d.mate[N + i] = broken ? mate_pack(0, ent[0].x) : -1;
+      d.ptr[N + i] = 0;
+      d.nom[N + i] = ent[0].x;  // round 0 nomination: the most distant partner
+    }
+  }
+  return (ba ? 1u : 0u) | (nbrk > 0 && !settled ? 2u : 0u);
+}
+
+// Per block of 256 consecutive beads: every thread bins its own bead when it
+// can form bonds (Appendix step 2); the beads with a bond of a type named by
+// a breakage rule are gathered in shared memory and nominated by the first
+// threads of the block, so the (rarer, longer) breakage work runs on dense
+// warps; the activity bitmaps of the block's 8 words are assembled in shared
+// memory.
 __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
   const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
   const CountTargets<2> tg{{d.stats + ST_BREAK_CANDIDATES, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
   ReplicaCounts<2> cnt;
-  int hit_r = -1;  // replica of the breakage pairs this thread matched (settled pairs, below)
+  int hit_r = -1;  // replica of the breakage pairs this thread matched (settled pairs)
+  __shared__ int s_list[256];
+  __shared__ int s_n;
+  __shared__ unsigned s_ba[8], s_bn[8];
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
-    long long i = base + threadIdx.x;
-    bool valid = i < N;
-    int nbrk = 0, ncand_b = 0, r = 0;
-    bool ba = false, nominates = false;
-    if (valid) {
-      r = rep_of(d, i);
-      int bt = d.type[i];
-      uint4 s = d.slots[i];
-      int4 p = pos[i];
-      int L = (int)d.box[r];
+    if (threadIdx.x < 8) s_ba[threadIdx.x] = s_bn[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const long long i = base + threadIdx.x;
+    if (i < N) {
+      const int r = rep_of(d, i);
+      const int bt = d.type[i];
+      const uint4 s = d.slots[i];
+      const int4 p = pos[i];
+      const int L = (int)d.box[r];
       if (p.x < 0 || p.y < 0 || p.z < 0 || p.x >= L || p.y >= L || p.z >= L) {
         atomicOr(d.err, ERR_POS);
         d.bead_cell[i] = -1;
       } else {
-        // creation: eligible beads are binned (Appendix step 2 searches them)
         if (creation_eligible(rt, bt, s)) {
-          int nc = d.nc[r];
+          const int nc = d.nc[r];
           const float f = (float)nc / (float)L;
           long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f), cz = cell_of(p.z, nc, L, f);
           long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nc + cz;
-          d.bead_rank[i] = atomicAdd(&d.cell_start[c], 1);
+          atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the ranks
           d.bead_cell[i] = (int)c;
         } else {
           d.bead_cell[i] = -1;
         }
-        // breakage: symmetric bonds of a type named by breakbond / convertbond /
-        // killbond (Appendix steps 3 and 5), both ends reactive
+        bool brk = false;
         if (rt.breakish && has_bit(rt.reactive, bt)) {
-          unsigned km = 0;
-          int4 ent[SLOTS];
-          int nbt = 0;        // slots of i holding a type named by break / convert / kill rules
-          uint4 sj_one = s;   // slots of the partner (meaningful when nbrk == 1)
 #pragma unroll
           for (int q = 0; q < SLOTS; ++q) {
-            unsigned v = s_get(s, q);
-            if (!v || !has_bit(rt.breakish, s_type(v))) continue;
-            ++nbt;
-            int bty = s_type(v), j = s_partner(v);
-            if (!has_bit(rt.reactive, d.type[j])) continue;
-            const uint4 sj = d.slots[j];
-            if (s_type_to(sj, (int)i) != bty) continue;
-            sj_one = sj;
-            long long dd = dist2(p, pos[j], L);
-            int rule = -1;
-            for (int q2 = rt.bk_start[bty], q3 = rt.bk_start[bty + 1]; q2 < q3; ++q2) {
-              int k = rt.bk_list[q2];
-              int kd = rt.kind[k];
-              if (kd == DYNBOND_KILLBOND && dd > rt.r2[k]) km |= 1u << q;
-              if ((kd == DYNBOND_BREAKBOND && dd > rt.r2[k]) || kd == DYNBOND_CONVERTBOND) rule = k;
-            }
-            if (rule < 0) continue;
-            // insert sorted by (-d2, partner)
-            long long key = -dd;
-            int at = nbrk;
-            while (at > 0) {
-              long long pk = ((long long)(unsigned)ent[at - 1].w << 32) | (unsigned)ent[at - 1].z;
-              if (pk < key || (pk == key && ent[at - 1].x < j)) break;
-              ent[at] = ent[at - 1];
-              --at;
-            }
-            ent[at] = make_int4(j, rule, (int)(unsigned)(unsigned long long)key, (int)(key >> 32));
-            ++nbrk;
-            ncand_b += j > i;
+            const unsigned v = s_get(s, q);
+            brk |= v && has_bit(rt.breakish, s_type(v));
           }
-          // A settled pair: both ends hold exactly one bond of a type named by
-          // break / convert / kill rules -- each other.  They nominate each
-          // other in round 0 and nobody else can nominate either, so they
-          // match there whatever else happens; the trial (step 5) is drawn
-          // now and only a successful one reaches the edit.
-          bool settled = false;
-          if (nbrk == 1 && nbt == 1) {
-            int nbt_j = 0;
-#pragma unroll
-            for (int q = 0; q < SLOTS; ++q) {
-              unsigned v = s_get(sj_one, q);
-              nbt_j += v && has_bit(rt.breakish, s_type(v));
-            }
-            settled = nbt_j == 1;
-          }
-          bool broken = false;
-          if (settled) {
-            const int j = ent[0].x, k = ent[0].y;
-            const int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
-            broken = trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k]);
-            if (j > i) {
-              cnt.add(tg, r, 1, 1);  // the pair matched in round 0
-              if (hit_r != r) {
-                if (hit_r >= 0) d.round_hit[d.R + hit_r] = 1;
-                hit_r = r;
-              }
-            }
-          }
-          if (km || (nbrk && !settled) || broken) {
-            ba = true;
-            d.killmask[i] = (unsigned char)km;
-            d.brk_len[i] = (unsigned char)nbrk;
-            for (int q = 0; q < nbrk; ++q) d.brk[4 * i + q] = ent[q];
-            if (nbrk) {
-              d.mate[N + i] = broken ? mate_pack(0, ent[0].x) : -1;
-              d.ptr[N + i] = 0;
-              d.nom[N + i] = ent[0].x;  // round 0 nomination: the most distant partner
-            }
-          }
-          nominates = nbrk > 0 && !settled;
         }
+        if (brk) s_list[atomicAdd(&s_n, 1)] = threadIdx.x;
       }
     }
-    unsigned m = __ballot_sync(FULL, ba), mn = __ballot_sync(FULL, nominates);
-    if (lane == 0 && valid) {
-      d.bm_ba[i >> 5] = m;
-      d.bm_bn[i >> 5] = mn;
+    __syncthreads();
+    if ((int)threadIdx.x < s_n) {
+      const long long k = base + s_list[threadIdx.x];
+      const unsigned fl = bead_breakage(d, rt, pos, k, rep_of(d, k), tg, cnt, hit_r);
+      const int o = (int)(k - base);
+      if (fl & 1u) atomicOr(&s_ba[o >> 5], 1u << (o & 31));
+      if (fl & 2u) atomicOr(&s_bn[o >> 5], 1u << (o & 31));
     }
-    if (valid) cnt.add(tg, r, 0, ncand_b);
+    __syncthreads();
+    if (threadIdx.x < 8 && base + 32 * threadIdx.x < N) {
+      d.bm_ba[(base >> 5) + threadIdx.x] = s_ba[threadIdx.x];
+      d.bm_bn[(base >> 5) + threadIdx.x] = s_bn[threadIdx.x];
+    }
   }
   cnt.flush_block(tg);
   // settled pairs count as round-0 breakage matches of their replica
@@ -260,7 +295,9 @@ __global__ void __launch_bounds__(256) k_scatter(Dev d) {
     if (c < 0) continue;
     int4 p = pos[i];
     p.w = (int)((i << 4) | d.type[i]);
-    d.sorted[d.cell_start[c] + d.bead_rank[i]] = p;
+    // after the scatter cell_start[c] holds the end of cell c, i.e. the start
+    // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
+    d.sorted[atomicAdd(&d.cell_start[c], 1)] = p;
   }
 }
 
@@ -406,8 +443,8 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
       q0[ab] = 0;
       if (a < noff && b < noff) {
         const int row = cbk + (xs[a] * nc + ys[b]) * nc;
-        q0[ab] = d.cell_start[row + lo];
-        len = d.cell_start[row + hi + 1] - q0[ab];
+        q0[ab] = d.cell_start[row + lo - 1];
+        len = d.cell_start[row + hi] - q0[ab];
       }
       ex[ab + 1] = ex[ab] + len;
     }
@@ -458,7 +495,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
           for (int run = 0; run < 2; ++run) {
             int lo = run ? w0 : z0, hi = run ? w1 : z1;
             if (hi < lo) continue;
-            int q0 = d.cell_start[row + lo], q1 = d.cell_start[row + hi + 1];
+            int q0 = d.cell_start[row + lo - 1], q1 = d.cell_start[row + hi];
             for (int q = q0; q < q1; ++q) {
               int4 o = d.sorted[q];
               long long dd = dist2(me, o, L);
