@@ -302,7 +302,7 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   mark(c, c->ev_step, k++);
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
-  E(launch(c, k_scatter, c->grid_bead, 256, d));
+  E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
   mark(c, c->ev_step, k++);
   E(launch(c, k_candidates, c->grid_cand, 256, d, c->d_rt));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
@@ -311,7 +311,7 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   mark(c, c->ev_step, k++);
   E(launch(c, k_edit, c->grid_edit, 256, d, c->d_rt));
   mark(c, c->ev_step, k++);
-  E(launch(c, k_purge, c->nsm * 2, PURGE_TILE / 8, d));
+  E(launch(c, k_purge, c->nsm * 4, PURGE_TILE / PURGE_PER_THREAD, d));
   E(launch(c, k_fill, c->nsm * 4, FILL_TILE, d));
   mark(c, c->ev_step, k++);
   E(launch(c, k_rebuild, c->grid_seg, 256, d, c->d_rt, 0));
@@ -448,7 +448,7 @@ cudaError_t enqueue_front(dynbond_ctx* c) {
   E(launch(c, k_setup, c->nsm * 2, 1024, d));
   E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
-  E(launch(c, k_scatter, c->grid_bead, 256, d));
+  E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
   E(launch(c, k_candidates, c->grid_cand, 256, d, c->d_rt));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   return cudaGetLastError();
@@ -638,6 +638,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.bm_ca, c->W);
   ALLOC(d.bm_ba, c->W);
   ALLOC(d.bm_bn, c->W);
+  ALLOC(d.bm_bk, c->W);
   ALLOC(d.bm_dirty, c->W);
   ALLOC(d.bm_new, c->W);
   ALLOC(d.live[0], 2 * N);
@@ -739,7 +740,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemcpyAsync(d.n_bonds, nb_rep.data(), 8 * R, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(d.tb_beads, tbeads.data(), 4 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
-  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_bn, d.bm_dirty, d.bm_new})
+  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_bn, d.bm_bk, d.bm_dirty, d.bm_new})
     CUDA_TRY(c, cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)c->W, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_ang, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_dih, 0, 4 * R, s));

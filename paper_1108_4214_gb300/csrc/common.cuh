@@ -145,6 +145,7 @@ struct Dev {
   unsigned* bm_ca;             // [W] creation-active beads
   unsigned* bm_ba;             // [W] breakage/kill-active beads
   unsigned* bm_bn;             // [W] beads nominating a breakage partner
+  unsigned* bm_bk;             // [W] beads holding a bond of a type named by a breakage rule
   unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
   unsigned* bm_new;            // [W] beads with a formed or retyped bond
   int* live[2];                // [2*N] each: active (system << 31 | bead) entries between rounds

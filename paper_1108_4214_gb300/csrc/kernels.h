@@ -6,7 +6,8 @@
 
 namespace dynbond {
 
-constexpr int PURGE_TILE = 4096;   // 512 threads x 8 records
+constexpr int PURGE_TILE = 1024;   // 256 threads x 4 records (small tiles balance the blocks)
+constexpr int PURGE_PER_THREAD = 4;
 constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
 constexpr int BEAD_TILE = 512;     // beads per force work item (2 per thread)
@@ -19,7 +20,7 @@ struct FF {
 
 __global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_scan_cells(Dev d);
-__global__ void k_scatter(Dev d);
+__global__ void k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks);
 __global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_match(Dev d, const RuleTab* __restrict__ rtp);

@@ -21,7 +21,6 @@
 
 namespace dynbond {
 
-constexpr int PURGE_PER_THREAD = 8;  // records per thread; PURGE_TILE / 8 threads per block
 constexpr int SCAN_PER_THREAD = 32;  // cells per thread in the histogram scan
 constexpr int SCAN_BATCH = 2;  // candidate entries loaded together
 constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
@@ -136,29 +135,20 @@ __device__ __forceinline__ unsigned bead_breakage(const Dev& d, const RuleTab& r
   return (ba ? 1u : 0u) | (nbrk > 0 && !settled ? 2u : 0u);
 }
 
-// Per block of 256 consecutive beads: every thread bins its own bead when it
-// can form bonds (Appendix step 2); the beads with a bond of a type named by
-// a breakage rule are gathered in shared memory and nominated by the first
-// threads of the block, so the (rarer, longer) breakage work runs on dense
-// warps; the activity bitmaps of the block's 8 words are assembled in shared
-// memory.
+// Per bead: bounds check, binning of the beads that can form bonds (Appendix
+// step 2; occupancy counts only, the scatter assigns the slots), and the
+// bitmap of beads holding a bond of a type named by a breakage rule, whose
+// nomination runs beside the scatter (k_scatter).
 __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
   const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const CountTargets<2> tg{{d.stats + ST_BREAK_CANDIDATES, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
-  ReplicaCounts<2> cnt;
-  int hit_r = -1;  // replica of the breakage pairs this thread matched (settled pairs)
-  __shared__ int s_list[256];
-  __shared__ int s_n;
-  __shared__ unsigned s_ba[8], s_bn[8];
+  const int lane = threadIdx.x & 31;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
-    if (threadIdx.x < 8) s_ba[threadIdx.x] = s_bn[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
     const long long i = base + threadIdx.x;
+    bool brk = false;
     if (i < N) {
       const int r = rep_of(d, i);
       const int bt = d.type[i];
@@ -174,12 +164,11 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
           const float f = (float)nc / (float)L;
           long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f), cz = cell_of(p.z, nc, L, f);
           long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nc + cz;
-          atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the ranks
+          atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
           d.bead_cell[i] = (int)c;
         } else {
           d.bead_cell[i] = -1;
         }
-        bool brk = false;
         if (rt.breakish && has_bit(rt.reactive, bt)) {
 #pragma unroll
           for (int q = 0; q < SLOTS; ++q) {
@@ -187,26 +176,11 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
             brk |= v && has_bit(rt.breakish, s_type(v));
           }
         }
-        if (brk) s_list[atomicAdd(&s_n, 1)] = threadIdx.x;
       }
     }
-    __syncthreads();
-    if ((int)threadIdx.x < s_n) {
-      const long long k = base + s_list[threadIdx.x];
-      const unsigned fl = bead_breakage(d, rt, pos, k, rep_of(d, k), tg, cnt, hit_r);
-      const int o = (int)(k - base);
-      if (fl & 1u) atomicOr(&s_ba[o >> 5], 1u << (o & 31));
-      if (fl & 2u) atomicOr(&s_bn[o >> 5], 1u << (o & 31));
-    }
-    __syncthreads();
-    if (threadIdx.x < 8 && base + 32 * threadIdx.x < N) {
-      d.bm_ba[(base >> 5) + threadIdx.x] = s_ba[threadIdx.x];
-      d.bm_bn[(base >> 5) + threadIdx.x] = s_bn[threadIdx.x];
-    }
+    const unsigned m = __ballot_sync(FULL, brk);
+    if (lane == 0 && i < N) d.bm_bk[i >> 5] = m;
   }
-  cnt.flush_block(tg);
-  // settled pairs count as round-0 breakage matches of their replica
-  block_flag(d.round_hit + d.R, hit_r);
 }
 
 // ---------------------------------------------------------------------------
@@ -285,20 +259,44 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(Dev d) {
+// Blocks [0, scatter_blocks): counting-sort scatter of the binned beads into
+// cell order.  The other blocks: breakage nomination of the beads of the
+// breakage bitmap (independent work, run beside the scatter to share its
+// latency), with their edit / nomination bits OR-ed into the activity bitmaps.
+__global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
   pdl_enter();
   if (aborted(d.err)) return;
   const int4* __restrict__ pos = d.args->pos;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += stride) {
-    int c = d.bead_cell[i];
-    if (c < 0) continue;
-    int4 p = pos[i];
-    p.w = (int)((i << 4) | d.type[i]);
-    // after the scatter cell_start[c] holds the end of cell c, i.e. the start
-    // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
-    d.sorted[atomicAdd(&d.cell_start[c], 1)] = p;
+  if ((int)blockIdx.x < scatter_blocks) {
+    const long long stride = (long long)scatter_blocks * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += stride) {
+      int c = d.bead_cell[i];
+      if (c < 0) continue;
+      int4 p = pos[i];
+      p.w = (int)((i << 4) | d.type[i]);
+      // after the scatter cell_start[c] holds the end of cell c, i.e. the start
+      // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
+      d.sorted[atomicAdd(&d.cell_start[c], 1)] = p;
+    }
+    return;
   }
+  const RuleTab& rt = *rtp;
+  const CountTargets<2> tg{{d.stats + ST_BREAK_CANDIDATES, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
+  ReplicaCounts<2> cnt;
+  int hit_r = -1;  // replica of the settled breakage pairs this thread counted
+  const int nb = gridDim.x - scatter_blocks, b = blockIdx.x - scatter_blocks;
+  const long long nchunks = (d.W + CHUNK_WORDS - 1) / CHUNK_WORDS;
+  const long long cpb = (nchunks + nb - 1) / nb;
+  const long long c0 = (long long)b * cpb, c1 = min(nchunks, c0 + cpb);
+  for_bits_block(d.bm_bk, nullptr, d.W, d.N, c0, c1, [&](bool valid, long long i, bool, bool) {
+    if (!valid) return;
+    const unsigned fl = bead_breakage(d, rt, pos, i, rep_of(d, i), tg, cnt, hit_r);
+    if (fl & 1u) atomicOr(&d.bm_ba[i >> 5], 1u << (i & 31));
+    if (fl & 2u) atomicOr(&d.bm_bn[i >> 5], 1u << (i & 31));
+  });
+  cnt.flush_block(tg);
+  // settled pairs count as round-0 breakage matches of their replica
+  block_flag(d.round_hit + d.R, hit_r);
 }
 
 // ---------------------------------------------------------------------------
@@ -1363,6 +1361,8 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
   for (long long k = g; k <= d.n_keys; k += stride) d.cell_start[k] = 0;
   for (long long k = g; k < d.W; k += stride) {
     d.bm_ca[k] = 0;
+    d.bm_ba[k] = 0;
+    d.bm_bn[k] = 0;
     d.bm_dirty[k] = 0;
     d.bm_new[k] = 0;
   }
