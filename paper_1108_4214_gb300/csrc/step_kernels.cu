@@ -1186,13 +1186,17 @@ struct Rebuild {
   // true if another bond (p, q) of the path is new and ranks below (u, v)
   __device__ bool outranked(int p, int q, unsigned long long kuv) const { return bkey(p, q) < kuv && is_new(p, q); }
 
+  // part 0: angles centred at u; 1: angles centred at v; 2: dihedrals with
+  // (u, v) in the middle; 3 / 4: dihedrals starting at u / at v.  The parts
+  // are independent and run on different threads.
   template <class Emit>
-  __device__ void run(int u, int v, Emit& emit) const {
+  __device__ void run(int u, int v, int part, Emit& emit) const {
     const unsigned long long kuv = bkey(u, v);
     uint4 su = d.slots[u], sv = d.slots[v];
     int tu = d.type[u], tv = d.type[v];
     int st_uv = s_type_to(su, v), st_vu = s_type_to(sv, u);
     // angles centred at u: (x, u, v) and at v: (u, v, y)
+    if (part == 0)
     for (int q = 0; q < SLOTS; ++q) {
       unsigned w = s_get(su, q);
       int x = s_partner(w);
@@ -1200,6 +1204,7 @@ struct Rebuild {
       int t = angle_type(rt, d.type[x], tu, tv, s_type(w), st_uv);
       if (t) emit.angle(min(x, v), u, max(x, v), t);
     }
+    if (part == 1)
     for (int q = 0; q < SLOTS; ++q) {
       unsigned w = s_get(sv, q);
       int y = s_partner(w);
@@ -1208,6 +1213,7 @@ struct Rebuild {
       if (t) emit.angle(min(u, y), v, max(u, y), t);
     }
     // dihedrals with (u, v) in the middle: (x, u, v, y)
+    if (part == 2)
     for (int q = 0; q < SLOTS; ++q) {
       unsigned wx = s_get(su, q);
       int x = s_partner(wx);
@@ -1226,7 +1232,8 @@ struct Rebuild {
       }
     }
     // dihedrals starting at u: (u, v, y, z) and starting at v: (v, u, x, w)
-    for (int side = 0; side < 2; ++side) {
+    if (part >= 3) {
+      const int side = part - 3;
       int a = side ? v : u, b = side ? u : v;  // path a - b - y - z
       const uint4& sb = side ? su : sv;
       int ta = side ? tv : tu, tb = side ? tu : tv;
@@ -1307,14 +1314,15 @@ __global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restric
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   const Rebuild rb{d, rt, all_new};
-  const int n = d.cnt->n_nbl;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int i = base + threadIdx.x;
+  const long long n = 5ll * d.cnt->n_nbl;  // five independent parts per new bond
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
     const bool valid = i < n;
-    int4 e = valid ? d.nbl[i] : make_int4(0, 0, -1, 0);
+    const int part = (int)(i % 5);
+    int4 e = valid ? d.nbl[i / 5] : make_int4(0, 0, -1, 0);
     CountEmit ce;
-    if (valid) rb.run(e.x, e.y, ce);
+    if (valid) rb.run(e.x, e.y, part, ce);
     int oa, od;
     reserve(d, e.z, ce.na, ce.nd, &oa, &od);
     if (valid && (ce.na || ce.nd)) {
@@ -1322,7 +1330,7 @@ __global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restric
       WriteEmit we{d.ang + 6 * d.off[r] + (d.n_ang[r] - d.m_ang[r]) + oa,
                    d.dih + 18 * d.off[r] + (d.n_dih[r] - d.m_dih[r]) + od, d.ang + 6 * d.off[r + 1],
                    d.dih + 18 * d.off[r + 1], d.err};
-      rb.run(e.x, e.y, we);
+      rb.run(e.x, e.y, part, we);
     }
   }
   // the last block: per-replica counts and statistics (step 10), then the
