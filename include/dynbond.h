@@ -281,11 +281,12 @@ dynbond_status dynbond_get_topology(dynbond_ctx* ctx, dynbond_topology* topo);
 dynbond_status dynbond_topology_hash(dynbond_ctx* ctx, uint64_t* h_out);
 
 /*
- * Autotuning of launch geometry (not part of the paper): the cell edge (1, 1.5,
- * 2 or 3 x the largest creation distance) and the bead-pass grid size (4, 8 or
- * 16 blocks per SM) are chosen by timing the front of a call (cell binning and
- * candidate search, which write scratch only) on the positions d_pos; the
- * fastest is kept and the captured work is rebuilt.  No choice changes results.
+ * Autotuning of launch geometry (not part of the paper): the cell edge (1, 1.25,
+ * 1.5, 2 or 3 x the largest creation distance) and the bead-pass grid size (4, 8
+ * or 16 blocks per SM) are chosen by timing the front of a call (cell binning,
+ * breakage nomination and candidate search, which write scratch only; best of
+ * three runs) on the positions d_pos; the fastest is kept and the captured work
+ * is rebuilt.  No choice changes results.
  * Runs by itself on the first dynbond_step of a context created with
  * cell_scale 0.  out (nullable) receives the choice.
  */

@@ -583,6 +583,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   d.N = N;
   d.R = R;
   d.n_cells = c->n_cells;
+  d.reach = c->reach;
   d.spin_limit = params->spin_limit > 0 ? params->spin_limit : (1 << 24);
   long long* p_off;
   long long* p_box;
@@ -860,7 +861,7 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
   if (c->sticky) return c->sticky;
   dynbond_status st = DYNBOND_OK;
   if (c->max_cells) {
-    const double scales[] = {1.0, 1.5, 2.0, 3.0};
+    const double scales[] = {1.0, 1.25, 1.5, 2.0, 3.0};
     const int grids[] = {4, 8, 16};
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
@@ -873,13 +874,15 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
       if ((st = set_geometry(c, sc))) break;
       for (int gm : grids) {
         c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * gm);
-        float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and clocks
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {  // the first run warms caches and clocks; best of three
           cudaEventRecord(e0, c->stream);
           enqueue_front(c);
           cudaEventRecord(e1, c->stream);
           if (cudaEventSynchronize(e1) != cudaSuccess) break;
-          cudaEventElapsedTime(&ms, e0, e1);
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep) ms = std::min(ms, t);
         }
         if (ms < best) {
           best = ms;

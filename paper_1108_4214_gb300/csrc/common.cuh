@@ -102,6 +102,7 @@ struct Dev {
   const long long* cell_base;  // [R+1]
   long long n_cells;            // cells of one class (all replicas)
   long long n_keys;             // n_cls * n_cells binned keys
+  long long reach;              // smallest integer >= the largest creation distance (quantised units)
   const int* rep;              // [N]
   const unsigned char* type;   // [N]
   const unsigned* stream;      // [R]
@@ -274,6 +275,13 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_enter() {
   pdl_wait();
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// f[i] += (x, y, z, 0) as one 16-byte reduction at L2 (no value returned, so
+// the issuing warp neither waits for it nor keeps registers for a result)
+__device__ __forceinline__ void red_add_f4(float4* f, long long i, float x, float y, float z) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(f + i), "f"(x), "f"(y), "f"(z), "f"(0.f)
+               : "memory");
 }
 
 // Replica of bead i: the common single-system case needs no load, so later

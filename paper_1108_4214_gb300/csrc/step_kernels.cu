@@ -406,14 +406,40 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   const int cb = (int)d.cell_base[r], ncl = (int)d.n_cells;
   const float f = (float)nc / (float)L;
   const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f), cz = cell_of(me.z, nc, L, f);
-  // x and y: the distinct neighbouring columns; z: the three neighbouring
-  // cells of a column are contiguous in cell order, so each column is one or
-  // two contiguous runs of the sorted array
-  const int noff = nc >= 3 ? 3 : nc;
-  const int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
-  const int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
+  // x and y: the distinct neighbouring columns; z: the neighbouring cells of
+  // a column are contiguous in cell order, so each column is one or two
+  // contiguous runs of the sorted array.  Cells at least twice the reach
+  // wide: a bead's reach only touches the neighbour on the side of the half
+  // it sits in, so 2 x 2 columns of 2 cells (octant); else 3 x 3 columns of 3.
+  const bool oct = nc >= 3 && 2 * d.reach * nc <= (long long)L;
+  int nx = nc >= 3 ? 3 : nc;
+  int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
+  int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
   int z0, z1, w0 = 0, w1 = -1;  // main run [z0, z1], wrapped run [w0, w1]
-  if (nc >= 3) {
+  // is coordinate x in the lower half of its cell c (exactly: 2 (x nc - c L) < L)?
+  auto lower = [&](int x, int c) { return 2 * ((long long)x * nc - (long long)c * L) < (long long)L; };
+  if (oct) {
+    nx = 2;
+    if (lower(me.x, cx)) xs[1] = xs[2];
+    if (lower(me.y, cy)) ys[1] = ys[2];
+    if (lower(me.z, cz)) {  // cells cz - 1 and cz
+      if (cz == 0) {
+        z0 = z1 = 0;
+        w0 = w1 = nc - 1;
+      } else {
+        z0 = cz - 1;
+        z1 = cz;
+      }
+    } else {  // cells cz and cz + 1
+      if (cz == nc - 1) {
+        z0 = z1 = nc - 1;
+        w0 = w1 = 0;
+      } else {
+        z0 = cz;
+        z1 = cz + 1;
+      }
+    }
+  } else if (nc >= 3) {
     z0 = cz - 1;
     z1 = cz + 1;
     if (z0 < 0) {  // cz = 0: cells nc-1, 0, 1
@@ -439,7 +465,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
       const int a = ab / 3, b = ab % 3;
       int len = 0;
       q0[ab] = 0;
-      if (a < noff && b < noff) {
+      if (a < nx && b < nx) {
         const int row = cbk + (xs[a] * nc + ys[b]) * nc;
         q0[ab] = d.cell_start[row + lo - 1];
         len = d.cell_start[row + hi] - q0[ab];
@@ -487,8 +513,8 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
     uint4 si = d.slots[i];
     for (unsigned cm = cmask; cm; cm &= cm - 1) {
       const int cbk = (__ffs(cm) - 1) * ncl + cb;
-      for (int a = 0; a < noff; ++a)
-        for (int b = 0; b < noff; ++b) {
+      for (int a = 0; a < nx; ++a)
+        for (int b = 0; b < nx; ++b) {
           const int row = cbk + (xs[a] * nc + ys[b]) * nc;
           for (int run = 0; run < 2; ++run) {
             int lo = run ? w0 : z0, hi = run ? w1 : z1;

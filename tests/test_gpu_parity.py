@@ -116,9 +116,13 @@ def test_initial_typing_of_the_papers_dna_ladder():
     assert d.tolist() == sorted(g["expected_dihedrals"])
 
 
-def test_plain_2048_beads_ten_calls():
+@pytest.mark.parametrize("cell_scale", [0, 1, 2, 3])
+def test_plain_2048_beads_ten_calls(cell_scale):
+    """Ten calls on 2048 beads, autotuned (0) and with fixed cell edges of 1,
+    2 and 3 x the creation reach: the last two search only the octant of
+    neighbouring cells on the side of the cell half each bead sits in."""
     s = W.config1()
-    _, worst = run_parity(s, 10)
+    _, worst = run_parity(s, 10, params=dict(cell_scale=cell_scale))
     print("max force / ev error", max(w[0] for w in worst), max(w[1] for w in worst))
 
 
@@ -166,10 +170,11 @@ def test_duplex_melts_and_reforms():
     run_parity(s, 2, snaps=[snap, snap])
 
 
-def test_plain_1m_beads_parity():
+@pytest.mark.parametrize("cell_scale", [0, 2])
+def test_plain_1m_beads_parity(cell_scale):
     s = W.config2()
     snaps = s.snapshots(0, 3)
-    _, worst = run_parity(s, 3, snaps=snaps)
+    _, worst = run_parity(s, 3, snaps=snaps, params=dict(cell_scale=cell_scale))
     print("1M: max force / ev error", worst)
 
 
@@ -312,7 +317,7 @@ def test_autotuned_and_fixed_geometries_give_identical_results():
         for x, y in zip(tops[0], t):
             assert np.array_equal(x, y)
     info = ctxs[0].autotune(torch.from_numpy(s.snapshot(4)).cuda())
-    assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.5, 2.0, 3.0)
+    assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.25, 1.5, 2.0, 3.0)
 
 
 def test_bounded_wait_gives_up_with_a_status_and_leaves_the_device_usable():
