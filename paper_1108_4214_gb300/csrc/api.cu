@@ -51,7 +51,8 @@ struct dynbond_ctx {
   double* d2h_ev = nullptr;
   // cell geometry (re-chosen by the autotuner; never changes results)
   std::vector<long long> h_box;
-  long long reach = 0;          // smallest integer cell width covering the largest creation distance
+  long long reach = 0;
+  bool octant = false;          // candidate search by octant (see set_geometry)          // smallest integer cell width covering the largest creation distance
   long long max_cells = 0;      // cells allocated (geometry at scale 1)
   int* d_nc = nullptr;
   long long* d_cb = nullptr;
@@ -304,7 +305,7 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
   E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
   mark(c, c->ev_step, k++);
-  E(launch(c, k_candidates, c->grid_cand, 256, d, c->d_rt));
+  E(launch(c, c->octant ? k_candidates_oct : k_candidates, c->grid_cand, 256, d, c->d_rt));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   mark(c, c->ev_step, k++);
   E(launch_match(c));
@@ -401,6 +402,7 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale) {
   const int R = c->R;
   std::vector<int> nc(R);
   std::vector<long long> cb(R + 1, 0);
+  bool octant = true;
   for (int r = 0; r < R; ++r) {
     long long L = c->h_box[r];
     long long ncap = c->reach > 0 ? L / c->reach : 1;
@@ -408,11 +410,14 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale) {
     n = std::max<long long>(1, std::min<long long>({n, ncap, 1024}));
     nc[r] = (int)n;
     cb[r + 1] = cb[r] + n * n * n;
+    // cells at least twice the reach on every axis: the octant search suffices
+    octant = octant && n >= 3 && 2 * c->reach * n <= L;
   }
   if (c->max_cells && cb[R] > c->max_cells) return fail(c, DYNBOND_EINVAL, "cell geometry larger than allocated");
   if (cb[R] * c->rt.n_cls >= 0x7FFFFFFFll)
     return fail(c, DYNBOND_EINVAL, "cell grid too large: boxes over 2^31 cell keys (cell classes x cells)");
   c->n_cells = cb[R];
+  c->octant = octant;
   c->d.n_cells = c->n_cells;
   c->d.n_keys = c->n_cells * c->rt.n_cls;
   c->grid_scan = bounded_grid(c->d.n_keys, 256 * 32, c->nsm * 4);
@@ -449,7 +454,7 @@ cudaError_t enqueue_front(dynbond_ctx* c) {
   E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
   E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
-  E(launch(c, k_candidates, c->grid_cand, 256, d, c->d_rt));
+  E(launch(c, c->octant ? k_candidates_oct : k_candidates, c->grid_cand, 256, d, c->d_rt));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   return cudaGetLastError();
 }
@@ -583,7 +588,6 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   d.N = N;
   d.R = R;
   d.n_cells = c->n_cells;
-  d.reach = c->reach;
   d.spin_limit = params->spin_limit > 0 ? params->spin_limit : (1 << 24);
   long long* p_off;
   long long* p_box;

@@ -102,7 +102,6 @@ struct Dev {
   const long long* cell_base;  // [R+1]
   long long n_cells;            // cells of one class (all replicas)
   long long n_keys;             // n_cls * n_cells binned keys
-  long long reach;              // smallest integer >= the largest creation distance (quantised units)
   const int* rep;              // [N]
   const unsigned char* type;   // [N]
   const unsigned* stream;      // [R]

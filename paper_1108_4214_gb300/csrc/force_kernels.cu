@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_bond_forces(Dev d, FF ff) {
 }
 
 __device__ __forceinline__ void add_force(float4* f, int i, float3 v) {
-  atomicAdd(f + i, make_float4(v.x, v.y, v.z, 0.f));
+  red_add_f4(f, i, v.x, v.y, v.z);
 }
 
 constexpr int ANG_PER_THREAD = FORCE_TILE / 256;

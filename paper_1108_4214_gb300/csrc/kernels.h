@@ -22,6 +22,7 @@ __global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_scan_cells(Dev d);
 __global__ void k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks);
 __global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_match(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_edit(Dev d, const RuleTab* __restrict__ rtp);

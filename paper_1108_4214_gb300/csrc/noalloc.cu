@@ -123,7 +123,7 @@ __global__ void na_bonds(const int4* __restrict__ pos, const uint4* __restrict__
   acc.flush_warp(ev);
 }
 
-__device__ __forceinline__ void na_add(float4* f, int i, float3 v) { atomicAdd(f + i, make_float4(v.x, v.y, v.z, 0.f)); }
+__device__ __forceinline__ void na_add(float4* f, int i, float3 v) { red_add_f4(f, i, v.x, v.y, v.z); }
 
 // angles E = K (1 + cos theta); dihedrals E = K (1 + d cos phi) with the
 // Blondel-Karplus derivatives of phi

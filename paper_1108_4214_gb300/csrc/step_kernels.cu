@@ -23,6 +23,10 @@ namespace dynbond {
 
 constexpr int SCAN_PER_THREAD = 32;  // cells per thread in the histogram scan
 constexpr int SCAN_BATCH = 2;  // candidate entries loaded together
+template <int N>
+struct IntC {
+  static constexpr int value = N;
+};
 constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
 
 __device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
@@ -396,6 +400,9 @@ __device__ __forceinline__ void cand_slow(const uint4* __restrict__ slots, const
 // per axis) within the largest creation distance are collected first; the
 // rule and graph-distance tests then run on them after the scan, so the
 // lanes of a warp take the rare path together instead of one after another.
+// GEO 1: every replica's cells are at least twice the reach wide (octant
+// search); GEO 0: full 3 x 3 x 3 search, correct for any cell geometry.
+template <int GEO>
 __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned cmask,
                                                 long long r2max, const int4& me, int i, LocalList* ll, int mode,
                                                 int4** out, int* pj, long long* pd, int* np_out) {
@@ -411,7 +418,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   // contiguous runs of the sorted array.  Cells at least twice the reach
   // wide: a bead's reach only touches the neighbour on the side of the half
   // it sits in, so 2 x 2 columns of 2 cells (octant); else 3 x 3 columns of 3.
-  const bool oct = nc >= 3 && 2 * d.reach * nc <= (long long)L;
+  const bool oct = GEO == 1;
   int nx = nc >= 3 ? 3 : nc;
   int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
   int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
@@ -455,34 +462,37 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   }
   int np = 0;
   bool more = false;
-  // entries of the 9 column runs [q0, q0 + len), fetched SCAN_BATCH at a
-  // time with independent loads (runs are short, most are empty)
-  auto scan_runs = [&](int lo, int hi, int cbk) {
-    int q0[9], ex[10];  // run starts; exclusive prefix of the run lengths
+  // entries of the NA x NA column runs (NA = 2 octant, else 3), fetched
+  // SCAN_BATCH at a time with independent loads (runs are short, many are
+  // empty).  Entry k of the concatenated runs is sorted[k + dl[u]] for the
+  // last run u starting at or before k (an empty run is never the last).
+  auto scan_runs = [&](auto na_c, int lo, int hi, int cbk) {
+    constexpr int NA = decltype(na_c)::value, NR = NA * NA;
+    int dl[NR], ex[NR + 1];  // run offsets; exclusive prefix of the run lengths
     ex[0] = 0;
 #pragma unroll
-    for (int ab = 0; ab < 9; ++ab) {
-      const int a = ab / 3, b = ab % 3;
-      int len = 0;
-      q0[ab] = 0;
+    for (int ab = 0; ab < NR; ++ab) {
+      const int a = ab / NA, b = ab % NA;
+      int len = 0, q0 = 0;
       if (a < nx && b < nx) {
         const int row = cbk + (xs[a] * nc + ys[b]) * nc;
-        q0[ab] = d.cell_start[row + lo - 1];
-        len = d.cell_start[row + hi] - q0[ab];
+        q0 = d.cell_start[row + lo - 1];
+        len = d.cell_start[row + hi] - q0;
       }
+      dl[ab] = q0 - ex[ab];
       ex[ab + 1] = ex[ab] + len;
     }
-    const int total = ex[9];
+    const int total = ex[NR];
     for (int k0 = 0; k0 < total; k0 += SCAN_BATCH) {
       int4 o[SCAN_BATCH];
 #pragma unroll
       for (int v = 0; v < SCAN_BATCH; ++v) {
         const int k = k0 + v;
-        int q = -1;
+        int dk = dl[0];
 #pragma unroll
-        for (int u = 0; u < 9; ++u)
-          if (k >= ex[u] && k < ex[u + 1]) q = q0[u] + (k - ex[u]);
-        if (q >= 0) o[v] = d.sorted[q];
+        for (int u = 1; u < NR; ++u)
+          if (k >= ex[u]) dk = dl[u];
+        if (k < total) o[v] = d.sorted[k + dk];
       }
 #pragma unroll
       for (int v = 0; v < SCAN_BATCH; ++v) {
@@ -501,8 +511,8 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
   };
   for (unsigned cm = cmask; cm; cm &= cm - 1) {
     const int cbk = (__ffs(cm) - 1) * ncl + cb;  // this class's cells of the replica
-    scan_runs(z0, z1, cbk);
-    if (w1 >= w0) scan_runs(w0, w1, cbk);  // next to a periodic boundary in z
+    scan_runs(IntC<GEO == 1 ? 2 : 3>{}, z0, z1, cbk);
+    if (w1 >= w0) scan_runs(IntC<GEO == 1 ? 2 : 3>{}, w0, w1, cbk);  // next to a periodic boundary in z
   }
   if (mode == 0) {  // survivors go back to the caller; the warp tests them together
     ll->overflow = more;  // finished exactly by k_cand_overflow
@@ -604,7 +614,8 @@ __device__ __forceinline__ void load_type_masks(const RuleTab& rt, unsigned* s_m
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+template <int GEO>
+__device__ __forceinline__ void candidates_body(const Dev& d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
   if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
@@ -631,7 +642,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
       ti = me.w & 15;
       r = rep_of(d, i);
       ll.me = i;
-      scan_candidates(d, rtp, s_mask[ti], r2max, me, i, &ll, 0, nullptr, pj, pd, &np);
+      scan_candidates<GEO>(d, rtp, s_mask[ti], r2max, me, i, &ll, 0, nullptr, pj, pd, &np);
       if (np) si = d.slots[i];
     }
     warp_survivors(d, rtp, i, ti, si, pj, pd, np, &ll, s_q[threadIdx.x >> 5]);
@@ -663,6 +674,13 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
   pairs.end_warp(tg);
 }
 
+__global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+  candidates_body<0>(d, rtp);
+}
+__global__ void __launch_bounds__(256, 3) k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp) {
+  candidates_body<1>(d, rtp);
+}
+
 // Exact path for beads with more than MAXC candidates: count, allocate,
 // write, then sort the bead's list by (d2, partner) in place.
 __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp) {
@@ -680,7 +698,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     cv.me = i;
     int pj[MAXC], np = 0;
     long long pd[MAXC];
-    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 1, nullptr, pj, pd, &np);
+    scan_candidates<0>(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 1, nullptr, pj, pd, &np);
     const int a = atomicAdd(&d.cnt->cand_used, cv.cnt);
     if ((long long)a + cv.cnt > d.cand_pool) {
       atomicOr(d.err, ERR_CAND_CAP);
@@ -689,7 +707,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     const long long at = d.cand_fixed + a;
     int pairs = cv.pairs;
     int4* w = d.cand + at;
-    scan_candidates(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 2, &w, pj, pd, &np);
+    scan_candidates<0>(d, rtp, s_mask[me.w & 15], r2max, me, i, &cv, 2, &w, pj, pd, &np);
     int4* lst = d.cand + at;
     for (int a = 1; a < cv.cnt; ++a) {
       int4 x = lst[a];
