@@ -263,24 +263,44 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
   }
 }
 
-// Blocks [0, scatter_blocks): counting-sort scatter of the binned beads into
-// cell order.  The other blocks: breakage nomination of the beads of the
+// The last scatter_blocks blocks: counting-sort scatter of the binned beads
+// into cell order.  The others: breakage nomination of the beads of the
 // breakage bitmap (independent work, run beside the scatter to share its
 // latency), with their edit / nomination bits OR-ed into the activity bitmaps.
 __global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
   pdl_enter();
   if (aborted(d.err)) return;
   const int4* __restrict__ pos = d.args->pos;
-  if ((int)blockIdx.x < scatter_blocks) {
+  // the breakage blocks come first, so their longer dependent chains start
+  // with the first wave instead of trailing the scatter
+  const int nb = gridDim.x - scatter_blocks;
+  if ((int)blockIdx.x >= nb) {
     const long long stride = (long long)scatter_blocks * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += stride) {
-      int c = d.bead_cell[i];
-      if (c < 0) continue;
-      int4 p = pos[i];
-      p.w = (int)((i << 4) | d.type[i]);
+    constexpr int U = 4;  // beads per thread and pass, every load issued first
+    for (long long i0 = (long long)(blockIdx.x - nb) * blockDim.x + threadIdx.x; i0 < d.N; i0 += U * stride) {
+      int c[U], at[U];
+      int4 p[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long i = i0 + u * stride;
+        c[u] = i < d.N ? d.bead_cell[i] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long i = i0 + u * stride;
+        if (c[u] >= 0) {
+          p[u] = pos[i];
+          p[u].w = (int)((i << 4) | d.type[i]);
+        }
+      }
       // after the scatter cell_start[c] holds the end of cell c, i.e. the start
       // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
-      d.sorted[atomicAdd(&d.cell_start[c], 1)] = p;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c[u] >= 0) at[u] = atomicAdd(&d.cell_start[c[u]], 1);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (c[u] >= 0) d.sorted[at[u]] = p[u];
     }
     return;
   }
@@ -288,7 +308,7 @@ __global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restric
   const CountTargets<2> tg{{d.stats + ST_BREAK_CANDIDATES, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
   ReplicaCounts<2> cnt;
   int hit_r = -1;  // replica of the settled breakage pairs this thread counted
-  const int nb = gridDim.x - scatter_blocks, b = blockIdx.x - scatter_blocks;
+  const int b = blockIdx.x;
   const long long nchunks = (d.W + CHUNK_WORDS - 1) / CHUNK_WORDS;
   const long long cpb = (nchunks + nb - 1) / nb;
   const long long c0 = (long long)b * cpb, c1 = min(nchunks, c0 + cpb);
