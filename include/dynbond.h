@@ -241,7 +241,8 @@ dynbond_status dynbond_create(const dynbond_params* params, const dynbond_rule* 
 
 /*
  * One call of the fix (Appendix steps 1-10) at call index `step` on the
- * positions d_pos (device int4[N], read only).  Trials are keyed by
+ * positions d_pos (device int4[N], 16-byte aligned, read only; EINVAL if
+ * misaligned).  Trials are keyed by
  * (seed, step, pair), so repeating a step index repeats its random numbers.
  * h_stats (nullable, host [n_replicas]): when given, the call waits for the
  * device and fills the statistics, and device errors are returned.
@@ -250,7 +251,7 @@ dynbond_status dynbond_step(dynbond_ctx* ctx, const int32_t* d_pos, uint64_t ste
 
 /*
  * Bonded forces of the current topology at d_pos: d_force (device float4[N],
- * overwritten; w = 0) in FP32; d_ev (device double[R*7], overwritten) per
+ * overwritten; w = 0) in FP32 (d_pos and d_force 16-byte aligned, else EINVAL); d_ev (device double[R*7], overwritten) per
  * replica (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz) with W_ab = sum over interactions
  * of (r_role - r_ref)_a F_role,b, reduced in FP64.
  */

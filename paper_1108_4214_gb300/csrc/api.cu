@@ -33,7 +33,8 @@ struct dynbond_ctx {
   bool use_graph = true;
   bool pdl = true;  // programmatic dependent launch between the kernels of a call
   int block = 256;
-  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_seg = 0, grid_force = 0, grid_edit = 0;
+  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_seg = 0, grid_edit = 0;
+  int grid_adf = 0, grid_bf = 0;
   long long st_scan_n = 0;
   void* small = nullptr;
   size_t small_bytes = 0;
@@ -235,9 +236,11 @@ dynbond_status build_rules(dynbond_ctx* c, const dynbond_rule* rules, int n) {
   return DYNBOND_OK;
 }
 
-int occupancy_grid(dynbond_ctx* c, const void* fn, int block, int per_sm_cap) {
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int occupancy_grid(dynbond_ctx* c, const void* fn, int block, int per_sm_cap, size_t smem = 0) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess || nb < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess || nb < 1) {
     cudaGetLastError();
     nb = 1;
   }
@@ -268,10 +271,11 @@ void mark(dynbond_ctx* c, std::vector<cudaEvent_t>& ev, size_t k) {
   } while (0)
 
 template <typename... KArgs, typename... Args>
-cudaError_t launch(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, Args... args) {
+cudaError_t launch_smem(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, size_t smem, Args... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -279,6 +283,10 @@ cudaError_t launch(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, 
   cfg.attrs = attr;
   cfg.numAttrs = c->pdl && !c->profile ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+template <typename... KArgs, typename... Args>
+cudaError_t launch(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, Args... args) {
+  return launch_smem(c, kern, grid, block, 0, args...);
 }
 
 cudaError_t launch_match(dynbond_ctx* c) {
@@ -324,9 +332,9 @@ cudaError_t enqueue_forces(dynbond_ctx* c) {
   const Dev& d = c->d;
   size_t k = 0;
   mark(c, c->ev_forces, k++);
-  E(launch(c, k_bond_forces, c->grid_force, 256, d, c->ff));
+  E(launch_smem(c, k_bond_forces, c->grid_bf, BF_THREADS, (size_t)BF_SMEM_BYTES, d, c->ff));
   mark(c, c->ev_forces, k++);
-  E(launch(c, k_angle_dihedral_forces, c->grid_force, 256, d, c->ff));
+  E(launch_smem(c, k_angle_dihedral_forces, c->grid_adf, AD_THREADS, (size_t)AD_SMEM_BYTES, d, c->ff));
   mark(c, c->ev_forces, k++);
   E(launch(c, k_ev_out, bounded_grid(7ll * c->R, 256, c->nsm), 256, d));
   return cudaGetLastError();
@@ -753,7 +761,13 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
 
   // ---- launch geometry
   c->grid_bead = bounded_grid(N, 256, c->nsm * 8);
-  c->grid_force = bounded_grid(N, 256, c->nsm * 8);
+  // angle / dihedral forces: one persistent wave (the blocks pipeline their tiles)
+  CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_angle_dihedral_forces,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, AD_SMEM_BYTES));
+  c->grid_adf = occupancy_grid(c, (const void*)k_angle_dihedral_forces, AD_THREADS, 8, AD_SMEM_BYTES);
+  CUDA_TRY(c, cudaFuncSetAttribute((const void*)k_bond_forces, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   BF_SMEM_BYTES));
+  c->grid_bf = occupancy_grid(c, (const void*)k_bond_forces, BF_THREADS, 8, BF_SMEM_BYTES);
   c->grid_edit = bounded_grid((c->W + 7) / 8, 8, c->nsm * 8);  // a warp per 8 bitmap words
   c->tuning.bead_blocks_per_sm = 8;
   c->tuning.candidate_blocks_per_sm = 8;
@@ -809,6 +823,7 @@ dynbond_status dynbond_create(const dynbond_params* params, const dynbond_rule* 
 
 dynbond_status dynbond_step(dynbond_ctx* c, const int32_t* d_pos, uint64_t step, dynbond_stats* h_stats) {
   if (!c || !d_pos) return DYNBOND_EINVAL;
+  if (!aligned16(d_pos)) return fail(c, DYNBOND_EINVAL, "d_pos must be 16-byte aligned (int4 per bead)");
   if (c->sticky) return c->sticky;
   if (!c->tuned) {
     dynbond_status st = dynbond_autotune(c, d_pos, nullptr);
@@ -832,6 +847,8 @@ dynbond_status dynbond_step(dynbond_ctx* c, const int32_t* d_pos, uint64_t step,
 
 dynbond_status dynbond_forces(dynbond_ctx* c, const int32_t* d_pos, float* d_force, double* d_ev) {
   if (!c || !d_pos || !d_force || !d_ev) return DYNBOND_EINVAL;
+  if (!aligned16(d_pos) || !aligned16(d_force))
+    return fail(c, DYNBOND_EINVAL, "d_pos and d_force must be 16-byte aligned (4-vectors per bead)");
   if (c->sticky) return c->sticky;
   k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, (float4*)d_force, d_ev, 0, 0, 1);
   cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_forces, c->stream) : enqueue_forces(c);
@@ -862,6 +879,7 @@ dynbond_status dynbond_run_host(dynbond_ctx* c, const int32_t* h_pos, uint64_t s
 
 dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tuning* out) {
   if (!c || !d_pos) return DYNBOND_EINVAL;
+  if (!aligned16(d_pos)) return fail(c, DYNBOND_EINVAL, "d_pos must be 16-byte aligned (int4 per bead)");
   if (c->sticky) return c->sticky;
   dynbond_status st = DYNBOND_OK;
   if (c->max_cells) {

@@ -128,58 +128,120 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
   __syncthreads();
 }
 
-// bonds: BEAD_TILE beads per work item, BEAD_PER_THREAD per thread with
-// every load issued before the arithmetic
-constexpr int BEAD_PER_THREAD = BEAD_TILE / 256;
+// 16-byte asynchronous copy global -> shared (zero-filled when !pred; the
+// source address is then not read)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-__global__ void __launch_bounds__(256) k_bond_forces(Dev d, FF ff) {
+// Bonds: each bead sums, over its occupied slots, the harmonic force of the
+// type it stores for that bond (directional bonds, Sec. 2) and books half the
+// energy; no atomics.  Software-pipelined per thread like the angle /
+// dihedral launch: the slots of the tile after next and the positions (own
+// and partners') of the next tile are in flight while the current tile is
+// computed.
+struct BondStage {
+  uint4 slot[3][BF_PER_THREAD][BF_THREADS];
+  int4 pos[2][BF_PER_THREAD][1 + SLOTS][BF_THREADS];
+};
+static_assert(sizeof(BondStage) == BF_SMEM_BYTES, "bond shared memory layout");
+
+__global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ff) {
   pdl_enter();
   if (aborted(d.err)) return;
+  extern __shared__ __align__(16) unsigned char bf_smem[];
+  BondStage& sm = *reinterpret_cast<BondStage*>(bf_smem);
   const int4* __restrict__ pos = d.args->pos;
   float4* __restrict__ force = d.args->force;
   const int R = d.R, nitems = d.tb_beads[R];
+  const unsigned N = (unsigned)d.N;
+  const int tid = threadIdx.x;
+  // first bead and end of work item k of this block (beg = end when none)
+  auto tile = [&](int k, long long& beg, long long& end, int& r) {
+    const int it = blockIdx.x + k * gridDim.x;
+    beg = end = 0;
+    r = 0;
+    if (it >= nitems) return;
+    r = find_seg(d.tb_beads, R, it);
+    beg = d.off[r] + (long long)(it - d.tb_beads[r]) * BEAD_TILE;
+    end = min(beg + BEAD_TILE, d.off[r + 1]);
+  };
+  auto issue_slots = [&](int k) {
+    long long beg, end;
+    int r;
+    tile(k, beg, end, r);
+#pragma unroll
+    for (int u = 0; u < BF_PER_THREAD; ++u) {
+      const long long i = beg + tid + u * BF_THREADS;
+      cp_async16(&sm.slot[k % 3][u][tid], i < end ? (const void*)(d.slots + i) : (const void*)d.slots, i < end);
+    }
+    cp_async_commit();
+  };
+  auto issue_pos = [&](int k) {
+    long long beg, end;
+    int r;
+    tile(k, beg, end, r);
+#pragma unroll
+    for (int u = 0; u < BF_PER_THREAD; ++u) {
+      const long long i = beg + tid + u * BF_THREADS;
+      const bool ok = i < end;
+      const uint4 sl = sm.slot[k % 3][u][tid];
+      cp_async16(&sm.pos[k & 1][u][0][tid], pos + (ok ? i : 0), ok);
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        const unsigned v = s_get(sl, q);
+        const bool has = ok && v && (unsigned)s_partner(v) < N;
+        cp_async16(&sm.pos[k & 1][u][1 + q][tid], pos + (has ? s_partner(v) : 0), has);
+      }
+    }
+    cp_async_commit();
+  };
+  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   EV acc;
   int racc = -1;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int r = find_seg(d.tb_beads, R, it);
+  // commit order: S0 S1 P0 | S2 P1 | S3 P2 ...; wait_group 2 leaves the two
+  // newest groups in flight
+  issue_slots(0);
+  issue_slots(1);
+  cp_async_wait<1>();
+  issue_pos(0);
+  for (int k = 0; k < ntiles; ++k) {
+    issue_slots(k + 2);  // past the last tile: an empty group
+    cp_async_wait<2>();  // slots of tile k + 1 have landed
+    issue_pos(k + 1);
+    cp_async_wait<2>();  // positions of tile k have landed
+    long long beg, end;
+    int r;
+    tile(k, beg, end, r);
     if (r != racc) {
       if (racc >= 0) flush_ev(d, acc, racc);
       racc = r;
     }
-    long long beg = d.off[r] + (long long)(it - d.tb_beads[r]) * BEAD_TILE;
-    long long end = min(beg + BEAD_TILE, d.off[r + 1]);
-    int L = (int)d.box[r];
-    int4 p[BEAD_PER_THREAD];
-    uint4 s[BEAD_PER_THREAD];
-#pragma unroll
-    for (int u = 0; u < BEAD_PER_THREAD; ++u) {
-      long long i = beg + threadIdx.x + u * 256;
-      s[u] = make_uint4(0, 0, 0, 0);
-      if (i < end) {
-        p[u] = pos[i];
-        s[u] = d.slots[i];
-      }
-    }
-    int4 q[BEAD_PER_THREAD][SLOTS];
-#pragma unroll
-    for (int u = 0; u < BEAD_PER_THREAD; ++u)
-#pragma unroll
-      for (int k = 0; k < SLOTS; ++k) {
-        unsigned v = s_get(s[u], k);
-        if (v) q[u][k] = pos[s_partner(v)];
-      }
+    const int L = (int)d.box[r];
     float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int u = 0; u < BEAD_PER_THREAD; ++u) {
-      long long i = beg + threadIdx.x + u * 256;
+    for (int u = 0; u < BF_PER_THREAD; ++u) {
+      const long long i = beg + tid + u * BF_THREADS;
       if (i >= end) continue;
+      const uint4 sl = sm.slot[k % 3][u][tid];
+      const int4 p = sm.pos[k & 1][u][0][tid];
       float3 f = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < SLOTS; ++k) {
-        unsigned v = s_get(s[u], k);
+      for (int q = 0; q < SLOTS; ++q) {
+        const unsigned v = s_get(sl, q);
         if (!v) continue;
-        int t = s_type(v);
-        float3 rij = relq(p[u], q[u][k], L);
+        if ((unsigned)s_partner(v) >= N) {
+          atomicOr(d.err, ERR_INTERNAL);
+          continue;
+        }
+        const int t = s_type(v);
+        float3 rij = relq(p, sm.pos[k & 1][u][1 + q][tid], L);
         float ir = rsqrtf(dot3(rij, rij));
         float dr = dot3(rij, rij) * ir - ff.bond_r0[t];
         float fscal = -2.0f * ff.bond_k[t] * dr * ir;
@@ -197,8 +259,9 @@ __global__ void __launch_bounds__(256) k_bond_forces(Dev d, FF ff) {
     }
     acc.add(0, e);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc.add(k + 1, 0.5f * w[k]);
+    for (int c = 0; c < 6; ++c) acc.add(c + 1, 0.5f * w[c]);
   }
+  cp_async_wait<0>();
   if (racc >= 0) flush_ev(d, acc, racc);
 }
 
@@ -206,151 +269,190 @@ __device__ __forceinline__ void add_force(float4* f, int i, float3 v) {
   red_add_f4(f, i, v.x, v.y, v.z);
 }
 
-constexpr int ANG_PER_THREAD = FORCE_TILE / 256;
-constexpr int DIH_PER_THREAD = FORCE_TILE / 256;
+// One angle: E = K (1 + cos theta) with r_A - r_B and r_C - r_B.
+__device__ __forceinline__ void angle_term(float4* force, const int4& a, const int4& pa, const int4& pb,
+                                           const int4& pc, int L, const FF& ff, float& e, float* w) {
+  float3 ra = relq(pa, pb, L), rc = relq(pc, pb, L);
+  float K = ff.angle_k[a.w];
+  float ia = rsqrtf(dot3(ra, ra)), ic = rsqrtf(dot3(rc, rc));
+  float inv = ia * ic;
+  float cs = dot3(ra, rc) * inv;
+  // F_A = -K d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
+  float3 Fa = scale(-K, axpy(-cs * ia * ia, ra, scale(inv, rc)));
+  float3 Fc = scale(-K, axpy(-cs * ic * ic, rc, scale(inv, ra)));
+  float3 Fb = make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z);
+  add_force(force, a.x, Fa);
+  add_force(force, a.y, Fb);
+  add_force(force, a.z, Fc);
+  e += K * (1.0f + cs);
+  w[0] += ra.x * Fa.x + rc.x * Fc.x;
+  w[1] += ra.y * Fa.y + rc.y * Fc.y;
+  w[2] += ra.z * Fa.z + rc.z * Fc.z;
+  w[3] += ra.x * Fa.y + rc.x * Fc.y;
+  w[4] += ra.x * Fa.z + rc.x * Fc.z;
+  w[5] += ra.y * Fa.z + rc.y * Fc.z;
+}
 
-// Angles and dihedrals in one launch: items [0, tb_fang[R]) are angle tiles,
-// the rest dihedral tiles; both add their forces with float4 atomics.
-__global__ void __launch_bounds__(256) k_angle_dihedral_forces(Dev d, FF ff) {
+// One dihedral: E = K (1 + d cos phi).  Blondel-Karplus: F = r_A - r_B,
+// G = r_B - r_C, H = r_D - r_C, A = F x G, B = H x G; cos phi = A.B /
+// (|A||B|), phi = 180 deg trans.  The cross, dot and triple products are
+// formed exactly from the integer displacements and rounded once, so
+// near-collinear quartets keep FP32 accuracy; the rest is FP32.
+__device__ __forceinline__ void dihedral_term(float4* force, const int4& rec, const int4& P0, const int4& P1,
+                                              const int4& P2, const int4& P3, int L, const FF& ff, float& e,
+                                              float* w) {
+  int ia = rec.x, ib = rec.y, ic = rec.z, id = rec.w & 0x0FFFFFFF;
+  int t = (int)((unsigned)rec.w >> 28);
+  int3 Fi = reli(P0, P1, L), Gi = reli(P1, P2, L), Hi = reli(P3, P2, L);
+  L3 Ai = crossi(Fi, Gi), Bi = crossi(Hi, Gi);
+  const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
+  float3 F = tof(Fi, s20), G = tof(Gi, s20), H = tof(Hi, s20);
+  float3 A = tof(Ai, s40), B = tof(Bi, s40);
+  float A2 = dot3(A, A), B2 = dot3(B, B);
+  float gg = (float)doti(Gi, Gi) * s40;
+  float irg = rsqrtf(gg), rg = gg * irg;
+  float rab = rsqrtf(A2 * B2);
+  float cs = dot3(A, B) * rab;
+  // (B x A).G = -|G|^2 F.B, so sin phi = -|G| (F.B) / (|A||B|)
+  float sn = -rg * triplei(Fi, Bi, -60) * rab;
+  float K = ff.dih_k[t], dd = ff.dih_d[t];
+  // E = K (1 + d cos phi): -dE/dphi = K d sin phi
+  float mdE = K * dd * sn;
+  float fg = (float)doti(Fi, Gi) * s40, hg = (float)doti(Hi, Gi) * s40;
+  float ia2 = __frcp_rn(A2), ib2 = __frcp_rn(B2);
+  // dphi/dr_A = -|G|/A^2 A ; dphi/dr_D = |G|/B^2 B
+  // dphi/dr_B = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B
+  // dphi/dr_C = -F.G/(A^2|G|) A + (H.G/(B^2|G|) - |G|/B^2) B
+  float3 dA = scale(-rg * ia2, A);
+  float3 dD = scale(rg * ib2, B);
+  float3 dB = axpy(-hg * ib2 * irg, B, scale(rg * ia2 + fg * ia2 * irg, A));
+  float3 dC = axpy(hg * ib2 * irg - rg * ib2, B, scale(-fg * ia2 * irg, A));
+  float3 Fa = scale(mdE, dA), Fb = scale(mdE, dB), Fc = scale(mdE, dC), Fd = scale(mdE, dD);
+  add_force(force, ia, Fa);
+  add_force(force, ib, Fb);
+  add_force(force, ic, Fc);
+  add_force(force, id, Fd);
+  e += K * (1.0f + dd * cs);
+  // virial relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
+  float3 mg = make_float3(-G.x, -G.y, -G.z), hm = make_float3(H.x - G.x, H.y - G.y, H.z - G.z);
+  w[0] += F.x * Fa.x + mg.x * Fc.x + hm.x * Fd.x;
+  w[1] += F.y * Fa.y + mg.y * Fc.y + hm.y * Fd.y;
+  w[2] += F.z * Fa.z + mg.z * Fc.z + hm.z * Fd.z;
+  w[3] += F.x * Fa.y + mg.x * Fc.y + hm.x * Fd.y;
+  w[4] += F.x * Fa.z + mg.x * Fc.z + hm.x * Fd.z;
+  w[5] += F.y * Fa.z + mg.y * Fc.z + hm.y * Fd.z;
+}
+
+// A work item of the angle / dihedral launch: tiles [0, tb_fang[R]) of the
+// angle lists, then the dihedral tiles.
+struct AdTile {
+  bool valid = false, dih = false;
+  int r = 0, beg = 0, end = 0;
+  const int4* recs = nullptr;
+};
+__device__ __forceinline__ AdTile ad_tile(const Dev& d, int it, int na_items, int nitems) {
+  AdTile t;
+  if (it >= nitems) return t;
+  t.valid = true;
+  t.dih = it >= na_items;
+  const int* tb = t.dih ? d.tb_fdih : d.tb_fang;
+  const int t0 = t.dih ? it - na_items : it;
+  t.r = find_seg(tb, d.R, t0);
+  t.recs = t.dih ? d.dih + 18 * d.off[t.r] : d.ang + 6 * d.off[t.r];
+  t.beg = (t0 - tb[t.r]) * FORCE_TILE;
+  t.end = min(t.beg + FORCE_TILE, (t.dih ? d.n_dih : d.n_ang)[t.r]);
+  return t;
+}
+
+// Angles and dihedrals in one launch, software-pipelined per thread: the
+// records of the tile after next and the bead positions of the next tile are
+// in flight (cp.async into this thread's own shared-memory slots) while the
+// current tile is computed, so the dependent record -> position loads of a
+// tile overlap the arithmetic of the previous one.  Forces are added with
+// 16-byte reductions.  Each thread reads back only what it copied itself, so
+// no block barrier is needed between the stages.
+struct AdStage {
+  int4 rec[3][AD_PER_THREAD][AD_THREADS];     // records, three tiles
+  int4 pos[2][AD_PER_THREAD][4][AD_THREADS];  // gathered positions, two tiles
+};
+
+static_assert(sizeof(AdStage) == AD_SMEM_BYTES, "angle / dihedral shared memory layout");
+
+__global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF ff) {
   pdl_enter();
   if (aborted(d.err)) return;
+  extern __shared__ __align__(16) unsigned char ad_smem[];
+  AdStage& sm = *reinterpret_cast<AdStage*>(ad_smem);
   const int4* __restrict__ pos = d.args->pos;
   float4* force = d.args->force;
-  const int R = d.R, na_items = d.tb_fang[R], nitems = na_items + d.tb_fdih[R];
+  const int na_items = d.tb_fang[d.R], nitems = na_items + d.tb_fdih[d.R];
   const unsigned N = (unsigned)d.N;
+  const int tid = threadIdx.x;
+  auto issue_rec = [&](int k) {
+    const AdTile t = ad_tile(d, blockIdx.x + k * gridDim.x, na_items, nitems);
+#pragma unroll
+    for (int u = 0; u < AD_PER_THREAD; ++u) {
+      const int q = t.beg + tid + u * AD_THREADS;
+      const bool ok = t.valid && q < t.end;
+      cp_async16(&sm.rec[k % 3][u][tid], ok ? (const void*)(t.recs + q) : (const void*)pos, ok);
+    }
+    cp_async_commit();
+  };
+  auto issue_pos = [&](int k) {
+    const AdTile t = ad_tile(d, blockIdx.x + k * gridDim.x, na_items, nitems);
+#pragma unroll
+    for (int u = 0; u < AD_PER_THREAD; ++u) {
+      const int q = t.beg + tid + u * AD_THREADS;
+      const int4 a = sm.rec[k % 3][u][tid];
+      const int b3 = t.dih ? (a.w & 0x0FFFFFFF) : a.z;
+      bool ok = t.valid && q < t.end;
+      const bool inb = (unsigned)a.x < N && (unsigned)a.y < N && (unsigned)a.z < N && (unsigned)b3 < N;
+      if (ok && !inb) atomicOr(d.err, ERR_INTERNAL);
+      ok = ok && inb;
+      cp_async16(&sm.pos[k & 1][u][0][tid], pos + (ok ? a.x : 0), ok);
+      cp_async16(&sm.pos[k & 1][u][1][tid], pos + (ok ? a.y : 0), ok);
+      cp_async16(&sm.pos[k & 1][u][2][tid], pos + (ok ? a.z : 0), ok);
+      cp_async16(&sm.pos[k & 1][u][3][tid], pos + (ok ? b3 : 0), ok && t.dih);
+    }
+    cp_async_commit();
+  };
+  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   EV acc;
   int racc = -1;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const bool dih = it >= na_items;
-    const int* tb = dih ? d.tb_fdih : d.tb_fang;
-    int t0 = dih ? it - na_items : it;
-    int r = find_seg(tb, R, t0);
-    if (r != racc) {
+  // commit order: R0 R1 P0 | R2 P1 | R3 P2 ...; wait_group 2 leaves the two
+  // newest groups in flight
+  issue_rec(0);
+  issue_rec(1);
+  cp_async_wait<1>();
+  issue_pos(0);
+  for (int k = 0; k < ntiles; ++k) {
+    issue_rec(k + 2);  // past the last tile: an empty group
+    cp_async_wait<2>();  // records of tile k + 1 have landed
+    issue_pos(k + 1);
+    cp_async_wait<2>();  // positions of tile k have landed
+    const AdTile t = ad_tile(d, blockIdx.x + k * gridDim.x, na_items, nitems);
+    if (t.r != racc) {
       if (racc >= 0) flush_ev(d, acc, racc);
-      racc = r;
+      racc = t.r;
     }
-    int lt = t0 - tb[r];
-    int L = (int)d.box[r];
+    const int L = (int)d.box[t.r];
     float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (!dih) {
-      const int4* recs = d.ang + 6 * d.off[r];
-      int beg = lt * FORCE_TILE, end = min(beg + FORCE_TILE, d.n_ang[r]);
-      int4 a[ANG_PER_THREAD], pa[ANG_PER_THREAD], pb[ANG_PER_THREAD], pc[ANG_PER_THREAD];
-      bool ok[ANG_PER_THREAD];
 #pragma unroll
-      for (int u = 0; u < ANG_PER_THREAD; ++u) {
-        int k = beg + threadIdx.x + u * 256;
-        ok[u] = k < end;
-        if (ok[u]) a[u] = recs[k];
-        ok[u] = ok[u] && (unsigned)a[u].x < N && (unsigned)a[u].y < N && (unsigned)a[u].z < N;
-        if (k < end && !ok[u]) atomicOr(d.err, ERR_INTERNAL);
-      }
-#pragma unroll
-      for (int u = 0; u < ANG_PER_THREAD; ++u)
-        if (ok[u]) {
-          pa[u] = pos[a[u].x];
-          pb[u] = pos[a[u].y];
-          pc[u] = pos[a[u].z];
-        }
-#pragma unroll
-      for (int u = 0; u < ANG_PER_THREAD; ++u) {
-        if (!ok[u]) continue;
-        float3 ra = relq(pa[u], pb[u], L), rc = relq(pc[u], pb[u], L);
-        float K = ff.angle_k[a[u].w];
-        float ia = rsqrtf(dot3(ra, ra)), ic = rsqrtf(dot3(rc, rc));
-        float inv = ia * ic;
-        float cs = dot3(ra, rc) * inv;
-        // F_A = -K d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
-        float3 Fa = scale(-K, axpy(-cs * ia * ia, ra, scale(inv, rc)));
-        float3 Fc = scale(-K, axpy(-cs * ic * ic, rc, scale(inv, ra)));
-        float3 Fb = make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z);
-        add_force(force, a[u].x, Fa);
-        add_force(force, a[u].y, Fb);
-        add_force(force, a[u].z, Fc);
-        e += K * (1.0f + cs);
-        w[0] += ra.x * Fa.x + rc.x * Fc.x;
-        w[1] += ra.y * Fa.y + rc.y * Fc.y;
-        w[2] += ra.z * Fa.z + rc.z * Fc.z;
-        w[3] += ra.x * Fa.y + rc.x * Fc.y;
-        w[4] += ra.x * Fa.z + rc.x * Fc.z;
-        w[5] += ra.y * Fa.z + rc.y * Fc.z;
-      }
-    } else {
-      const int4* recs = d.dih + 18 * d.off[r];
-      int beg = lt * FORCE_TILE, end = min(beg + FORCE_TILE, d.n_dih[r]);
-      int4 rec[DIH_PER_THREAD], P[DIH_PER_THREAD][4];
-      bool ok[DIH_PER_THREAD];
-#pragma unroll
-      for (int u = 0; u < DIH_PER_THREAD; ++u) {
-        int k = beg + threadIdx.x + u * 256;
-        ok[u] = k < end;
-        if (ok[u]) rec[u] = recs[k];
-        unsigned id = (unsigned)(rec[u].w & 0x0FFFFFFF);
-        ok[u] = ok[u] && (unsigned)rec[u].x < N && (unsigned)rec[u].y < N && (unsigned)rec[u].z < N && id < N;
-        if (k < end && !ok[u]) atomicOr(d.err, ERR_INTERNAL);
-      }
-#pragma unroll
-      for (int u = 0; u < DIH_PER_THREAD; ++u)
-        if (ok[u]) {
-          P[u][0] = pos[rec[u].x];
-          P[u][1] = pos[rec[u].y];
-          P[u][2] = pos[rec[u].z];
-          P[u][3] = pos[rec[u].w & 0x0FFFFFFF];
-        }
-#pragma unroll
-      for (int u = 0; u < DIH_PER_THREAD; ++u) {
-        if (!ok[u]) continue;
-        int ia = rec[u].x, ib = rec[u].y, ic = rec[u].z, id = rec[u].w & 0x0FFFFFFF;
-        int t = (int)((unsigned)rec[u].w >> 28);
-        // Blondel-Karplus: F = r_A - r_B, G = r_B - r_C, H = r_D - r_C,
-        // A = F x G, B = H x G; cos phi = A.B / (|A||B|), phi = 180 deg trans.
-        // The cross, dot and triple products are formed exactly from the
-        // integer displacements and rounded once, so near-collinear quartets
-        // keep FP32 accuracy; the rest is FP32.
-        int3 Fi = reli(P[u][0], P[u][1], L), Gi = reli(P[u][1], P[u][2], L), Hi = reli(P[u][3], P[u][2], L);
-        L3 Ai = crossi(Fi, Gi), Bi = crossi(Hi, Gi);
-        const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
-        float3 F = tof(Fi, s20), G = tof(Gi, s20), H = tof(Hi, s20);
-        float3 A = tof(Ai, s40), B = tof(Bi, s40);
-        float A2 = dot3(A, A), B2 = dot3(B, B);
-        float gg = (float)doti(Gi, Gi) * s40;
-        float irg = rsqrtf(gg), rg = gg * irg;
-        float rab = rsqrtf(A2 * B2);
-        float cs = dot3(A, B) * rab;
-        // (B x A).G = -|G|^2 F.B, so sin phi = -|G| (F.B) / (|A||B|)
-        float sn = -rg * triplei(Fi, Bi, -60) * rab;
-        float K = ff.dih_k[t], dd = ff.dih_d[t];
-        // E = K (1 + d cos phi): -dE/dphi = K d sin phi
-        float mdE = K * dd * sn;
-        float fg = (float)doti(Fi, Gi) * s40, hg = (float)doti(Hi, Gi) * s40;
-        float ia2 = __frcp_rn(A2), ib2 = __frcp_rn(B2);
-        // dphi/dr_A = -|G|/A^2 A ; dphi/dr_D = |G|/B^2 B
-        // dphi/dr_B = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B
-        // dphi/dr_C = -F.G/(A^2|G|) A + (H.G/(B^2|G|) - |G|/B^2) B
-        float3 dA = scale(-rg * ia2, A);
-        float3 dD = scale(rg * ib2, B);
-        float3 dB = axpy(-hg * ib2 * irg, B, scale(rg * ia2 + fg * ia2 * irg, A));
-        float3 dC = axpy(hg * ib2 * irg - rg * ib2, B, scale(-fg * ia2 * irg, A));
-        float3 Fa = scale(mdE, dA), Fb = scale(mdE, dB), Fc = scale(mdE, dC), Fd = scale(mdE, dD);
-        add_force(force, ia, Fa);
-        add_force(force, ib, Fb);
-        add_force(force, ic, Fc);
-        add_force(force, id, Fd);
-        e += K * (1.0f + dd * cs);
-        // virial relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
-        float3 mg = make_float3(-G.x, -G.y, -G.z), hm = make_float3(H.x - G.x, H.y - G.y, H.z - G.z);
-        w[0] += F.x * Fa.x + mg.x * Fc.x + hm.x * Fd.x;
-        w[1] += F.y * Fa.y + mg.y * Fc.y + hm.y * Fd.y;
-        w[2] += F.z * Fa.z + mg.z * Fc.z + hm.z * Fd.z;
-        w[3] += F.x * Fa.y + mg.x * Fc.y + hm.x * Fd.y;
-        w[4] += F.x * Fa.z + mg.x * Fc.z + hm.x * Fd.z;
-        w[5] += F.y * Fa.z + mg.y * Fc.z + hm.y * Fd.z;
-      }
+    for (int u = 0; u < AD_PER_THREAD; ++u) {
+      const int q = t.beg + tid + u * AD_THREADS;
+      if (q >= t.end) continue;
+      const int4 a = sm.rec[k % 3][u][tid];
+      const int b3 = t.dih ? (a.w & 0x0FFFFFFF) : a.z;
+      if ((unsigned)a.x >= N || (unsigned)a.y >= N || (unsigned)a.z >= N || (unsigned)b3 >= N) continue;
+      const int4 P0 = sm.pos[k & 1][u][0][tid], P1 = sm.pos[k & 1][u][1][tid], P2 = sm.pos[k & 1][u][2][tid];
+      if (t.dih) dihedral_term(force, a, P0, P1, P2, sm.pos[k & 1][u][3][tid], L, ff, e, w);
+      else angle_term(force, a, P0, P1, P2, L, ff, e, w);
     }
     acc.add(0, e);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc.add(k + 1, w[k]);
+    for (int c = 0; c < 6; ++c) acc.add(c + 1, w[c]);
   }
+  cp_async_wait<0>();
   if (racc >= 0) flush_ev(d, acc, racc);
 }
 

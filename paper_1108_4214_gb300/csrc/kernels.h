@@ -10,7 +10,17 @@ constexpr int PURGE_TILE = 1024;   // 256 threads x 4 records (small tiles balan
 constexpr int PURGE_PER_THREAD = 4;
 constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
+constexpr int AD_THREADS = 256;    // threads of the angle / dihedral force blocks
+constexpr int AD_PER_THREAD = FORCE_TILE / AD_THREADS;
+// shared memory of an angle / dihedral block: records of three tiles and four
+// positions per record of two tiles, 16 bytes each
+constexpr int AD_SMEM_BYTES = 16 * AD_THREADS * AD_PER_THREAD * (3 + 2 * 4);
 constexpr int BEAD_TILE = 512;     // beads per force work item (2 per thread)
+constexpr int BF_THREADS = 256;    // threads of the bond force blocks
+constexpr int BF_PER_THREAD = BEAD_TILE / BF_THREADS;
+// shared memory of a bond force block: slots of three tiles, own and partner
+// positions of two tiles, 16 bytes each
+constexpr int BF_SMEM_BYTES = 16 * BF_THREADS * BF_PER_THREAD * (3 + 2 * (1 + DYNBOND_SLOTS));
 constexpr int EV_COPIES = 32;      // striped copies of each replica's energy / virial sums
 
 // bonded force-field tables in FP32 (kernel parameter space)

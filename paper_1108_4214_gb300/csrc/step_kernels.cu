@@ -1378,13 +1378,16 @@ __global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restric
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   const Rebuild rb{d, rt, all_new};
-  const long long n = 5ll * d.cnt->n_nbl;  // five independent parts per new bond
+  // five independent parts per new bond, part-major: the lanes of a warp run
+  // the same part on consecutive bonds (convergent, and the records of a
+  // chain's consecutive bonds land next to each other)
+  const long long nn = d.cnt->n_nbl, n = 5 * nn;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long i = base + threadIdx.x;
     const bool valid = i < n;
-    const int part = (int)(i % 5);
-    int4 e = valid ? d.nbl[i / 5] : make_int4(0, 0, -1, 0);
+    const int part = valid ? (int)(i / nn) : 0;
+    int4 e = valid ? d.nbl[i - part * nn] : make_int4(0, 0, -1, 0);
     CountEmit ce;
     if (valid) rb.run(e.x, e.y, part, ce);
     int oa, od;

@@ -264,6 +264,31 @@ def test_host_buffer_entry_point_matches_device_path():
         assert np.abs(ev_h - ev_d).max() <= 1e-7 * np.abs(ev_d).max()
 
 
+def test_misaligned_buffers_are_rejected_before_any_launch():
+    """int4 / float4 per bead: a device pointer off a 16-byte boundary is an
+    argument error (nothing is launched, the context stays usable)."""
+    s = W.config1()
+    D = dynbond()
+    ctx = D.Context(s, flags=D.FLAG_NO_AUTOTUNE)
+    p = torch.from_numpy(s.snapshot(0)).cuda()
+    n = p.numel()
+    buf = torch.zeros(n + 4, dtype=torch.int32, device=p.device)
+    buf[1:1 + n] = p.reshape(-1)
+    bad = buf[1:1 + n].view(-1, 4)
+    assert bad.data_ptr() % 16 == 4
+    with pytest.raises(D.DynbondError) as e:
+        ctx.step(bad, 0, stats=True)
+    assert e.value.status == 1 and "aligned" in str(e.value)
+    fbuf = torch.zeros(4 * s.n_beads + 4, dtype=torch.float32, device=p.device)
+    ev = torch.zeros((s.n_replicas, 7), dtype=torch.float64, device=p.device)
+    with pytest.raises(D.DynbondError) as e:
+        ctx.forces(p, fbuf[1:1 + 4 * s.n_beads].view(-1, 4), ev)
+    assert e.value.status == 1
+    st = ctx.step(p, 0, stats=True)
+    o = O.Oracle(s)
+    assert np.array_equal(st, o.step(s.snapshot(0), 0))
+
+
 def test_position_outside_box_is_reported_and_sticks():
     s = W.config1()
     D = dynbond()
