@@ -123,7 +123,11 @@ enum {
  *                 pairs / bonds of two reactive beads.
  *   flags         DYNBOND_FLAG_*.
  *   cell_scale    0 = autotune on the first dynbond_step (dynbond_autotune);
- *                 k >= 1: cell edge = k x the largest creation distance.
+ *                 k >= 1: cell edge along x and y = k x the largest creation
+ *                 distance (the reach).
+ *   cell_zdiv     with cell_scale k >= 1: cells are cell_zdiv times thinner
+ *                 along z (0 = 1, cubic cells).  Along z the search reads, in
+ *                 each cell column, the cells overlapping [z - reach, z + reach].
  *                 The cell geometry never changes results.
  *   block_size    0 = default (256) threads per block for the bead passes.
  *   spin_limit    0 = default; iterations of every bounded device-side wait.
@@ -139,7 +143,8 @@ typedef struct dynbond_params {
   int32_t cell_scale;
   int32_t block_size;
   int32_t spin_limit;
-  int32_t reserved[5];
+  int32_t cell_zdiv;
+  int32_t reserved[4];
 } dynbond_params;
 
 /*
@@ -282,9 +287,11 @@ dynbond_status dynbond_get_topology(dynbond_ctx* ctx, dynbond_topology* topo);
 dynbond_status dynbond_topology_hash(dynbond_ctx* ctx, uint64_t* h_out);
 
 /*
- * Autotuning of launch geometry (not part of the paper): the cell edge (1, 1.25,
- * 1.5, 2 or 3 x the largest creation distance) and the bead-pass grid size (4, 8
- * or 16 blocks per SM) are chosen by timing the front of a call (cell binning,
+ * Autotuning of launch geometry (not part of the paper): the cell edge along x
+ * and y (1, 1.25, 1.5, 2 or 3 x the largest creation distance), the z edge (the
+ * x / y edge divided by 1, 2 or 4; grids larger than the one allocated at
+ * creation are skipped) and the bead-pass grid size (4, 8 or 16 blocks per
+ * SM) are chosen by timing the front of a call (cell binning,
  * breakage nomination and candidate search, which write scratch only; best of
  * three runs) on the positions d_pos; the fastest is kept and the captured work
  * is rebuilt.  No choice changes results.
@@ -297,6 +304,7 @@ typedef struct dynbond_tuning {
   int32_t candidate_blocks_per_sm;
   float front_ms;   /* device time of the timed front at the chosen geometry */
   int32_t tuned;
+  int32_t cell_zdiv; /* z edge = x / y edge / cell_zdiv */
 } dynbond_tuning;
 
 dynbond_status dynbond_autotune(dynbond_ctx* ctx, const int32_t* d_pos, dynbond_tuning* out);

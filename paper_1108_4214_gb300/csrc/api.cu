@@ -56,6 +56,7 @@ struct dynbond_ctx {
   bool octant = false;          // candidate search by octant (see set_geometry)          // smallest integer cell width covering the largest creation distance
   long long max_cells = 0;      // cells allocated (geometry at scale 1)
   int* d_nc = nullptr;
+  int* d_ncz = nullptr;
   long long* d_cb = nullptr;
   dynbond_tuning tuning{};
   unsigned long long* d_hash = nullptr;  // per-replica topology hashes
@@ -406,9 +407,9 @@ void collect_profile(dynbond_ctx* c, int which) {
 
 // Cell grid of every replica for a cell edge of `scale` x the reach (at least
 // the reach, at most 1024 cells per axis); uploads it and sizes the scan.
-dynbond_status set_geometry(dynbond_ctx* c, double scale) {
+dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
   const int R = c->R;
-  std::vector<int> nc(R);
+  std::vector<int> nc(R), nz(R);
   std::vector<long long> cb(R + 1, 0);
   bool octant = true;
   for (int r = 0; r < R; ++r) {
@@ -416,12 +417,17 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale) {
     long long ncap = c->reach > 0 ? L / c->reach : 1;
     long long n = c->reach > 0 ? (long long)((double)L / (scale * (double)c->reach)) : 1;
     n = std::max<long long>(1, std::min<long long>({n, ncap, 1024}));
+    // z: zdiv cells per x / y edge (any count works: the search takes the
+    // z cells overlapping the reach interval)
+    long long m = c->reach > 0 ? (long long)((double)L * zdiv / (scale * (double)c->reach)) : 1;
+    m = std::max<long long>(1, std::min<long long>(m, 4096));
     nc[r] = (int)n;
-    cb[r + 1] = cb[r] + n * n * n;
+    nz[r] = (int)m;
+    cb[r + 1] = cb[r] + n * n * m;
     // cells at least twice the reach on every axis: the octant search suffices
     octant = octant && n >= 3 && 2 * c->reach * n <= L;
   }
-  if (c->max_cells && cb[R] > c->max_cells) return fail(c, DYNBOND_EINVAL, "cell geometry larger than allocated");
+  if (c->max_cells && cb[R] > c->max_cells) return fail(c, DYNBOND_ECAPACITY, "cell geometry larger than allocated");
   if (cb[R] * c->rt.n_cls >= 0x7FFFFFFFll)
     return fail(c, DYNBOND_EINVAL, "cell grid too large: boxes over 2^31 cell keys (cell classes x cells)");
   c->n_cells = cb[R];
@@ -431,10 +437,12 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale) {
   c->grid_scan = bounded_grid(c->d.n_keys, 256 * 32, c->nsm * 4);
   if (c->d_nc) {
     CUDA_TRY(c, cudaMemcpyAsync(c->d_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ncz, nz.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cb, cb.data(), 8 * (R + 1), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
   c->tuning.cell_scale = scale;
+  c->tuning.cell_zdiv = zdiv;
   return DYNBOND_OK;
 }
 
@@ -586,7 +594,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->h_box.assign(sys->box_q, sys->box_q + R);
   c->reach = 0;
   while (c->reach * c->reach < c->rt.r2max) ++c->reach;
-  st = set_geometry(c, params->cell_scale > 0 ? (double)params->cell_scale : 1.0);
+  st = set_geometry(c, params->cell_scale > 0 ? (double)params->cell_scale : 1.0,
+                    params->cell_scale > 0 && params->cell_zdiv > 0 ? params->cell_zdiv : 1);
   if (st) return st;
   c->max_cells = c->n_cells;
   c->W = N / 32 + 1;
@@ -601,6 +610,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   long long* p_box;
   long long* p_cb;
   int* p_nc;
+  int* p_ncz;
   int* p_rep;
   unsigned char* p_type;
   unsigned* p_stream;
@@ -614,7 +624,9 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(p_box, R);
   ALLOC(p_cb, R + 1);
   ALLOC(p_nc, R);
+  ALLOC(p_ncz, R);
   c->d_nc = p_nc;
+  c->d_ncz = p_ncz;
   c->d_cb = p_cb;
   ALLOC(p_rep, N);
   ALLOC(p_type, N);
@@ -714,6 +726,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   d.box = p_box;
   d.cell_base = p_cb;
   d.nc = p_nc;
+  d.ncz = p_ncz;
+  d.reach = c->reach;
   d.rep = p_rep;
   d.type = p_type;
   d.stream = p_stream;
@@ -742,7 +756,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemcpyAsync(c->d_rt, &c->rt, sizeof(RuleTab), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_off, offv.data(), 8 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_box, boxv.data(), 8 * R, cudaMemcpyHostToDevice, s));
-  st = set_geometry(c, c->tuning.cell_scale);
+  st = set_geometry(c, c->tuning.cell_scale, c->tuning.cell_zdiv);
   if (st) return st;
   CUDA_TRY(c, cudaMemcpyAsync(p_rep, rep.data(), 4 * N, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(p_type, type.data(), N, cudaMemcpyHostToDevice, s));
@@ -889,11 +903,19 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
     k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, 0, 1, 0);
+    const int zdivs[] = {1, 2, 4};
     float best = 1e30f;
     double best_scale = 1.0;
-    int best_grid = 8;
-    for (double sc : scales) {
-      if ((st = set_geometry(c, sc))) break;
+    int best_grid = 8, best_zdiv = 1;
+    for (int g = 0; g < 15; ++g) {
+      const double sc = scales[g / 3];
+      const int zd = zdivs[g % 3];
+      st = set_geometry(c, sc, zd);
+      if (st == DYNBOND_ECAPACITY) {  // more cells than allocated: not a candidate
+        st = DYNBOND_OK;
+        continue;
+      }
+      if (st) break;
       for (int gm : grids) {
         c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * gm);
         float ms = 1e30f;
@@ -909,13 +931,14 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
         if (ms < best) {
           best = ms;
           best_scale = sc;
+          best_zdiv = zd;
           best_grid = gm;
         }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!st) st = set_geometry(c, best_scale);
+    if (!st) st = set_geometry(c, best_scale, best_zdiv);
     c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * best_grid);
     c->tuning.bead_blocks_per_sm = c->tuning.candidate_blocks_per_sm = best_grid;
     c->tuning.front_ms = best;

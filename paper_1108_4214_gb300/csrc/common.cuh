@@ -98,7 +98,9 @@ struct Dev {
   int spin_limit;
   const long long* off;        // [R+1]
   const long long* box;        // [R]
-  const int* nc;               // [R] cells per axis
+  const int* nc;               // [R] cells along x and y
+  const int* ncz;              // [R] cells along z
+  long long reach;              // smallest integer >= the largest creation distance (quantised units)
   const long long* cell_base;  // [R+1]
   long long n_cells;            // cells of one class (all replicas)
   long long n_keys;             // n_cls * n_cells binned keys

@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
         d.bead_cell[i] = -1;
       } else {
         if (creation_eligible(rt, bt, s)) {
-          const int nc = d.nc[r];
+          const int nc = d.nc[r], nz = d.ncz[r];
           const float f = (float)nc / (float)L;
-          long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f), cz = cell_of(p.z, nc, L, f);
-          long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nc + cz;
+          long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f);
+          long long cz = cell_of(p.z, nz, L, (float)nz / (float)L);
+          long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nz + cz;
           atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
           d.bead_cell[i] = (int)c;
         } else {
@@ -415,29 +416,31 @@ __device__ __forceinline__ void cand_slow(const uint4* __restrict__ slots, const
 }
 
 // Visit every creation candidate of eligible bead i (sorted entry `me`):
-// for each cell-list class holding partner types of bead i, the entries of
-// the 27 neighbouring cells (distinct cells when a replica has fewer than 3
-// per axis) within the largest creation distance are collected first; the
-// rule and graph-distance tests then run on them after the scan, so the
-// lanes of a warp take the rare path together instead of one after another.
-// GEO 1: every replica's cells are at least twice the reach wide (octant
-// search); GEO 0: full 3 x 3 x 3 search, correct for any cell geometry.
+// for each cell-list class holding partner types of bead i, the entries
+// within the largest creation distance (the reach) among the neighbouring
+// cell columns (distinct columns when a replica has fewer than 3 per axis),
+// restricted along z to the cells overlapping [z - reach, z + reach], are
+// collected first; the rule and graph-distance tests then run on them after
+// the scan, so the lanes of a warp take the rare path together instead of
+// one after another.  GEO 1: every replica's columns are at least twice the
+// reach wide (octant of columns); GEO 0: 3 x 3 columns, correct for any
+// geometry with columns at least the reach wide.
 template <int GEO>
 __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned cmask,
                                                 long long r2max, const int4& me, int i, LocalList* ll, int mode,
                                                 int4** out, int* pj, long long* pd, int* np_out) {
   const int ti = me.w & 15;
   const int r = rep_of(d, i);
-  const int L = (int)d.box[r], nc = d.nc[r];
+  const int L = (int)d.box[r], nc = d.nc[r], nz = d.ncz[r];
   // cell keys fit in 32 bits (n_cls * n_cells < 2^31 is checked on the host)
   const int cb = (int)d.cell_base[r], ncl = (int)d.n_cells;
   const float f = (float)nc / (float)L;
-  const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f), cz = cell_of(me.z, nc, L, f);
-  // x and y: the distinct neighbouring columns; z: the neighbouring cells of
-  // a column are contiguous in cell order, so each column is one or two
-  // contiguous runs of the sorted array.  Cells at least twice the reach
-  // wide: a bead's reach only touches the neighbour on the side of the half
-  // it sits in, so 2 x 2 columns of 2 cells (octant); else 3 x 3 columns of 3.
+  const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f);
+  // x and y: the distinct neighbouring columns.  Columns at least twice the
+  // reach wide: a bead's reach only touches the neighbour on the side of the
+  // half it sits in, so 2 x 2 columns (octant); else 3 x 3.  z: the cells of a
+  // column are contiguous in cell order, so the cells a column contributes
+  // are one or two contiguous runs of the sorted array.
   const bool oct = GEO == 1;
   int nx = nc >= 3 ? 3 : nc;
   int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
@@ -449,36 +452,35 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
     nx = 2;
     if (lower(me.x, cx)) xs[1] = xs[2];
     if (lower(me.y, cy)) ys[1] = ys[2];
-    if (lower(me.z, cz)) {  // cells cz - 1 and cz
-      if (cz == 0) {
-        z0 = z1 = 0;
-        w0 = w1 = nc - 1;
-      } else {
-        z0 = cz - 1;
-        z1 = cz;
-      }
-    } else {  // cells cz and cz + 1
-      if (cz == nc - 1) {
-        z0 = z1 = nc - 1;
-        w0 = w1 = 0;
-      } else {
-        z0 = cz;
-        z1 = cz + 1;
-      }
-    }
-  } else if (nc >= 3) {
-    z0 = cz - 1;
-    z1 = cz + 1;
-    if (z0 < 0) {  // cz = 0: cells nc-1, 0, 1
+  }
+  // z: the cells overlapping [z - reach, z + reach] (periodic), as a main run
+  // and, across the boundary, a wrapped run; the whole column if they meet
+  {
+    const float fz = (float)nz / (float)L;
+    const long long zlo = (long long)me.z - d.reach, zhi = (long long)me.z + d.reach;
+    if (zlo >= 0 && zhi < L) {
+      z0 = cell_of((int)zlo, nz, L, fz);
+      z1 = cell_of((int)zhi, nz, L, fz);
+    } else if (zlo < 0 && zhi < L) {
+      const int a = cell_of((int)(zlo + L), nz, L, fz), b = cell_of((int)zhi, nz, L, fz);
       z0 = 0;
-      w0 = w1 = nc - 1;
-    } else if (z1 >= nc) {  // cz = nc-1: cells nc-2, nc-1, 0
-      z1 = nc - 1;
-      w0 = w1 = 0;
+      z1 = a > b ? b : nz - 1;
+      if (a > b) {
+        w0 = a;
+        w1 = nz - 1;
+      }
+    } else if (zlo >= 0 && zhi >= L) {
+      const int a = cell_of((int)zlo, nz, L, fz), b = cell_of((int)(zhi - L), nz, L, fz);
+      z0 = b < a ? a : 0;
+      z1 = nz - 1;
+      if (b < a) {
+        w0 = 0;
+        w1 = b;
+      }
+    } else {
+      z0 = 0;
+      z1 = nz - 1;
     }
-  } else {
-    z0 = 0;
-    z1 = nc - 1;
   }
   int np = 0;
   bool more = false;
@@ -495,7 +497,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
       const int a = ab / NA, b = ab % NA;
       int len = 0, q0 = 0;
       if (a < nx && b < nx) {
-        const int row = cbk + (xs[a] * nc + ys[b]) * nc;
+        const int row = cbk + (xs[a] * nc + ys[b]) * nz;
         q0 = d.cell_start[row + lo - 1];
         len = d.cell_start[row + hi] - q0;
       }
@@ -545,7 +547,7 @@ __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __r
       const int cbk = (__ffs(cm) - 1) * ncl + cb;
       for (int a = 0; a < nx; ++a)
         for (int b = 0; b < nx; ++b) {
-          const int row = cbk + (xs[a] * nc + ys[b]) * nc;
+          const int row = cbk + (xs[a] * nc + ys[b]) * nz;
           for (int run = 0; run < 2; ++run) {
             int lo = run ? w0 : z0, hi = run ? w1 : z1;
             if (hi < lo) continue;

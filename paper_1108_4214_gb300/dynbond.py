@@ -50,7 +50,8 @@ class Rule(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("seed", c_u64), ("paircheck13", c_i32), ("paircheck14", c_i32), ("max_rounds", c_i32),
                 ("prob_mode", c_i32), ("reactive_mask", c_u32), ("flags", c_i32), ("cell_scale", c_i32),
-                ("block_size", c_i32), ("spin_limit", c_i32), ("reserved", c_i32 * 5)]
+                ("block_size", c_i32), ("spin_limit", c_i32), ("cell_zdiv", c_i32),
+                ("reserved", c_i32 * 4)]
 
 
 class ForceField(ctypes.Structure):
@@ -70,7 +71,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("cell_scale", c_dbl), ("bead_blocks_per_sm", c_i32), ("candidate_blocks_per_sm", c_i32),
-                ("front_ms", ctypes.c_float), ("tuned", c_i32)]
+                ("front_ms", ctypes.c_float), ("tuned", c_i32), ("cell_zdiv", c_i32)]
 
 
 class DPD(ctypes.Structure):
@@ -222,6 +223,7 @@ class Context:
         p.reactive_mask = int(prm["reactive_mask"])
         p.flags = int(flags) | int(prm.get("flags", 0))
         p.cell_scale = int(prm.get("cell_scale", 0))
+        p.cell_zdiv = int(prm.get("cell_zdiv", 0))
         p.spin_limit = int(prm.get("spin_limit", 0))
         ff = ForceField()
         f = system.forcefield

@@ -116,13 +116,15 @@ def test_initial_typing_of_the_papers_dna_ladder():
     assert d.tolist() == sorted(g["expected_dihedrals"])
 
 
-@pytest.mark.parametrize("cell_scale", [0, 1, 2, 3])
-def test_plain_2048_beads_ten_calls(cell_scale):
+@pytest.mark.parametrize("cell_scale,cell_zdiv", [(0, 0), (1, 1), (2, 1), (3, 1), (1, 4), (2, 2), (2, 4), (3, 7)])
+def test_plain_2048_beads_ten_calls(cell_scale, cell_zdiv):
     """Ten calls on 2048 beads, autotuned (0) and with fixed cell edges of 1,
-    2 and 3 x the creation reach: the last two search only the octant of
-    neighbouring cells on the side of the cell half each bead sits in."""
+    2 and 3 x the creation reach along x and y (2 and 3: only the octant of
+    columns on the side of the column half each bead sits in is searched)
+    and 1 to 7 cells per edge along z (the cells overlapping the reach
+    interval are searched)."""
     s = W.config1()
-    _, worst = run_parity(s, 10, params=dict(cell_scale=cell_scale))
+    _, worst = run_parity(s, 10, params=dict(cell_scale=cell_scale, cell_zdiv=cell_zdiv))
     print("max force / ev error", max(w[0] for w in worst), max(w[1] for w in worst))
 
 
@@ -133,7 +135,9 @@ def test_random_systems_all_rule_kinds(seed):
                               n_replicas=1 + seed % 3,
                               params=dict(paircheck13=seed % 2, paircheck14=(seed // 2) % 2, max_rounds=seed % 3,
                                           prob_mode=(seed // 3) % 2))
-    run_parity(s, 4)
+    # seeds from 20 on: fixed cell geometries, 1 or 2 reaches along x / y, 1 to 5 cells per edge along z
+    geo = dict(cell_scale=1 + (seed % 3 == 0), cell_zdiv=1 + seed % 5) if seed >= 20 else None
+    run_parity(s, 4, params=geo)
 
 
 def test_paper_exact_mode_oligomers_on_templates():
@@ -170,11 +174,11 @@ def test_duplex_melts_and_reforms():
     run_parity(s, 2, snaps=[snap, snap])
 
 
-@pytest.mark.parametrize("cell_scale", [0, 2])
-def test_plain_1m_beads_parity(cell_scale):
+@pytest.mark.parametrize("cell_scale,cell_zdiv", [(0, 0), (2, 1), (2, 4)])
+def test_plain_1m_beads_parity(cell_scale, cell_zdiv):
     s = W.config2()
     snaps = s.snapshots(0, 3)
-    _, worst = run_parity(s, 3, snaps=snaps, params=dict(cell_scale=cell_scale))
+    _, worst = run_parity(s, 3, snaps=snaps, params=dict(cell_scale=cell_scale, cell_zdiv=cell_zdiv))
     print("1M: max force / ev error", worst)
 
 
@@ -342,7 +346,7 @@ def test_autotuned_and_fixed_geometries_give_identical_results():
         for x, y in zip(tops[0], t):
             assert np.array_equal(x, y)
     info = ctxs[0].autotune(torch.from_numpy(s.snapshot(4)).cuda())
-    assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.25, 1.5, 2.0, 3.0)
+    assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.25, 1.5, 2.0, 3.0) and info["cell_zdiv"] in (1, 2, 4)
 
 
 def test_bounded_wait_gives_up_with_a_status_and_leaves_the_device_usable():
