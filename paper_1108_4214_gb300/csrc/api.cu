@@ -434,7 +434,7 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
   c->octant = octant;
   c->d.n_cells = c->n_cells;
   c->d.n_keys = c->n_cells * c->rt.n_cls;
-  c->grid_scan = bounded_grid(c->d.n_keys, 256 * 32, c->nsm * 4);
+  c->grid_scan = bounded_grid(c->d.n_keys, 256 * SCAN_PER_THREAD, c->nsm * 4);
   if (c->d_nc) {
     CUDA_TRY(c, cudaMemcpyAsync(c->d_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_ncz, nz.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
@@ -664,6 +664,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.bm_ba, c->W);
   ALLOC(d.bm_bn, c->W);
   ALLOC(d.bm_bk, c->W);
+  ALLOC(d.bm_elig, c->W);
   ALLOC(d.bm_dirty, c->W);
   ALLOC(d.bm_new, c->W);
   ALLOC(d.live[0], 2 * N);
@@ -707,7 +708,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     d.stats = (long long*)(base + ((ints * sizeof(int) + 15) / 16) * 16);
   }
   {
-    c->st_scan_n = c->n_cells * c->rt.n_cls / (256 * 32) + 2;
+    c->st_scan_n = c->n_cells * c->rt.n_cls / (256 * SCAN_PER_THREAD) + 2;  // tiles of the cell scan
     long long tot = c->st_scan_n;
     unsigned long long* base;
     ALLOC(base, tot);
@@ -767,7 +768,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemcpyAsync(d.n_bonds, nb_rep.data(), 8 * R, cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemcpyAsync(d.tb_beads, tbeads.data(), 4 * (R + 1), cudaMemcpyHostToDevice, s));
   CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
-  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_bn, d.bm_bk, d.bm_dirty, d.bm_new})
+  for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_bn, d.bm_bk, d.bm_elig, d.bm_dirty, d.bm_new})
     CUDA_TRY(c, cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)c->W, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_ang, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_dih, 0, 4 * R, s));
@@ -795,6 +796,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s));
   CUDA_TRY(c, cudaMemsetAsync(c->small, 0, c->small_bytes, s));
   CUDA_TRY(c, cudaMemsetAsync(c->status_all, 0, c->status_bytes, s));
+  k_bead_flags<<<c->grid_bead, 256, 0, s>>>(d, c->d_rt);
   k_allbonds<<<c->grid_bead, 256, 0, s>>>(d);
   k_rebuild<<<c->grid_seg, 256, 0, s>>>(d, c->d_rt, 1);
   CUDA_TRY(c, cudaMemsetAsync(d.ev_acc, 0, sizeof(double) * 7 * (size_t)R * EV_COPIES, s));

@@ -147,7 +147,8 @@ struct Dev {
   unsigned* bm_ca;             // [W] creation-active beads
   unsigned* bm_ba;             // [W] breakage/kill-active beads
   unsigned* bm_bn;             // [W] beads nominating a breakage partner
-  unsigned* bm_bk;             // [W] beads holding a bond of a type named by a breakage rule
+  unsigned* bm_bk;             // [W] beads holding a bond of a type named by a breakage rule (kept current)
+  unsigned* bm_elig;           // [W] beads that can form a bond (creation_eligible; kept current)
   unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
   unsigned* bm_new;            // [W] beads with a formed or retyped bond
   int* live[2];                // [2*N] each: active (system << 31 | bead) entries between rounds
@@ -285,6 +286,18 @@ __device__ __forceinline__ void red_add_f4(float4* f, long long i, float x, floa
                : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async; zero-filled when
+// !pred, the source address is then not read)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Replica of bead i: the common single-system case needs no load, so later
 // loads that depend on the replica (box, offsets, streams) are not delayed.
 __device__ __forceinline__ int rep_of(const Dev& d, long long i) { return d.R == 1 ? 0 : d.rep[i]; }
@@ -348,6 +361,19 @@ __device__ __forceinline__ bool maxbond_ok(const RuleTab& rt, int bt, const uint
 
 // Can the bead take part in any creation pair (reactive, named by a creation
 // rule in some role with room for the type it would store)?
+// Does a reactive bead of type bt hold a bond of a type named by a breakage
+// (break / convert / kill) rule?
+__device__ __forceinline__ bool holds_breakable(const RuleTab& rt, int bt, const uint4& s) {
+  if (!rt.breakish || !has_bit(rt.reactive, bt)) return false;
+  bool b = false;
+#pragma unroll
+  for (int q = 0; q < SLOTS; ++q) {
+    const unsigned v = s_get(s, q);
+    b |= v && has_bit(rt.breakish, s_type(v));
+  }
+  return b;
+}
+
 __device__ __forceinline__ bool creation_eligible(const RuleTab& rt, int bt, const uint4& s) {
   if (!has_bit(rt.reactive, bt) || s_deg(s) >= SLOTS) return false;
   uint32_t m = rt.role_store[bt];
@@ -548,6 +574,39 @@ __device__ __forceinline__ int block_alloc(int* counter, int want) {
   }
   __syncthreads();
   const int at = s_base + s_off[wid] + incl - want;
+  __syncthreads();
+  return at;
+}
+
+// block_alloc for four counters at once: each thread takes one slot of
+// counter[role] (role 0..3) or none (role < 0); the four block totals are
+// added with independent atomics by four lanes, so the block waits for one
+// round trip.  Returns this thread's slot.  Every thread of the block must
+// call it.
+__device__ __forceinline__ int block_alloc4(int* counter, int role) {
+  __shared__ int s_cnt[32][4];
+  __shared__ int s_base[4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  unsigned bal[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) bal[q] = __ballot_sync(FULL, role == q);
+  if (lane < 4) s_cnt[wid][lane] = __popc(lane == 0 ? bal[0] : lane == 1 ? bal[1] : lane == 2 ? bal[2] : bal[3]);
+  __syncthreads();
+  if (wid == 0 && lane < 4) {
+    int run = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int c = s_cnt[w][lane];
+      s_cnt[w][lane] = run;
+      run += c;
+    }
+    s_base[lane] = run ? atomicAdd(counter + lane, run) : 0;
+  }
+  __syncthreads();
+  int at = 0;
+  if (role >= 0) {
+    const unsigned b = role == 0 ? bal[0] : role == 1 ? bal[1] : role == 2 ? bal[2] : bal[3];
+    at = s_base[role] + s_cnt[wid][role] + __popc(b & ((1u << lane) - 1u));
+  }
   __syncthreads();
   return at;
 }

@@ -128,18 +128,6 @@ __device__ void flush_ev(const Dev& d, EV& acc, int r) {
   __syncthreads();
 }
 
-// 16-byte asynchronous copy global -> shared (zero-filled when !pred; the
-// source address is then not read)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(src), "r"(pred ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // Bonds: each bead sums, over its occupied slots, the harmonic force of the
 // type it stores for that bond (directional bonds, Sec. 2) and books half the
 // energy; no atomics.  Software-pipelined per thread like the angle /

@@ -9,6 +9,7 @@ namespace dynbond {
 constexpr int PURGE_TILE = 1024;   // 256 threads x 4 records (small tiles balance the blocks)
 constexpr int PURGE_PER_THREAD = 4;
 constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
+constexpr int SCAN_PER_THREAD = 32;  // cell keys per thread in the histogram scan (a multiple of 4)
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
 constexpr int AD_THREADS = 256;    // threads of the angle / dihedral force blocks
 constexpr int AD_PER_THREAD = FORCE_TILE / AD_THREADS;
@@ -29,6 +30,7 @@ struct FF {
 };
 
 __global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_bead_flags(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_scan_cells(Dev d);
 __global__ void k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks);
 __global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);

@@ -21,7 +21,6 @@
 
 namespace dynbond {
 
-constexpr int SCAN_PER_THREAD = 32;  // cells per thread in the histogram scan
 constexpr int SCAN_BATCH = 2;  // candidate entries loaded together
 template <int N>
 struct IntC {
@@ -139,52 +138,58 @@ __device__ __forceinline__ unsigned bead_breakage(const Dev& d, const RuleTab& r
   return (ba ? 1u : 0u) | (nbrk > 0 && !settled ? 2u : 0u);
 }
 
-// Per bead: bounds check, binning of the beads that can form bonds (Appendix
-// step 2; occupancy counts only, the scatter assigns the slots), and the
-// bitmap of beads holding a bond of a type named by a breakage rule, whose
-// nomination runs beside the scatter (k_scatter).
+// Per bead: bounds check and binning of the beads that can form bonds
+// (Appendix step 2; occupancy counts only, the scatter assigns the slots).
+// Which beads can form a bond, and which hold a breakable bond, depends on
+// their bonds only: both bitmaps are computed at creation (k_bead_flags) and
+// kept current by the edit, so this pass reads positions and the bitmap.
 __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
   const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const int r = rep_of(d, i);
+    const int4 p = pos[i];
+    const bool elig = (d.bm_elig[i >> 5] >> (i & 31)) & 1u;
+    const int L = (int)d.box[r];
+    int cell = -1;
+    if (p.x < 0 || p.y < 0 || p.z < 0 || p.x >= L || p.y >= L || p.z >= L) {
+      atomicOr(d.err, ERR_POS);
+    } else if (elig) {
+      const int bt = d.type[i];
+      const int nc = d.nc[r], nz = d.ncz[r];
+      const float f = (float)nc / (float)L;
+      long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f);
+      long long cz = cell_of(p.z, nz, L, (float)nz / (float)L);
+      long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nz + cz;
+      atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
+      cell = (int)c;
+    }
+    d.bead_cell[i] = cell;
+  }
+}
+
+// Both bead bitmaps from the bonds, for every bead (at creation).
+__global__ void __launch_bounds__(256) k_bead_flags(Dev d, const RuleTab* __restrict__ rtp) {
+  const RuleTab& rt = *rtp;
+  const long long N = d.N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += stride) {
     const long long i = base + threadIdx.x;
-    bool brk = false;
+    bool el = false, bk = false;
     if (i < N) {
-      const int r = rep_of(d, i);
       const int bt = d.type[i];
       const uint4 s = d.slots[i];
-      const int4 p = pos[i];
-      const int L = (int)d.box[r];
-      if (p.x < 0 || p.y < 0 || p.z < 0 || p.x >= L || p.y >= L || p.z >= L) {
-        atomicOr(d.err, ERR_POS);
-        d.bead_cell[i] = -1;
-      } else {
-        if (creation_eligible(rt, bt, s)) {
-          const int nc = d.nc[r], nz = d.ncz[r];
-          const float f = (float)nc / (float)L;
-          long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f);
-          long long cz = cell_of(p.z, nz, L, (float)nz / (float)L);
-          long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nz + cz;
-          atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
-          d.bead_cell[i] = (int)c;
-        } else {
-          d.bead_cell[i] = -1;
-        }
-        if (rt.breakish && has_bit(rt.reactive, bt)) {
-#pragma unroll
-          for (int q = 0; q < SLOTS; ++q) {
-            const unsigned v = s_get(s, q);
-            brk |= v && has_bit(rt.breakish, s_type(v));
-          }
-        }
-      }
+      el = creation_eligible(rt, bt, s);
+      bk = holds_breakable(rt, bt, s);
     }
-    const unsigned m = __ballot_sync(FULL, brk);
-    if (lane == 0 && i < N) d.bm_bk[i >> 5] = m;
+    const unsigned me = __ballot_sync(FULL, el), mb = __ballot_sync(FULL, bk);
+    if ((threadIdx.x & 31) == 0 && i < N) {
+      d.bm_elig[i >> 5] = me;
+      d.bm_bk[i >> 5] = mb;
+    }
   }
 }
 
@@ -982,6 +987,15 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
     else s_set(ns, nk++, ((unsigned)form_partner << 4) | (unsigned)form_type);
   }
   d.slots[i] = ns;
+  // the bead's bonds changed: refresh its bits in the two bead bitmaps
+  {
+    const int bt = d.type[i];
+    const unsigned bit = 1u << (i & 31);
+    if (creation_eligible(rt, bt, ns)) atomicOr(&d.bm_elig[i >> 5], bit);
+    else atomicAnd(&d.bm_elig[i >> 5], ~bit);
+    if (holds_breakable(rt, bt, ns)) atomicOr(&d.bm_bk[i >> 5], bit);
+    else atomicAnd(&d.bm_bk[i >> 5], ~bit);
+  }
   o.dirty = (removed | changed) != 0;
   o.fresh = form_partner >= 0 || conv_partner >= 0;
   if (o.dirty) d.rem[i] = rp;
@@ -1212,12 +1226,7 @@ __global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
         pos = p;
       }
     }
-    int at = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {  // the tile lies in one replica
-      int a = block_alloc(&d.fillc[4 * r + q], role == q ? 1 : 0);
-      if (role == q) at = a;
-    }
+    const int at = block_alloc4(&d.fillc[4 * r], role);  // the tile lies in one replica
     if (role < 0) continue;
     int code = (role & 1) ? -(pos + 1) : pos + 1;
     int other = atomicExch((dih ? d.pr_dih : d.pr_ang) + base + at, code);
