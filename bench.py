@@ -171,10 +171,10 @@ def sources_sha1():
     return h.hexdigest()
 
 
-def recorded_traffic(phase):
+def recorded_traffic(phase, tuning=None):
     """DRAM bytes per launch of the phase's kernel from the committed ncu
     summary, or None if none was recorded or the kernel sources changed since."""
-    kern = PHASE_KERNEL.get(phase)
+    kern = phase_kernel(phase, tuning) if phase in PHASE_KERNEL else None
     path = os.path.join(ROOT, "profiles", "traffic_plain-1M.txt")
     if kern is None or not os.path.exists(path):
         return None
@@ -186,10 +186,18 @@ def recorded_traffic(phase):
     return None
 
 
+def phase_kernel(phase, tuning):
+    """The kernel the roofline names for a phase (the candidate search runs the
+    octant kernel when the tuned cell columns are at least twice the reach wide)."""
+    if phase == "candidates" and tuning and tuning.get("octant"):
+        return "k_candidates_oct"
+    return PHASE_KERNEL.get(phase, phase)
+
+
 def kernel_bytes(phase, N, st, na_before, nd_before):
     """Algorithmic bytes of one launch of the phase that dominates the step."""
-    if phase == "bead":
-        return 16 * N + 16 * N + N + 4 * N  # positions, slots, types, replica ids
+    if phase == "bead":  # positions, the eligibility bit, the bead's cell
+        return 16 * N + N // 8 + 4 * N
     if phase == "purge":  # every record read once; each hole takes one tail record (read + write)
         return 16 * (na_before + nd_before) + 2 * 16 * (st["angles_removed"] + st["dihedrals_removed"])
     if phase == "bond_forces":
@@ -454,9 +462,9 @@ def main():
     roof = None
     if kb is not None and ph[dom] > 0:
         ach = kb / (ph[dom] * 1e-3) / 1e9
-        roof = dict(bound="hbm", kernel=PHASE_KERNEL.get(dom, dom), achieved=ach, peak=peak, unit="GB/s",
+        roof = dict(bound="hbm", kernel=phase_kernel(dom, res["tuning"]), achieved=ach, peak=peak, unit="GB/s",
                     frac=ach / peak, peak_source=peak_kind, bytes_per_launch=kb, ms_per_launch=ph[dom],
-                    traffic=recorded_traffic(dom))
+                    traffic=recorded_traffic(dom, res["tuning"]))
     alg = algorithmic_bytes((res["na_before"], res["nd_before"]), res["stats"], res["N"], res["R"])
     step_gbs = alg / (res["ms"] * 1e-3) / 1e9
     rank, world, _ = dist_env()

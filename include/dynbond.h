@@ -305,6 +305,7 @@ typedef struct dynbond_tuning {
   float front_ms;   /* device time of the timed front at the chosen geometry */
   int32_t tuned;
   int32_t cell_zdiv; /* z edge = x / y edge / cell_zdiv */
+  int32_t octant;    /* 1: columns at least twice the reach wide, the search reads 2 x 2 columns */
 } dynbond_tuning;
 
 dynbond_status dynbond_autotune(dynbond_ctx* ctx, const int32_t* d_pos, dynbond_tuning* out);

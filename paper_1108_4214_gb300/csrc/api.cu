@@ -443,6 +443,7 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
   }
   c->tuning.cell_scale = scale;
   c->tuning.cell_zdiv = zdiv;
+  c->tuning.octant = octant ? 1 : 0;
   return DYNBOND_OK;
 }
 

@@ -71,7 +71,8 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("cell_scale", c_dbl), ("bead_blocks_per_sm", c_i32), ("candidate_blocks_per_sm", c_i32),
-                ("front_ms", ctypes.c_float), ("tuned", c_i32), ("cell_zdiv", c_i32)]
+                ("front_ms", ctypes.c_float), ("tuned", c_i32), ("cell_zdiv", c_i32),
+                ("octant", c_i32)]
 
 
 class DPD(ctypes.Structure):
