@@ -26,6 +26,7 @@ template <int N>
 struct IntC {
   static constexpr int value = N;
 };
+constexpr int FO_BATCH = 4;     // list entries examined together by first_open
 constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
 
 __device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
@@ -767,11 +768,23 @@ __device__ __forceinline__ int first_open(const Dev& d, int sys, int i, int& p, 
   const long long o = sys ? d.N : 0;
   const int len = sys ? d.brk_len[i] : d.cand_len[i];
   const int4* lst = sys ? d.brk + 4 * (long long)i : d.cand + d.cand_start[i];
-  for (; p < len; ++p) {
-    const int q = lst[p].x;
-    const long long m = __ldcg(d.mate + o + q);
-    if (m < 0 || (m >> 32) == round) return q;
+  // FO_BATCH list entries and then their partners' match states are loaded
+  // together, so skipping matched partners costs no extra dependent loads
+  for (; p < len; p += FO_BATCH) {
+    int q[FO_BATCH];
+    long long m[FO_BATCH];
+#pragma unroll
+    for (int u = 0; u < FO_BATCH; ++u) q[u] = p + u < len ? lst[p + u].x : -1;
+#pragma unroll
+    for (int u = 0; u < FO_BATCH; ++u) m[u] = q[u] >= 0 ? __ldcg(d.mate + o + q[u]) : 0;
+#pragma unroll
+    for (int u = 0; u < FO_BATCH; ++u)
+      if (q[u] >= 0 && (m[u] < 0 || (m[u] >> 32) == round)) {
+        p += u;
+        return q[u];
+      }
   }
+  p = len;
   return -1;
 }
 
