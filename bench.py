@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--cell-scale", type=int, default=0,
+                    help="fixed cell edge (x the creation reach) instead of autotuning, e.g. for profiler runs, "
+                         "under which the autotuner's timings mean nothing")
+    ap.add_argument("--cell-zdiv", type=int, default=1, help="z cells per x / y edge with --cell-scale")
     return ap.parse_args()
 
 
@@ -229,8 +233,9 @@ def run_gpu(args):
     snaps_np = s.snapshots(0, K + Wm)
     snaps = [torch.from_numpy(x).to(dev) for x in snaps_np]
     stream = torch.cuda.current_stream()
-    ctx = dynbond.Context(s, stream=stream)
-    tuning = ctx.autotune(snaps[0])
+    geo = dict(cell_scale=args.cell_scale, cell_zdiv=args.cell_zdiv) if args.cell_scale > 0 else None
+    ctx = dynbond.Context(s, stream=stream, params=geo)
+    tuning = ctx.tuning() if geo else ctx.autotune(snaps[0])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     force = torch.empty((N, 4), dtype=torch.float32, device=dev)
     ev = torch.empty((R, 7), dtype=torch.float64, device=dev)
@@ -263,8 +268,9 @@ def run_gpu(args):
     # per-phase device times from a second context that records events
     # between the phases (events inside the replayed work serialize the
     # kernels, so the headline above is timed without them)
-    ctx_p = dynbond.Context(s, flags=dynbond.FLAG_PROFILE, stream=stream)
-    ctx_p.autotune(snaps[0])
+    ctx_p = dynbond.Context(s, flags=dynbond.FLAG_PROFILE, stream=stream, params=geo)
+    if not geo:
+        ctx_p.autotune(snaps[0])
     for k in range(Wm + K):
         flush.zero_()
         ctx_p.step(snaps[k], k)
@@ -288,7 +294,7 @@ def run_gpu(args):
     pin_pos = torch.empty((N, 4), dtype=torch.int32).pin_memory()
     pin_f = torch.empty((N, 4), dtype=torch.float32).pin_memory()
     pin_ev = torch.empty((R, 7), dtype=torch.float64).pin_memory()
-    ctx_h = dynbond.Context(s, stream=stream)
+    ctx_h = dynbond.Context(s, stream=stream, params=geo)
     for k in range(min(Wm, 3)):
         pin_pos.copy_(torch.from_numpy(snaps_np[k]))
         ctx_h.run_host(pin_pos, k, pin_f, pin_ev)

@@ -310,6 +310,10 @@ typedef struct dynbond_tuning {
 
 dynbond_status dynbond_autotune(dynbond_ctx* ctx, const int32_t* d_pos, dynbond_tuning* out);
 
+/* The context's current launch geometry (tuned or fixed at creation) in *out
+ * (host).  EINVAL on NULL arguments.  Launches nothing. */
+dynbond_status dynbond_get_tuning(dynbond_ctx* ctx, dynbond_tuning* out);
+
 /* Wait for the context's stream and return any device-side error. */
 dynbond_status dynbond_sync(dynbond_ctx* ctx);
 

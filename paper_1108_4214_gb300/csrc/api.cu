@@ -954,6 +954,12 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
   return st;
 }
 
+dynbond_status dynbond_get_tuning(dynbond_ctx* c, dynbond_tuning* out) {
+  if (!c || !out) return DYNBOND_EINVAL;
+  *out = c->tuning;
+  return DYNBOND_OK;
+}
+
 dynbond_status dynbond_sync(dynbond_ctx* c) {
   if (!c) return DYNBOND_EINVAL;
   if (c->sticky) return c->sticky;

@@ -29,7 +29,7 @@ STAT_NAMES = [
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
            "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
            "dynbond_forces_noalloc", "dynbond_autotune", "dynbond_md_create", "dynbond_md_advance",
-           "dynbond_md_destroy", "dynbond_topology_hash"]
+           "dynbond_md_destroy", "dynbond_topology_hash", "dynbond_get_tuning"]
 NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
@@ -128,6 +128,8 @@ def load() -> ctypes.CDLL:
     L.dynbond_topology_hash.argtypes = [c_p, c_p]
     L.dynbond_autotune.restype = c_i32
     L.dynbond_autotune.argtypes = [c_p, c_p, c_p]
+    L.dynbond_get_tuning.restype = c_i32
+    L.dynbond_get_tuning.argtypes = [c_p, c_p]
     L.dynbond_forces_noalloc.restype = c_i32
     L.dynbond_forces_noalloc.argtypes = [c_p, c_p, c_p, c_p, c_i32, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_p, c_p, c_p]
     _lib = L
@@ -297,6 +299,12 @@ class Context:
         """dynbond_autotune on device positions; returns the chosen geometry."""
         t = Tuning()
         self._check(self.L.dynbond_autotune(self.h, c_p(_ptr(pos)), ctypes.byref(t)))
+        return {n: getattr(t, n) for n, _ in Tuning._fields_}
+
+    def tuning(self) -> Dict:
+        """dynbond_get_tuning: the current launch geometry (nothing is timed or launched)."""
+        t = Tuning()
+        self._check(self.L.dynbond_get_tuning(self.h, ctypes.byref(t)))
         return {n: getattr(t, n) for n, _ in Tuning._fields_}
 
     def topology_hash(self) -> np.ndarray:
