@@ -347,6 +347,11 @@ def test_autotuned_and_fixed_geometries_give_identical_results():
             assert np.array_equal(x, y)
     info = ctxs[0].autotune(torch.from_numpy(s.snapshot(4)).cuda())
     assert info["tuned"] == 1 and info["cell_scale"] in (1.0, 1.25, 1.5, 2.0, 3.0) and info["cell_zdiv"] in (1, 2, 4)
+    assert ctxs[0].tuning() == info
+    # a fixed geometry is reported as created: 2 x 2 columns of 2 reaches (L = 20 sigma: 7 per axis), 2 z cells per edge
+    fixed = D.Context(s, params=dict(cell_scale=2, cell_zdiv=2)).tuning()
+    assert fixed["tuned"] == 0 and fixed["cell_scale"] == 2.0 and fixed["cell_zdiv"] == 2 and fixed["octant"] == 1
+    assert ctxs[2].tuning()["octant"] == 1 and ctxs[1].tuning()["octant"] == 0
 
 
 def test_bounded_wait_gives_up_with_a_status_and_leaves_the_device_usable():
