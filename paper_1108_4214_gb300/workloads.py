@@ -366,6 +366,56 @@ def dna_system(name, n_strands, n_nt, density, seed, rules, n_duplex=0, box=None
     )
 
 
+def rules_dna2_ligation(p_form: float = 0.5, p_break: float = 0.05, p_lig: float = 0.5,
+                        lig_dist: float = 1.1) -> List[Dict]:
+    """The 2-bead rules plus directional ligation of backbone ends: two
+    backbone beads within lig_dist join by a directional backbone bond
+    (createdirbond, types 2 / 3) with probability p_lig.  A backbone bead
+    holds at most one bond of type 2 and one of type 3 (maxbond per stored
+    type), so only a strand's 3' end (which stores 3 toward its neighbour)
+    and a 5' end (which stores 2) can ligate, and the maxbond test picks the
+    orientation that continues the chain: the 3' end stores 2, the 5' end 3.
+    The new bond's backbone angles and stacking dihedrals follow from the
+    pattern table of rules_dna2."""
+    rules = rules_dna2(p_form=p_form, p_break=p_break)
+    head = rules[:5]
+    rest = rules[5:]
+    return head + [
+        dict(kind="maxbond", bonds=bit(BB3), beads=bit(BB), max=1),
+        dict(kind="maxbond", bonds=bit(BB5), beads=bit(BB), max=1),
+        dict(kind="createdirbond", btype=BB3, btype2=BB5, beads=(bit(BB), bit(BB)), dist=lig_dist, prob=p_lig),
+    ] + rest
+
+
+def dna2_nicked_system(n_strands: int = 64, n_nt: int = 16, n_duplex: int = 16, nick_every: int = 4,
+                       density: float = 0.5, seed: int = 7, p_lig: float = 0.5) -> "System":
+    """Nicked duplexes in the 2-bead model: the first 2 n_duplex strands form
+    complementary anti-parallel ladders (as in the melting workload), and the
+    second strand of each ladder is cut into pieces of nick_every nucleotides
+    by removing the backbone bonds between them; the ends at each nick sit
+    1 sigma apart along the ladder, within reach of the ligation rule
+    (rules_dna2_ligation).  The other strands are random walks."""
+    N = n_strands * 2 * n_nt
+    box = (N / density) ** (1.0 / 3.0)
+    rng = np.random.default_rng([seed, 71])
+    pos, types, bonds = _replica_strands(rng, n_strands, n_nt, box, 0, n_duplex)
+    nb = 2 * n_nt
+    cut = set()
+    for dpx in range(n_duplex):
+        first = (2 * dpx + 1) * nb
+        for m in range(nick_every - 1, n_nt - 1, nick_every):
+            cut.add((first + 2 * m, first + 2 * (m + 1)))
+    keep = np.array([(int(b[0]), int(b[1])) not in cut for b in bonds])
+    assert len(bonds) - keep.sum() == len(cut)
+    return System(
+        name=f"nicked-{N} ({n_duplex} duplexes nicked every {nick_every} nt)",
+        bead_offset=np.array([0, N], dtype=np.int64),
+        box_q=np.array([int(np.rint(box * QSCALE))], dtype=np.int64),
+        types=types, bonds=bonds[keep], rules=rules_dna2_ligation(p_lig=p_lig), pos0=pos, seed=seed,
+        params=default_params(seed),
+    )
+
+
 def default_params(seed):
     return dict(seed=int(seed) * 0x9E3779B97F4A7C15 % (1 << 64), paircheck13=0, paircheck14=0,
                 max_rounds=0, prob_mode=0, reactive_mask=ALL_BEADS)

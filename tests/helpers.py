@@ -112,3 +112,14 @@ def topology_hash(bonds, angles, dihedrals):
                      _chain(0xD, [d[:, k] for k in range(5)])):
             total = (total + int(part.sum(dtype=np.uint64))) & M64
     return total
+
+
+def half_bond_pair():
+    """Two beads 1.3 sigma apart on x joined by a directional bond whose two
+    stored types carry different potentials: bead 0 stores type 2 (K 100,
+    r0 1.0), bead 1 stores type 3 (K 40, r0 1.2)."""
+    rules = [dict(kind="createbond", btype=1, beads=(W.ALL_BEADS, W.ALL_BEADS), dist=0.5, prob=0.0)]
+    s = make_system([0, 0], [[0, 1, W.BB3, W.BB5]], [[2.0, 2.0, 2.0], [3.3, 2.0, 2.0]], 10.0, rules)
+    s.forcefield["bond_k"][W.BB3], s.forcefield["bond_r0"][W.BB3] = 100.0, 1.0
+    s.forcefield["bond_k"][W.BB5], s.forcefield["bond_r0"][W.BB5] = 40.0, 1.2
+    return s

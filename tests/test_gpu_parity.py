@@ -15,7 +15,7 @@ import pytest
 from oracle import oracle as O
 from paper_1108_4214_gb300 import workloads as W
 
-from helpers import golden, golden_rules, ladder_1bead_positions, make_system
+from helpers import golden, golden_rules, half_bond_pair, ladder_1bead_positions, make_system
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -152,6 +152,34 @@ def test_paper_exact_mode_oligomers_on_templates():
     ligated = int(((bonds[:, 2] == W.BB3) & (bonds[:, 3] == W.BB5)).sum()) - 64 * (16 - 1) - 64 * 4 * 3
     assert ligated > 0, "no ligation happened"
     print("ligated", ligated, "max force / ev error", max(w[0] for w in worst), max(w[1] for w in worst))
+
+
+def test_nicked_duplexes_ligate_like_the_oracle():
+    """Directional ligation of backbone ends in the 2-bead model: bit-exact
+    topology and statistics against the oracle while the nicks close."""
+    s = W.dna2_nicked_system()
+    o, _ = run_parity(s, 8)
+    bonds = o.topology()[0]
+    backbone = int(np.isin(bonds[:, 2], (W.BB3, W.BB5)).sum())
+    assert backbone > int(np.isin(s.bonds[:, 2], (W.BB3, W.BB5)).sum()), "no nick closed"
+
+
+def test_nicked_duplexes_16k_beads():
+    s = W.dna2_nicked_system(n_strands=512, n_duplex=128, nick_every=8, seed=8)
+    run_parity(s, 4)
+
+
+def test_half_bonds_net_force_matches_the_oracle():
+    """Unequal potentials on the two ends of a directional bond: the GPU's
+    per-end forces (and their nonzero sum) match the oracle's closed form."""
+    s = half_bond_pair()
+    o = O.Oracle(s)
+    ctx = dynbond().Context(s)
+    snap = s.snapshot(0)
+    compare_forces(ctx, o, snap, "half bonds")
+    f, _ = ctx.forces(torch.from_numpy(snap).cuda())
+    f = f.cpu().numpy()
+    assert abs(float(f[0, 0] + f[1, 0])) > 50.0
 
 
 def test_rounds_matching_and_single_nomination():

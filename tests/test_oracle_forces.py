@@ -8,7 +8,7 @@ import pytest
 from oracle import oracle as O
 from paper_1108_4214_gb300 import workloads as W
 
-from helpers import make_system
+from helpers import half_bond_pair, make_system
 
 
 def rot(rng):
@@ -161,3 +161,22 @@ def test_translation_invariance_through_the_box():
     from helpers import qpos
     f1, e1 = o.forces(qpos(s, pos + np.array([19.75, -33.125, 5.5])))  # wraps through the boundary
     assert np.allclose(f0, f1, atol=1e-6) and np.allclose(e0, e1, rtol=1e-9, atol=1e-6)
+
+
+def test_half_bonds_with_different_stored_types_give_a_net_force():
+    """Each end of a directional bond feels the full force of the type it
+    stores and books half the energy (Sec. 2): with unequal potentials the
+    pair feels a net force (the 'active matter' remark of Sec. 2), in closed
+    form (bead 1 on +x of bead 0, r the exact quantized distance)
+    F0 = +2 K2 (r - r02) x^, F1 = -2 K3 (r - r03) x^."""
+    s = half_bond_pair()
+    o = O.Oracle(s)
+    snap = s.snapshot(0)
+    f, ev = o.forces(snap)
+    r = (int(snap[1, 0]) - int(snap[0, 0])) / W.QSCALE
+    f0 = 2.0 * 100.0 * (r - 1.0)
+    f1 = -2.0 * 40.0 * (r - 1.2)
+    assert np.allclose(f[0], [f0, 0.0, 0.0], rtol=1e-12, atol=1e-12)
+    assert np.allclose(f[1], [f1, 0.0, 0.0], rtol=1e-12, atol=1e-12)
+    assert abs(f[0, 0] + f[1, 0]) > 50.0  # no third law across a directional bond with unequal halves
+    assert np.isclose(ev[0, 0], 0.5 * 100.0 * (r - 1.0) ** 2 + 0.5 * 40.0 * (r - 1.2) ** 2, rtol=1e-12)
