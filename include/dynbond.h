@@ -152,9 +152,14 @@ typedef struct dynbond_params {
  *   bond      E = bond_k (r - bond_r0)^2; each endpoint feels the force of the
  *             type IT stores and books half the energy (directional bonds,
  *             Sec. 2: equal potentials both ways conserve momentum);
- *   angle     E = angle_k (1 + cos theta), theta the angle at the centre bead;
+ *   angle     angle_style 0: E = angle_k (1 + cos theta), theta the angle at
+ *             the centre bead; angle_style 1: E = angle_k (theta -
+ *             angle_theta0)^2 (the DNA angles of Sec. 3, theta0 in radians),
+ *             its forces dividing by sin theta clamped below at 1e-3 (so a
+ *             straight angle with theta0 below 180 degrees stays finite);
  *   dihedral  E = dihedral_k (1 + dihedral_d cos phi) (the form of Sec. 3),
  *             phi = 180 degrees for the trans conformation.
+ * An angle_style other than 0 or 1 is EINVAL.
  */
 typedef struct dynbond_forcefield {
   double bond_k[DYNBOND_MAX_TYPES];
@@ -162,6 +167,8 @@ typedef struct dynbond_forcefield {
   double angle_k[DYNBOND_MAX_TYPES];
   double dihedral_k[DYNBOND_MAX_TYPES];
   int32_t dihedral_d[DYNBOND_MAX_TYPES];
+  double angle_theta0[DYNBOND_MAX_TYPES];
+  int32_t angle_style[DYNBOND_MAX_TYPES];
 } dynbond_forcefield;
 
 /*

@@ -687,6 +687,29 @@ void angle_cos(const double ra[3], const double rc[3], double K, double* E, doub
   *E = K * (1.0 + cs);
 }
 
+// Harmonic angle E = K (theta - theta0)^2 (the DNA angles of Sec. 3) with
+// ra = r_A - r_B, rc = r_C - r_B.  F_A = -dE/dr_A = -2K (theta - theta0)
+// dtheta/dr_A, and dtheta/dr_A = -(1 / sin theta) dcos/dr_A; sin theta is
+// clamped below at 1e-3 (a straight angle with theta0 < pi would otherwise
+// have an unbounded force).
+void angle_harmonic(const double ra[3], const double rc[3], double K, double theta0, double* E, double Fa[3],
+                    double Fc[3]) {
+  double la = std::sqrt(dot(ra, ra)), lc = std::sqrt(dot(rc, rc));
+  double cs = dot(ra, rc) / (la * lc);
+  double x[3] = {ra[1] * rc[2] - ra[2] * rc[1], ra[2] * rc[0] - ra[0] * rc[2], ra[0] * rc[1] - ra[1] * rc[0]};
+  double cr = std::sqrt(dot(x, x));
+  double theta = std::atan2(cr, dot(ra, rc));  // the angle at B, accurate near 0 and pi
+  double sn = std::max(cr / (la * lc), 1e-3);
+  double dEdth = 2.0 * K * (theta - theta0);
+  for (int k = 0; k < 3; ++k) {
+    double ga = rc[k] / (la * lc) - cs * ra[k] / (la * la);  // dcos/dr_A
+    double gc = ra[k] / (la * lc) - cs * rc[k] / (lc * lc);  // dcos/dr_C
+    Fa[k] = dEdth / sn * ga;
+    Fc[k] = dEdth / sn * gc;
+  }
+  *E = K * (theta - theta0) * (theta - theta0);
+}
+
 // Dihedral E = K (1 + d cos phi), b1 = r_B - r_A, b2 = r_C - r_B, b3 = r_D - r_C,
 // cos phi = m.n / (|m||n|) with m = b1 x b2, n = b2 x b3 (trans = 180 deg).
 // The gradient is taken of cos phi through m and n directly.
@@ -861,7 +884,8 @@ uint64_t orc_threshold(double p) { return threshold_of(p); }
 // force[N*3], ev[R*7] = (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz) per replica with
 // W_ab = sum over interactions of (r_role - r_ref)_a F_role,b.
 int orc_forces(void* h, const int32_t* pos, const double* bond_k, const double* bond_r0, const double* angle_k,
-               const double* dih_k, const int32_t* dih_d, double* force, double* ev) {
+               const double* dih_k, const int32_t* dih_d, const double* angle_theta0, const int32_t* angle_style,
+               double* force, double* ev) {
   Oracle* o = static_cast<Oracle*>(h);
   o->pos = pos;
   std::memset(force, 0, sizeof(double) * 3 * o->N);
@@ -883,7 +907,8 @@ int orc_forces(void* h, const int32_t* pos, const double* bond_k, const double* 
     double ra[3], rc[3], Fa[3], Fc[3], E;
     o->rel(a[0], a[1], ra);
     o->rel(a[2], a[1], rc);
-    angle_cos(ra, rc, angle_k[a[3]], &E, Fa, Fc);
+    if (angle_style[a[3]] == 1) angle_harmonic(ra, rc, angle_k[a[3]], angle_theta0[a[3]], &E, Fa, Fc);
+    else angle_cos(ra, rc, angle_k[a[3]], &E, Fa, Fc);
     double* e = ev + 7 * o->rep[a[1]];
     e[0] += E;
     add_virial(e, ra, Fa, 1.0);
@@ -925,6 +950,10 @@ int orc_forces(void* h, const int32_t* pos, const double* bond_k, const double* 
 void orc_bond_half(const double* rij, double K, double r0, double* E, double* F) { bond_half(rij, K, r0, E, F); }
 void orc_angle(const double* ra, const double* rc, double K, double* E, double* Fa, double* Fc) {
   angle_cos(ra, rc, K, E, Fa, Fc);
+}
+void orc_angle_harmonic(const double* ra, const double* rc, double K, double theta0, double* E, double* Fa,
+                        double* Fc) {
+  angle_harmonic(ra, rc, K, theta0, E, Fa, Fc);
 }
 void orc_dihedral(const double* b1, const double* b2, const double* b3, double K, double d, double* E, double* Fa,
                   double* Fb, double* Fc, double* Fd) {

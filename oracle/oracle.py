@@ -76,9 +76,10 @@ def lib():
         L.orc_threshold.restype = ctypes.c_uint64
         L.orc_threshold.argtypes = [ctypes.c_double]
         L.orc_forces.restype = ctypes.c_int
-        L.orc_forces.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.orc_forces.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
         L.orc_bond_half.argtypes = [P, ctypes.c_double, ctypes.c_double, P, P]
         L.orc_angle.argtypes = [P, P, ctypes.c_double, P, P, P]
+        L.orc_angle_harmonic.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P]
         L.orc_dihedral.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
         assert L.orc_stat_count() == len(STAT_NAMES)
         _lib = L
@@ -198,7 +199,9 @@ class Oracle:
         ev = np.zeros((self.R, 7), np.float64)
         arrs = [np.ascontiguousarray(ff[k], np.float64) for k in ("bond_k", "bond_r0", "angle_k", "dihedral_k")]
         dd = np.ascontiguousarray(ff["dihedral_d"], np.int32)
-        lib().orc_forces(self.h, _p(pos), *[_p(a) for a in arrs], _p(dd), _p(f), _p(ev))
+        t0 = np.ascontiguousarray(ff.get("angle_theta0", np.zeros(16)), np.float64)
+        sty = np.ascontiguousarray(ff.get("angle_style", np.zeros(16)), np.int32)
+        lib().orc_forces(self.h, _p(pos), *[_p(a) for a in arrs], _p(dd), _p(t0), _p(sty), _p(f), _p(ev))
         return f, ev
 
 
@@ -233,6 +236,15 @@ def bond_half(rij, K, r0):
     F = np.zeros(3)
     lib().orc_bond_half(_p(rij), K, r0, _p(E), _p(F))
     return E[0], F
+
+
+def angle_harmonic(ra, rc, K, theta0):
+    ra = np.ascontiguousarray(ra, np.float64)
+    rc = np.ascontiguousarray(rc, np.float64)
+    E = np.zeros(1)
+    Fa, Fc = np.zeros(3), np.zeros(3)
+    lib().orc_angle_harmonic(_p(ra), _p(rc), K, theta0, _p(E), _p(Fa), _p(Fc))
+    return E[0], Fa, Fc
 
 
 def angle(ra, rc, K):

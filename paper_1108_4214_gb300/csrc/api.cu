@@ -578,13 +578,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     ((unsigned*)&slots[j])[deg[j]++] = ((unsigned)i << 4) | (unsigned)tj;
     nb_rep[rep[i]] += 1;
   }
-  for (int t = 0; t < 16; ++t) {
-    c->ff.bond_k[t] = (float)ff->bond_k[t];
-    c->ff.bond_r0[t] = (float)ff->bond_r0[t];
-    c->ff.angle_k[t] = (float)ff->angle_k[t];
-    c->ff.dih_k[t] = (float)ff->dihedral_k[t];
-    c->ff.dih_d[t] = (float)ff->dihedral_d[t];
-  }
+  if (!make_ff(*ff, c->ff)) return fail(c, DYNBOND_EINVAL, "angle_style must be 0 (cosine) or 1 (harmonic)");
 
   // ---- device
   CUDA_TRY(c, cudaGetDevice(&c->device));

@@ -3,7 +3,8 @@
 // block reductions of the energy and the virial per replica.
 //   bonds     each bead sums the harmonic force of the type IT stores for
 //             each of its bonds (directional bonds, Sec. 2) -- no atomics;
-//   angles    E = K (1 + cos theta), forces added with float4 atomics;
+//   angles    E = K (1 + cos theta) or K (theta - theta0)^2 (per type),
+//             forces added with 16-byte reductions;
 //   dihedrals E = K (1 + d cos phi) (Sec. 3), forces from the
 //             Blondel-Karplus (J. Comput. Chem. 17, 1132 (1996)) derivatives
 //             of phi, free of the sin(phi) = 0 singularity.
@@ -257,22 +258,24 @@ __device__ __forceinline__ void add_force(float4* f, int i, float3 v) {
   red_add_f4(f, i, v.x, v.y, v.z);
 }
 
-// One angle: E = K (1 + cos theta) with r_A - r_B and r_C - r_B.
+// One angle (cosine or harmonic in theta, see angle_coef) with r_A - r_B and
+// r_C - r_B.
 __device__ __forceinline__ void angle_term(float4* force, const int4& a, const int4& pa, const int4& pb,
                                            const int4& pc, int L, const FF& ff, float& e, float* w) {
   float3 ra = relq(pa, pb, L), rc = relq(pc, pb, L);
-  float K = ff.angle_k[a.w];
   float ia = rsqrtf(dot3(ra, ra)), ic = rsqrtf(dot3(rc, rc));
   float inv = ia * ic;
   float cs = dot3(ra, rc) * inv;
-  // F_A = -K d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
-  float3 Fa = scale(-K, axpy(-cs * ia * ia, ra, scale(inv, rc)));
-  float3 Fc = scale(-K, axpy(-cs * ic * ic, rc, scale(inv, ra)));
+  float Ea;
+  const float cf = angle_coef(ff, a.w, pa, pb, pc, L, cs, inv, &Ea);
+  // F_A = c d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
+  float3 Fa = scale(cf, axpy(-cs * ia * ia, ra, scale(inv, rc)));
+  float3 Fc = scale(cf, axpy(-cs * ic * ic, rc, scale(inv, ra)));
   float3 Fb = make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z);
   add_force(force, a.x, Fa);
   add_force(force, a.y, Fb);
   add_force(force, a.z, Fc);
-  e += K * (1.0f + cs);
+  e += Ea;
   w[0] += ra.x * Fa.x + rc.x * Fc.x;
   w[1] += ra.y * Fa.y + rc.y * Fc.y;
   w[2] += ra.z * Fa.z + rc.z * Fc.z;

@@ -27,7 +27,51 @@ constexpr int EV_COPIES = 32;      // striped copies of each replica's energy / 
 // bonded force-field tables in FP32 (kernel parameter space)
 struct FF {
   float bond_k[16], bond_r0[16], angle_k[16], dih_k[16], dih_d[16];
+  float angle_pt0[16];  // pi - theta0 of the harmonic angle types
+  unsigned angle_harm;  // bit t: angle type t is harmonic in theta
 };
+
+// Device copy of a force field (FP32 parameters); false for an unknown angle style.
+inline bool make_ff(const dynbond_forcefield& in, FF& out) {
+  out = FF{};
+  for (int t = 0; t < 16; ++t) {
+    out.bond_k[t] = (float)in.bond_k[t];
+    out.bond_r0[t] = (float)in.bond_r0[t];
+    out.angle_k[t] = (float)in.angle_k[t];
+    out.dih_k[t] = (float)in.dihedral_k[t];
+    out.dih_d[t] = (float)in.dihedral_d[t];
+    out.angle_pt0[t] = (float)(3.14159265358979323846 - in.angle_theta0[t]);
+    if (in.angle_style[t] != 0 && in.angle_style[t] != 1) return false;
+    if (in.angle_style[t] == 1) out.angle_harm |= 1u << t;
+  }
+  return true;
+}
+
+// Coefficient c and energy of an angle term of type t (centre bead B, ends A
+// and C; cos theta = cs, inv = 1 / (|r_A - r_B| |r_C - r_B|) in sigma^-2):
+// F_A = c dcos/dr_A, F_C = c dcos/dr_C.  Cosine: E = K (1 + cos), c = -K.
+// Harmonic: E = K (theta - theta0)^2, c = 2 K (theta - theta0) / sin theta
+// (d theta / d cos = -1 / sin), sin clamped below at 1e-3.  For the harmonic
+// form pi - theta = atan2(|u x v|, -u.v) is taken from the exact integer
+// cross and dot products of the displacements u, v, so nearly straight
+// angles keep FP32 relative accuracy.
+__device__ __forceinline__ float angle_coef(const FF& ff, int t, const int4& pa, const int4& pb, const int4& pc, int L,
+                                            float cs, float inv, float* E) {
+  const float K = ff.angle_k[t];
+  if (!((ff.angle_harm >> t) & 1u)) {
+    *E = K * (1.0f + cs);
+    return -K;
+  }
+  const long long ux = wrap_dx(pa.x - pb.x, L), uy = wrap_dx(pa.y - pb.y, L), uz = wrap_dx(pa.z - pb.z, L);
+  const long long vx = wrap_dx(pc.x - pb.x, L), vy = wrap_dx(pc.y - pb.y, L), vz = wrap_dx(pc.z - pb.z, L);
+  const float cx = (float)(uy * vz - uz * vy), cy = (float)(uz * vx - ux * vz), cz = (float)(ux * vy - uy * vx);
+  const float sr = sqrtf(cx * cx + cy * cy + cz * cz);          // |u x v|, units^2
+  const float pth = atan2f(sr, -(float)(ux * vx + uy * vy + uz * vz));  // pi - theta
+  const float dth = ff.angle_pt0[t] - pth;                         // theta - theta0
+  const float s = fmaxf(sr * (1.0f / 1099511627776.0f) * inv, 1e-3f);  // sin theta (units^2 -> sigma^2)
+  *E = K * dth * dth;
+  return 2.0f * K * dth / s;
+}
 
 __global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_bead_flags(Dev d, const RuleTab* __restrict__ rtp);

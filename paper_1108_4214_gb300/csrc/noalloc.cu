@@ -141,18 +141,19 @@ __global__ void na_angles_dihedrals(const int4* __restrict__ pos, const long lon
       int L = (int)box[r];
       int4 pb = pos[b];
       float3 ra = na_rel(pos[a], pb, L), rc = na_rel(pos[c], pb, L);
-      float K = ff.angle_k[t];
       float la2 = na_dot(ra, ra), lc2 = na_dot(rc, rc);
       float inv = rsqrtf(la2 * lc2);
       float cs = na_dot(ra, rc) * inv;
-      float3 Fa = make_float3(-K * (rc.x * inv - cs * ra.x / la2), -K * (rc.y * inv - cs * ra.y / la2),
-                              -K * (rc.z * inv - cs * ra.z / la2));
-      float3 Fc = make_float3(-K * (ra.x * inv - cs * rc.x / lc2), -K * (ra.y * inv - cs * rc.y / lc2),
-                              -K * (ra.z * inv - cs * rc.z / lc2));
+      float Ea;
+      const float cf = angle_coef(ff, t, pos[a], pb, pos[c], L, cs, inv, &Ea);
+      float3 Fa = make_float3(cf * (rc.x * inv - cs * ra.x / la2), cf * (rc.y * inv - cs * ra.y / la2),
+                              cf * (rc.z * inv - cs * ra.z / la2));
+      float3 Fc = make_float3(cf * (ra.x * inv - cs * rc.x / lc2), cf * (ra.y * inv - cs * rc.y / lc2),
+                              cf * (ra.z * inv - cs * rc.z / lc2));
       na_add(force, a, Fa);
       na_add(force, b, make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z));
       na_add(force, c, Fc);
-      acc.e[0] += (double)(K * (1.0f + cs));
+      acc.e[0] += (double)Ea;
       acc.vir(ra, Fa, 1.f);
       acc.vir(rc, Fc, 1.f);
     } else {
@@ -260,13 +261,7 @@ extern "C" dynbond_status dynbond_forces_noalloc(const int32_t* d_pos, const uin
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return DYNBOND_ECUDA;
   FF f;
-  for (int t = 0; t < 16; ++t) {
-    f.bond_k[t] = (float)ff->bond_k[t];
-    f.bond_r0[t] = (float)ff->bond_r0[t];
-    f.angle_k[t] = (float)ff->angle_k[t];
-    f.dih_k[t] = (float)ff->dihedral_k[t];
-    f.dih_d[t] = (float)ff->dihedral_d[t];
-  }
+  if (!make_ff(*ff, f)) return DYNBOND_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int nev = 7 * n_replicas;
   na_clear<<<(nev + 255) / 256, 256, 0, s>>>(scratch, nev);

@@ -56,7 +56,8 @@ class Params(ctypes.Structure):
 
 class ForceField(ctypes.Structure):
     _fields_ = [("bond_k", c_dbl * 16), ("bond_r0", c_dbl * 16), ("angle_k", c_dbl * 16),
-                ("dihedral_k", c_dbl * 16), ("dihedral_d", c_i32 * 16)]
+                ("dihedral_k", c_dbl * 16), ("dihedral_d", c_i32 * 16), ("angle_theta0", c_dbl * 16),
+                ("angle_style", c_i32 * 16)]
 
 
 class SystemDesc(ctypes.Structure):
@@ -228,12 +229,7 @@ class Context:
         p.cell_scale = int(prm.get("cell_scale", 0))
         p.cell_zdiv = int(prm.get("cell_zdiv", 0))
         p.spin_limit = int(prm.get("spin_limit", 0))
-        ff = ForceField()
-        f = system.forcefield
-        for t in range(16):
-            ff.bond_k[t], ff.bond_r0[t] = float(f["bond_k"][t]), float(f["bond_r0"][t])
-            ff.angle_k[t], ff.dihedral_k[t] = float(f["angle_k"][t]), float(f["dihedral_k"][t])
-            ff.dihedral_d[t] = int(f["dihedral_d"][t])
+        ff = forcefield_struct(system.forcefield)
         rules = pack_rules(system.rules)
         h = c_p()
         st = self.L.dynbond_create(ctypes.byref(p), rules, len(system.rules), ctypes.byref(sd), ctypes.byref(ff),
@@ -334,10 +330,13 @@ class Context:
 
 def forcefield_struct(f) -> ForceField:
     ff = ForceField()
+    t0 = f.get("angle_theta0", np.zeros(16))
+    sty = f.get("angle_style", np.zeros(16, np.int32))
     for t in range(16):
         ff.bond_k[t], ff.bond_r0[t] = float(f["bond_k"][t]), float(f["bond_r0"][t])
         ff.angle_k[t], ff.dihedral_k[t] = float(f["angle_k"][t]), float(f["dihedral_k"][t])
         ff.dihedral_d[t] = int(f["dihedral_d"][t])
+        ff.angle_theta0[t], ff.angle_style[t] = float(t0[t]), int(sty[t])
     return ff
 
 

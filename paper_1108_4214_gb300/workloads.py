@@ -166,20 +166,33 @@ def dna1_oligo_system(n_motifs: int = 64, template_nt: int = 16, oligo_nt: int =
             kk = np.arange(oligo_nt - 1)
             bonds.append(np.stack([first + kk, first + kk + 1, np.full(oligo_nt - 1, BB3),
                                    np.full(oligo_nt - 1, BB5)], axis=1))
-    ff = forcefield_dna2()
-    for t_ in (HYB, BB3, BB5):
-        ff["bond_r0"][t_] = 0.6
-    ff["angle_k"][:4] = 2.0
-    ff["dihedral_k"][:4] = 1.0
-    ff["dihedral_d"][:4] = 1
     return System(
         name=f"dna1-oligo-{N}", bead_offset=np.array([0, N], np.int64),
         box_q=np.array([int(np.rint(box * QSCALE))], np.int64), types=types,
         bonds=np.concatenate(bonds).astype(np.int32), rules=rules_dna1_paper(), pos0=pos, seed=seed,
         sigma_perturb=0.05,
         params=dict(default_params(seed), paircheck14=1, max_rounds=1, prob_mode=1),
-        forcefield=ff,
+        forcefield=forcefield_dna1_paper(),
     )
+
+
+def forcefield_dna1_paper() -> Dict[str, np.ndarray]:
+    """Bonded parameters of the paper's 1-bead DNA model (Sec. 3): harmonic
+    angles E = K (theta - theta0)^2, type 1 (along the backbone) K = 20,
+    theta0 = 180 degrees, type 2 (backbone - hybridization) K = 1, theta0 =
+    90 degrees; dihedrals E = K (1 + d cos phi) with K = 1, d = -1 (cis) for
+    types 1 and 2 and d = +1 (trans) for type 3.  The paper's bond wells are
+    garbled as printed; bonds here are harmonic, K = 100, r0 = 0.6 sigma
+    (the spacing of the oligomer geometry)."""
+    ff = forcefield_dna2()
+    for t in (HYB, BB3, BB5):
+        ff["bond_k"][t], ff["bond_r0"][t] = 100.0, 0.6
+    ff["angle_style"][1:3] = 1
+    ff["angle_k"][1], ff["angle_theta0"][1] = 20.0, np.pi
+    ff["angle_k"][2], ff["angle_theta0"][2] = 1.0, np.pi / 2
+    for t, dd in ((1, -1), (2, -1), (3, 1)):
+        ff["dihedral_k"][t], ff["dihedral_d"][t] = 1.0, dd
+    return ff
 
 
 def forcefield_dna2() -> Dict[str, np.ndarray]:
@@ -190,6 +203,7 @@ def forcefield_dna2() -> Dict[str, np.ndarray]:
     ff = dict(
         bond_k=np.zeros(16), bond_r0=np.zeros(16), angle_k=np.zeros(16),
         dihedral_k=np.zeros(16), dihedral_d=np.zeros(16, dtype=np.int32),
+        angle_theta0=np.zeros(16), angle_style=np.zeros(16, dtype=np.int32),
     )
     for t in (HYB, BB3, BB5, SUGAR):
         ff["bond_k"][t] = 100.0

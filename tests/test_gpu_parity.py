@@ -182,6 +182,15 @@ def test_half_bonds_net_force_matches_the_oracle():
     assert abs(float(f[0, 0] + f[1, 0])) > 50.0
 
 
+def test_unknown_angle_style_is_rejected():
+    s = W.config1()
+    s.forcefield = W.forcefield_dna1_paper()
+    s.forcefield["angle_style"][3] = 2
+    with pytest.raises(dynbond().DynbondError) as e:
+        dynbond().Context(s)
+    assert e.value.status == 1 and "angle_style" in str(e.value)
+
+
 def test_rounds_matching_and_single_nomination():
     pos2 = [[2.0, 2, 2], [2.0, 3.0, 2], [2.5, 2, 2], [2.95, 2.6, 2]]
     rules = [dict(kind="createbond", btype=1, beads=(W.bit(1), W.bit(2)), dist=1.1, prob=1.0),

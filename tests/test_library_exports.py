@@ -50,7 +50,10 @@ def test_binding_matches_header(lib_path):
     assert ctypes.sizeof(dynbond.Rule) == 64
     assert ctypes.sizeof(dynbond.Params) == 64
     assert ctypes.sizeof(dynbond.SystemDesc) == 72
-    assert ctypes.sizeof(dynbond.ForceField) == 4 * 16 * 8 + 16 * 4
+    # bond_k, bond_r0, angle_k, dihedral_k, angle_theta0 (double); dihedral_d, angle_style (int32)
+    assert ctypes.sizeof(dynbond.ForceField) == 5 * 16 * 8 + 2 * 16 * 4
+    # cell_scale (double); bead / candidate blocks, front_ms, tuned, cell_zdiv, octant (4 bytes each)
+    assert ctypes.sizeof(dynbond.Tuning) == 8 + 6 * 4
 
 
 def test_create_rejects_bad_input_without_touching_the_device(lib_path):

@@ -34,6 +34,25 @@ def test_closed_forms():
     assert O.dihedral([0, -1, 0], [1, 0, 0], [0, 0, 1], 1.5, 1.0)[0] == pytest.approx(1.5)
 
 
+def test_harmonic_angle_closed_forms():
+    """E = K (theta - theta0)^2 (Sec. 3): zero at theta0; otherwise the end
+    forces are tangential with magnitude 2 K |theta - theta0| / |r_end|."""
+    E, Fa, Fc = O.angle_harmonic([1, 0, 0], [0, 2, 0], 1.0, np.pi / 2)  # right angle, theta0 = 90 deg
+    assert E == pytest.approx(0.0, abs=1e-15) and np.allclose(Fa, 0) and np.allclose(Fc, 0)
+    E, Fa, Fc = O.angle_harmonic([1, 0, 0], [-3, 0, 0], 20.0, np.pi)  # straight, theta0 = 180 deg
+    assert E == pytest.approx(0.0, abs=1e-15) and np.allclose(Fa, 0) and np.allclose(Fc, 0)
+    th = np.deg2rad(120.0)
+    ra, rc = np.array([2.0, 0, 0]), 0.5 * np.array([np.cos(th), np.sin(th), 0])
+    for K, th0 in ((20.0, np.pi), (1.0, np.pi / 2)):
+        E, Fa, Fc = O.angle_harmonic(ra, rc, K, th0)
+        assert E == pytest.approx(K * (th - th0) ** 2, rel=1e-12)
+        assert np.linalg.norm(Fa) == pytest.approx(2 * K * abs(th - th0) / 2.0, rel=1e-12)
+        assert np.linalg.norm(Fc) == pytest.approx(2 * K * abs(th - th0) / 0.5, rel=1e-12)
+        assert abs(Fa @ ra) < 1e-12 and abs(Fc @ rc) < 1e-12
+        # opening the angle toward theta0 lowers the energy: F_A points away from C's side when theta < theta0
+        assert (np.cross(ra, Fa)[2] < 0) == (th < th0)
+
+
 def _fd(fun, x, h=1e-6):
     g = np.zeros_like(x)
     for i in range(x.size):
@@ -62,6 +81,14 @@ def test_finite_differences_and_newton3(seed):
     g = _fd(Eang, P.ravel()).reshape(3, 3)
     Fb = -(Fa + Fc)
     assert np.allclose(np.stack([Fa, Fb, Fc]), -g, rtol=1e-6, atol=1e-7)
+    # harmonic angle (random configurations stay far from the straight-angle clamp)
+
+    def Eharm(x):
+        x = x.reshape(3, 3)
+        return O.angle_harmonic(x[0] - x[1], x[2] - x[1], 1.7, 1.9)[0]
+    E, Fa, Fc = O.angle_harmonic(P[0] - P[1], P[2] - P[1], 1.7, 1.9)
+    g = _fd(Eharm, P.ravel()).reshape(3, 3)
+    assert np.allclose(np.stack([Fa, -(Fa + Fc), Fc]), -g, rtol=1e-6, atol=1e-6)
     # dihedral
     Q = rng.normal(size=(4, 3))
 
@@ -110,9 +137,12 @@ def _molecule(seed, box=40.0):
     return s, pos
 
 
-@pytest.mark.parametrize("seed", range(6))
-def test_system_forces_are_minus_energy_gradient(seed):
+@pytest.mark.parametrize("seed,harmonic", [(k, k % 2 == 1) for k in range(6)])
+def test_system_forces_are_minus_energy_gradient(seed, harmonic):
     s, pos = _molecule(seed)
+    if harmonic:  # the DNA angles of Sec. 3: K (theta - theta0)^2
+        s.forcefield["angle_style"] = np.ones(16, np.int32)
+        s.forcefield["angle_theta0"] = np.full(16, 1.9)
     o = O.Oracle(s)
     _, a, d = o.topology()
     assert len(a) > 5 and len(d) > 3

@@ -33,9 +33,12 @@ def slots_from_bonds(bonds, n):
     return slots
 
 
-def test_noalloc_forces_match_the_context_path_on_two_calls():
+@pytest.mark.parametrize("paper_ff", [False, True])
+def test_noalloc_forces_match_the_context_path_on_two_calls(paper_ff):
     from paper_1108_4214_gb300 import dynbond as D
     s = W.config3(n_replicas=6)  # several replicas: per-replica scratch rows
+    if paper_ff:  # harmonic angles K (theta - theta0)^2 with theta0 = 180 and 90 degrees (Sec. 3)
+        s.forcefield = W.forcefield_dna1_paper()
     ctx = D.Context(s)
     snaps = s.snapshots(0, 3)
     for k in range(2):
