@@ -208,9 +208,10 @@ def kernel_bytes(phase, N, st, na_before, nd_before):
         return 16 * N + 16 * N + 16 * N  # positions, slots, forces
     if phase == "angle_dihedral_forces":  # records + one force read-modify-write per role
         return 16 * (st["n_angles"] + st["n_dihedrals"]) + 2 * 16 * (3 * st["n_angles"] + 4 * st["n_dihedrals"])
-    if phase == "candidates":
+    if phase == "candidates":  # per reactive bead (N / 2 bases, an upper bound on the binned ones): its
+        # sorted entry and its slots (16 B each); per candidate pair: one 16-B list entry at each end
         return 16 * N // 2 + 16 * N // 2 + 16 * 2 * st["candidates"]
-    if phase == "cells":
+    if phase == "cells":  # per reactive bead: position read and sorted entry written (16 B each); the cell of every bead
         return 16 * N // 2 * 2 + 8 * N
     return None
 

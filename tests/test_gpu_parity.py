@@ -191,6 +191,21 @@ def test_unknown_angle_style_is_rejected():
     assert e.value.status == 1 and "angle_style" in str(e.value)
 
 
+def test_degenerate_systems_without_candidates_or_interactions():
+    """Nothing to bin or record: beads whose types no creation rule pairs
+    (empty cell lists, no candidates, no bonds, no angle or dihedral tiles in
+    the force launches: zero forces and energies), and one bond without typing
+    rules (bond forces only)."""
+    rules = [dict(kind="createbond", btype=1, beads=(W.bit(1), W.bit(2)), dist=1.1, prob=1.0)]
+    s = make_system([3, 3, 4, 4], [], [[1, 1, 1], [1.5, 1, 1], [1, 1.5, 1], [1.2, 1.2, 1.2]], 10.0, rules)
+    o, _ = run_parity(s, 2, forces=False)
+    f, ev = dynbond().Context(s).forces(torch.from_numpy(s.snapshot(0)).cuda())
+    assert not f.any() and not ev.any()
+    s2 = make_system([1, 2], [[0, 1, 1, 1]], [[1, 1, 1], [2.2, 1, 1]], 10.0, rules)
+    o2, _ = run_parity(s2, 2)
+    assert len(o2.topology()[1]) == 0 and len(o2.topology()[2]) == 0
+
+
 def test_rounds_matching_and_single_nomination():
     pos2 = [[2.0, 2, 2], [2.0, 3.0, 2], [2.5, 2, 2], [2.95, 2.6, 2]]
     rules = [dict(kind="createbond", btype=1, beads=(W.bit(1), W.bit(2)), dist=1.1, prob=1.0),
