@@ -1,12 +1,18 @@
 // Kernels of one dynamic-bonding call (Svaneborg, arXiv:1108.4214, Appendix
 // steps 1-10), in launch order:
-//   k_bead        per bead: creation eligibility and cell histogram; breakage
-//                 nomination lists and killbond marks (steps 2-3, 5)
+//   k_setup       zero the per-call scratch and cell counts
+//   k_bead        per bead: bounds check, cell histogram of the beads whose
+//                 eligibility bit is set (step 2)
 //   k_scan_cells  exclusive scan of the cell histogram (single pass)
-//   k_scatter     counting-sort scatter of eligible beads into cell order
-//   k_candidates  per eligible bead: every creation partner in the 27
-//                 neighbouring cells, last-rule-wins typing, graph-distance
-//                 exclusion, maxbond (step 2); sorted per-bead lists
+//   k_scatter     counting-sort scatter of eligible beads into cell order;
+//                 beside it, breakage nomination lists and killbond marks of
+//                 the beads holding breakable bonds (steps 3, 5)
+//   k_candidates(_oct)  per eligible bead: every creation partner in the
+//                 neighbouring cell columns (an octant of them when columns
+//                 are twice the reach wide) within the z reach interval,
+//                 last-rule-wins typing, graph-distance exclusion, maxbond
+//                 (step 2); sorted per-bead lists (k_cand_overflow finishes
+//                 beads with more than MAXC candidates)
 //   k_match       rounds of mutual nomination for creation and breakage at
 //                 once (step 4), cooperative launch with a bounded barrier
 //   k_edit        trials, kill / break / convert / form applied to each
