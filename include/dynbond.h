@@ -155,8 +155,10 @@ typedef struct dynbond_params {
  *   angle     angle_style 0: E = angle_k (1 + cos theta), theta the angle at
  *             the centre bead; angle_style 1: E = angle_k (theta -
  *             angle_theta0)^2 (the DNA angles of Sec. 3, theta0 in radians),
- *             its forces dividing by sin theta clamped below at 1e-3 (so a
- *             straight angle with theta0 below 180 degrees stays finite);
+ *             its forces taken through the unit normal of the plane of the
+ *             three beads, exact up to rounding at every angle; exactly
+ *             collinear beads (no plane) get no angle force, which is the
+ *             exact force when theta0 is 180 degrees;
  *   dihedral  E = dihedral_k (1 + dihedral_d cos phi) (the form of Sec. 3),
  *             phi = 180 degrees for the trans conformation.
  * An angle_style other than 0 or 1 is EINVAL.
@@ -262,10 +264,19 @@ dynbond_status dynbond_create(const dynbond_params* params, const dynbond_rule* 
 dynbond_status dynbond_step(dynbond_ctx* ctx, const int32_t* d_pos, uint64_t step, dynbond_stats* h_stats);
 
 /*
- * Bonded forces of the current topology at d_pos: d_force (device float4[N],
- * overwritten; w = 0) in FP32 (d_pos and d_force 16-byte aligned, else EINVAL); d_ev (device double[R*7], overwritten) per
- * replica (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz) with W_ab = sum over interactions
- * of (r_role - r_ref)_a F_role,b, reduced in FP64.
+ * Bonded forces of the current topology at d_pos (device int4[N], read only).
+ * The topology is the state the last dynbond_step left (Appendix steps 7 and
+ * 9: the bonds with the type each end stores, and the typed angles and
+ * dihedrals); the potentials are those of dynbond_forcefield: each end of a
+ * bond feels the force of the type it stores (the directional half bonds of
+ * Sec. 2), angles and dihedrals follow the forms of Sec. 3.
+ *   d_force  device float4[N], overwritten (w = 0), FP32 per term;
+ *   d_ev     device double[R*7], overwritten: per replica (E, Wxx, Wyy, Wzz,
+ *            Wxy, Wxz, Wyz) with W_ab = sum over interactions of
+ *            (r_role - r_ref)_a F_role,b, reduced in FP64.
+ * d_pos and d_force must be 16-byte aligned (EINVAL otherwise, nothing is
+ * launched).  Stream-ordered; device errors surface at the next
+ * synchronizing call.
  */
 dynbond_status dynbond_forces(dynbond_ctx* ctx, const int32_t* d_pos, float* d_force, double* d_ev);
 
@@ -277,7 +288,14 @@ dynbond_status dynbond_forces(dynbond_ctx* ctx, const int32_t* d_pos, float* d_f
 dynbond_status dynbond_run_host(dynbond_ctx* ctx, const int32_t* h_pos, uint64_t step, float* h_force,
                                 double* h_ev, dynbond_stats* h_stats);
 
-/* Export the current topology (two-call protocol above).  Synchronizes. */
+/*
+ * Export the current topology: the bond set with the type each end stores
+ * and the typed angle and dihedral sets that the last dynbond_step left
+ * (Appendix steps 7 and 9; at creation, the typed set of every path of the
+ * initial bonds).  Two-call protocol of dynbond_topology above: host arrays,
+ * canonical records, sorted.  EINVAL if a given array is smaller than its
+ * count.  Synchronizes.
+ */
 dynbond_status dynbond_get_topology(dynbond_ctx* ctx, dynbond_topology* topo);
 
 /*
@@ -351,14 +369,22 @@ dynbond_status dynbond_phase_times(dynbond_ctx* ctx, float* ms, const char** nam
  *   d_force      float4[n_beads] output (overwritten, w = 0);
  *   d_ev         double[n_replicas*7] output (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).
  * Its scratch (the FP64 accumulators of up to DYNBOND_NOALLOC_MAX_REPLICAS
- * replicas, 229 KB) is a fixed array in device memory that every GPU loading
- * the library holds until the process exits; n_replicas above that limit
- * returns EINVAL.  The first call on a device looks up the array's device
- * address once (cudaGetSymbolAddress), so make that first call outside any
- * stream capture.  All calls on a device share the array: calls that overlap
- * on the GPU (different streams, no ordering) race and give wrong energies.
- * Work is enqueued on `stream`; returns EINVAL for bad sizes or NULL
- * pointers, ECUDA if a CUDA call fails.
+ * replicas and one error word, 229 KB) is a fixed array in device memory that
+ * every GPU loading the library holds until the process exits; n_replicas
+ * above that limit returns EINVAL.  The first call on a device looks up the
+ * array's device address once (cudaGetSymbolAddress), so make that first call
+ * outside any stream capture; no call may follow a cudaDeviceReset of that
+ * device in the same process.  All calls on a device share the array: calls
+ * that overlap on the GPU (different streams, no ordering) race and give
+ * wrong energies.
+ * Every bead id is checked on the device: a bond partner outside its bead's
+ * replica, an angle or dihedral bead outside the replica of its centre bead
+ * b, or an angle / dihedral type outside 0..15 is never dereferenced; the
+ * term is skipped (the others are still computed) and the call returns
+ * EINVAL.  Work is enqueued on `stream` and the call waits for it to finish
+ * (to read the error word).  Returns EINVAL for bad sizes, NULL or misaligned
+ * pointers (positions, slots and forces 16-byte, offsets, boxes and d_ev
+ * 8-byte, records 4-byte aligned) and bad ids, ECUDA if a CUDA call fails.
  */
 dynbond_status dynbond_forces_noalloc(const int32_t* d_pos, const uint32_t* d_slots, const int64_t* d_bead_offset,
                                       const int64_t* d_box_q, int32_t n_replicas, int64_t n_beads,
@@ -396,6 +422,16 @@ typedef struct dynbond_md dynbond_md;
 dynbond_status dynbond_md_create(dynbond_ctx* ctx, const dynbond_dpd* dpd, dynbond_md** out);
 dynbond_status dynbond_md_advance(dynbond_md* md, int32_t* d_pos, float* d_vel, int64_t n_steps, uint64_t first_step,
                                   double* d_ev);
+/*
+ * The DPD pair forces alone (Sec. 3: F^C + F^D + F^R along r_ij for r < r_c,
+ * none between beads fewer than 3 bonds apart) at d_pos (int4[N]) and d_vel
+ * (float4[N], w ignored) for step index `step` (which selects the Gaussian
+ * numbers xi), written to d_force (device float4[N], w = 0).  All three
+ * 16-byte aligned (else EINVAL).  Positions and velocities are not changed.
+ * Waits for completion.
+ */
+dynbond_status dynbond_md_pair_forces(dynbond_md* md, const int32_t* d_pos, const float* d_vel, uint64_t step,
+                                      float* d_force);
 void dynbond_md_destroy(dynbond_md* md);
 
 /* Human-readable text of the last error of ctx (never NULL). */

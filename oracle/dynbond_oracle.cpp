@@ -688,26 +688,34 @@ void angle_cos(const double ra[3], const double rc[3], double K, double* E, doub
 }
 
 // Harmonic angle E = K (theta - theta0)^2 (the DNA angles of Sec. 3) with
-// ra = r_A - r_B, rc = r_C - r_B.  F_A = -dE/dr_A = -2K (theta - theta0)
-// dtheta/dr_A, and dtheta/dr_A = -(1 / sin theta) dcos/dr_A; sin theta is
-// clamped below at 1e-3 (a straight angle with theta0 < pi would otherwise
-// have an unbounded force).
+// ra = r_A - r_B, rc = r_C - r_B and theta the angle at B.  The gradient of
+// theta follows from rotating each end about the unit normal n = (ra x rc) /
+// |ra x rc| of the plane ABC: moving A along n x ra opens the angle, so
+// dtheta/dr_A = (ra x n) / |ra|^2 and dtheta/dr_C = -(rc x n) / |rc|^2, each
+// of magnitude 1 / |r|.  F = -dE/dr = -2K (theta - theta0) dtheta/dr.  This
+// holds at every angle where the plane exists; exactly collinear beads have
+// no plane and get no angle force.
 void angle_harmonic(const double ra[3], const double rc[3], double K, double theta0, double* E, double Fa[3],
                     double Fc[3]) {
-  double la = std::sqrt(dot(ra, ra)), lc = std::sqrt(dot(rc, rc));
-  double cs = dot(ra, rc) / (la * lc);
-  double x[3] = {ra[1] * rc[2] - ra[2] * rc[1], ra[2] * rc[0] - ra[0] * rc[2], ra[0] * rc[1] - ra[1] * rc[0]};
-  double cr = std::sqrt(dot(x, x));
-  double theta = std::atan2(cr, dot(ra, rc));  // the angle at B, accurate near 0 and pi
-  double sn = std::max(cr / (la * lc), 1e-3);
-  double dEdth = 2.0 * K * (theta - theta0);
-  for (int k = 0; k < 3; ++k) {
-    double ga = rc[k] / (la * lc) - cs * ra[k] / (la * la);  // dcos/dr_A
-    double gc = ra[k] / (la * lc) - cs * rc[k] / (lc * lc);  // dcos/dr_C
-    Fa[k] = dEdth / sn * ga;
-    Fc[k] = dEdth / sn * gc;
-  }
+  double w[3];
+  cross(ra, rc, w);
+  double wn = std::sqrt(dot(w, w));
+  double theta = std::atan2(wn, dot(ra, rc));  // accurate near 0 and pi
+  double g = 2.0 * K * (theta - theta0);        // dE/dtheta
   *E = K * (theta - theta0) * (theta - theta0);
+  if (wn == 0.0) {
+    for (int k = 0; k < 3; ++k) Fa[k] = Fc[k] = 0.0;
+    return;
+  }
+  double n[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+  double ta[3], tc[3];
+  cross(ra, n, ta);
+  cross(rc, n, tc);
+  double la2 = dot(ra, ra), lc2 = dot(rc, rc);
+  for (int k = 0; k < 3; ++k) {
+    Fa[k] = -g * ta[k] / la2;
+    Fc[k] = g * tc[k] / lc2;
+  }
 }
 
 // Dihedral E = K (1 + d cos phi), b1 = r_B - r_A, b2 = r_C - r_B, b3 = r_D - r_C,
@@ -944,6 +952,54 @@ int orc_forces(void* h, const int32_t* pos, const double* bond_k, const double* 
   }
   o->pos = nullptr;
   return 0;
+}
+
+// DPD pair forces of Sec. 3 (FP64), by brute force over every pair of beads
+// of a replica: for r = |r_i - r_j| < r_c,
+//   F_i += (F^C + F^D + F^R) r_ij / r,  F^C = a w(r),
+//   F^D = -gamma w(r)^2 (r_ij . v_ij) / r,  F^R = sigma w(r) xi / sqrt(dt),
+// w(r) = 1 - r / r_c, sigma = sqrt(2 kT gamma), r_ij = r_i - r_j, v_ij = v_i
+// - v_j; pairs fewer than 3 bonds apart (graph distance 1 or 2) carry no pair
+// force (Sec. 3).  "r < r_c" is decided exactly on the integer grid as d2 <
+// floor((r_c 2^20)^2).  xi is the unit Gaussian of the pair at this step:
+// Philox4x32-10 on the counter (lower id, higher id, step low word, step high
+// word xor 0x3D000000) with the 64-bit seed as key; its first two words give
+// u1 = ((x0 >> 9) + 1/2) 2^-23 in (0, 1) and u2 = (x1 >> 9) 2^-23 in [0, 1),
+// and xi = sqrt(-2 ln u1) cos(2 pi u2) (Box and Muller, Ann. Math. Stat. 29,
+// 610 (1958)), the same number for both beads of the pair.
+void orc_dpd_forces(void* h, const int32_t* pos, const double* vel, double a, double gamma, double kT, double rc,
+                    double dt, uint64_t seed, uint64_t step, double* force) {
+  Oracle* o = static_cast<Oracle*>(h);
+  o->pos = pos;
+  std::memset(force, 0, sizeof(double) * 3 * o->N);
+  const int64_t rc2 = r2_of(rc);
+  const double sigma = std::sqrt(2.0 * kT * gamma);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const double pi = 3.14159265358979323846;
+  for (int r = 0; r < o->R; ++r)
+    for (int64_t i = o->off[r]; i < o->off[r + 1]; ++i)
+      for (int64_t j = i + 1; j < o->off[r + 1]; ++j) {
+        if (o->d2(i, j) >= rc2) continue;
+        if (o->graph_distance(i, j) < 3) continue;
+        double rij[3];
+        o->rel(i, j, rij);
+        const double rr = std::sqrt(dot(rij, rij));
+        if (rr <= 0.0) continue;
+        const double w = 1.0 - rr / rc;
+        double rv = 0.0;
+        for (int c = 0; c < 3; ++c) rv += rij[c] * (vel[3 * i + c] - vel[3 * j + c]);
+        const uint32_t ctr[4] = {(uint32_t)i, (uint32_t)j, (uint32_t)step, (uint32_t)(step >> 32) ^ 0x3D000000u};
+        uint32_t u[4];
+        philox4x32_10(ctr, key, u);
+        const double u1 = ((double)(u[0] >> 9) + 0.5) / 8388608.0, u2 = (double)(u[1] >> 9) / 8388608.0;
+        const double xi = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * pi * u2);
+        const double fs = a * w - gamma * w * w * rv / rr + sigma * w * xi / std::sqrt(dt);
+        for (int c = 0; c < 3; ++c) {
+          force[3 * i + c] += fs * rij[c] / rr;
+          force[3 * j + c] -= fs * rij[c] / rr;
+        }
+      }
+  o->pos = nullptr;
 }
 
 // Force primitives on explicit relative vectors (for finite-difference pins).

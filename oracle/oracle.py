@@ -81,6 +81,7 @@ def lib():
         L.orc_angle.argtypes = [P, P, ctypes.c_double, P, P, P]
         L.orc_angle_harmonic.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P]
         L.orc_dihedral.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
+        L.orc_dpd_forces.argtypes = [P, P, P] + [ctypes.c_double] * 5 + [ctypes.c_uint64, ctypes.c_uint64, P]
         assert L.orc_stat_count() == len(STAT_NAMES)
         _lib = L
     return _lib
@@ -203,6 +204,17 @@ class Oracle:
         sty = np.ascontiguousarray(ff.get("angle_style", np.zeros(16)), np.int32)
         lib().orc_forces(self.h, _p(pos), *[_p(a) for a in arrs], _p(dd), _p(t0), _p(sty), _p(f), _p(ev))
         return f, ev
+
+    def dpd_forces(self, pos: np.ndarray, vel: np.ndarray, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.01,
+                   seed=12345, step=0) -> np.ndarray:
+        """DPD pair forces of Sec. 3 on the oracle's current bonds (FP64,
+        brute force over pairs): float64 [N, 3]."""
+        pos = np.ascontiguousarray(pos, np.int32)
+        vel = np.ascontiguousarray(np.asarray(vel)[:, :3], np.float64)
+        f = np.zeros((self.N, 3), np.float64)
+        lib().orc_dpd_forces(self.h, _p(pos), _p(vel), a, gamma, kT, rc, dt, int(seed) % (1 << 64), int(step),
+                             _p(f))
+        return f
 
 
 def philox(ctr, key) -> np.ndarray:

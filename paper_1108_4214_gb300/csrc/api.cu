@@ -381,9 +381,6 @@ dynbond_status device_status(dynbond_ctx* c) {
   } else if (err & ERR_ROUNDS) {
     s = DYNBOND_ENOTCONVERGED;
     msg = "matching did not reach a fixpoint within DYNBOND_MAX_ROUNDS rounds";
-  } else if (err & ERR_CAND) {
-    s = DYNBOND_ECAPACITY;
-    msg = "a bead had more than DYNBOND_MAX_CANDIDATES creation candidates";
   } else if (err & ERR_CAND_CAP) {
     s = DYNBOND_ECAPACITY;
     msg = "candidate buffer exhausted";

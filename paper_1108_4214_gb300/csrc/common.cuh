@@ -22,7 +22,6 @@ constexpr unsigned FULL = 0xffffffffu;
 // bits of the sticky device error word
 enum : unsigned {
   ERR_POS = 1u,        // a position outside [0, box)
-  ERR_CAND = 2u,       // (unused: beads with many candidates take the exact overflow path)
   ERR_CAND_CAP = 4u,   // candidate buffer exhausted
   ERR_SLOTS = 8u,      // a bead would exceed SLOTS bonds (internal)
   ERR_TIMEOUT = 16u,   // a bounded wait gave up

@@ -20,44 +20,6 @@ __device__ __forceinline__ float3 relq(const int4& a, const int4& b, int L) {
   return make_float3((float)wrap_dx(a.x - b.x, L) * q, (float)wrap_dx(a.y - b.y, L) * q,
                      (float)wrap_dx(a.z - b.z, L) * q);
 }
-// exact integer minimum-image displacement a - b (quantized units)
-__device__ __forceinline__ int3 reli(const int4& a, const int4& b, int L) {
-  return make_int3(wrap_dx(a.x - b.x, L), wrap_dx(a.y - b.y, L), wrap_dx(a.z - b.z, L));
-}
-struct L3 {
-  long long x, y, z;
-};
-__device__ __forceinline__ L3 crossi(int3 a, int3 b) {
-  return L3{(long long)a.y * b.z - (long long)a.z * b.y, (long long)a.z * b.x - (long long)a.x * b.z,
-            (long long)a.x * b.y - (long long)a.y * b.x};
-}
-__device__ __forceinline__ long long doti(int3 a, int3 b) {
-  return (long long)a.x * b.x + (long long)a.y * b.y + (long long)a.z * b.z;
-}
-// a . b formed exactly in 128 bits, returned as FP32 times 2^e2
-__device__ __forceinline__ float triplei(int3 a, L3 b, int e2) {
-  __int128 t = (__int128)a.x * b.x + (__int128)a.y * b.y + (__int128)a.z * b.z;
-  const __int128 lim = (__int128)0x3FFFFFFFFFFFFFFFll;
-  while (t > lim || t < -lim) {  // drop low bits: relative change below 2^-54
-    t >>= 8;
-    e2 += 8;
-  }
-  return ldexpf((float)(long long)t, e2);
-}
-__device__ __forceinline__ float3 tof(int3 v, float s) {
-  return make_float3((float)v.x * s, (float)v.y * s, (float)v.z * s);
-}
-__device__ __forceinline__ float3 tof(L3 v, float s) {
-  return make_float3((float)v.x * s, (float)v.y * s, (float)v.z * s);
-}
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float3 axpy(float a, float3 x, float3 y) {
-  return make_float3(a * x.x + y.x, a * x.y + y.y, a * x.z + y.z);
-}
-__device__ __forceinline__ float3 scale(float a, float3 x) { return make_float3(a * x.x, a * x.y, a * x.z); }
 
 // Energy / virial accumulators: a thread sums its own few terms (at most a
 // few tens: its beads' bonds or its records over the launch) in plain FP32;
@@ -229,14 +191,11 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ff) {
           atomicOr(d.err, ERR_INTERNAL);
           continue;
         }
-        const int t = s_type(v);
-        float3 rij = relq(p, sm.pos[k & 1][u][1 + q][tid], L);
-        float ir = rsqrtf(dot3(rij, rij));
-        float dr = dot3(rij, rij) * ir - ff.bond_r0[t];
-        float fscal = -2.0f * ff.bond_k[t] * dr * ir;
-        float3 fq = scale(fscal, rij);
+        const float3 rij = relq(p, sm.pos[k & 1][u][1 + q][tid], L);
+        const BondHalf h = bond_half_force(ff, s_type(v), rij);
+        const float3 fq = h.f;
         f = make_float3(f.x + fq.x, f.y + fq.y, f.z + fq.z);
-        e += 0.5f * ff.bond_k[t] * dr * dr;
+        e += h.E;
         w[0] += rij.x * fq.x;
         w[1] += rij.y * fq.y;
         w[2] += rij.z * fq.z;
@@ -258,80 +217,44 @@ __device__ __forceinline__ void add_force(float4* f, int i, float3 v) {
   red_add_f4(f, i, v.x, v.y, v.z);
 }
 
-// One angle (cosine or harmonic in theta, see angle_coef) with r_A - r_B and
-// r_C - r_B.
+// One angle (angle_term_forces); F_B = -(F_A + F_C).
 __device__ __forceinline__ void angle_term(float4* force, const int4& a, const int4& pa, const int4& pb,
                                            const int4& pc, int L, const FF& ff, float& e, float* w) {
-  float3 ra = relq(pa, pb, L), rc = relq(pc, pb, L);
-  float ia = rsqrtf(dot3(ra, ra)), ic = rsqrtf(dot3(rc, rc));
-  float inv = ia * ic;
-  float cs = dot3(ra, rc) * inv;
-  float Ea;
-  const float cf = angle_coef(ff, a.w, pa, pb, pc, L, cs, inv, &Ea);
-  // F_A = c d(cos)/d(r_A), F_C likewise, F_B = -(F_A + F_C)
-  float3 Fa = scale(cf, axpy(-cs * ia * ia, ra, scale(inv, rc)));
-  float3 Fc = scale(cf, axpy(-cs * ic * ic, rc, scale(inv, ra)));
-  float3 Fb = make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z);
-  add_force(force, a.x, Fa);
+  const AngleTerm o = angle_term_forces(ff, a.w, pa, pb, pc, L);
+  const float3 Fb = make_float3(-o.Fa.x - o.Fc.x, -o.Fa.y - o.Fc.y, -o.Fa.z - o.Fc.z);
+  add_force(force, a.x, o.Fa);
   add_force(force, a.y, Fb);
-  add_force(force, a.z, Fc);
-  e += Ea;
-  w[0] += ra.x * Fa.x + rc.x * Fc.x;
-  w[1] += ra.y * Fa.y + rc.y * Fc.y;
-  w[2] += ra.z * Fa.z + rc.z * Fc.z;
-  w[3] += ra.x * Fa.y + rc.x * Fc.y;
-  w[4] += ra.x * Fa.z + rc.x * Fc.z;
-  w[5] += ra.y * Fa.z + rc.y * Fc.z;
+  add_force(force, a.z, o.Fc);
+  e += o.E;
+  w[0] += o.ra.x * o.Fa.x + o.rc.x * o.Fc.x;
+  w[1] += o.ra.y * o.Fa.y + o.rc.y * o.Fc.y;
+  w[2] += o.ra.z * o.Fa.z + o.rc.z * o.Fc.z;
+  w[3] += o.ra.x * o.Fa.y + o.rc.x * o.Fc.y;
+  w[4] += o.ra.x * o.Fa.z + o.rc.x * o.Fc.z;
+  w[5] += o.ra.y * o.Fa.z + o.rc.y * o.Fc.z;
 }
 
-// One dihedral: E = K (1 + d cos phi).  Blondel-Karplus: F = r_A - r_B,
-// G = r_B - r_C, H = r_D - r_C, A = F x G, B = H x G; cos phi = A.B /
-// (|A||B|), phi = 180 deg trans.  The cross, dot and triple products are
-// formed exactly from the integer displacements and rounded once, so
-// near-collinear quartets keep FP32 accuracy; the rest is FP32.
+// One dihedral (dihedral_term_forces); the record's fourth bead carries the
+// type in its top 4 bits.
 __device__ __forceinline__ void dihedral_term(float4* force, const int4& rec, const int4& P0, const int4& P1,
                                               const int4& P2, const int4& P3, int L, const FF& ff, float& e,
                                               float* w) {
-  int ia = rec.x, ib = rec.y, ic = rec.z, id = rec.w & 0x0FFFFFFF;
-  int t = (int)((unsigned)rec.w >> 28);
-  int3 Fi = reli(P0, P1, L), Gi = reli(P1, P2, L), Hi = reli(P3, P2, L);
-  L3 Ai = crossi(Fi, Gi), Bi = crossi(Hi, Gi);
-  const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
-  float3 F = tof(Fi, s20), G = tof(Gi, s20), H = tof(Hi, s20);
-  float3 A = tof(Ai, s40), B = tof(Bi, s40);
-  float A2 = dot3(A, A), B2 = dot3(B, B);
-  float gg = (float)doti(Gi, Gi) * s40;
-  float irg = rsqrtf(gg), rg = gg * irg;
-  float rab = rsqrtf(A2 * B2);
-  float cs = dot3(A, B) * rab;
-  // (B x A).G = -|G|^2 F.B, so sin phi = -|G| (F.B) / (|A||B|)
-  float sn = -rg * triplei(Fi, Bi, -60) * rab;
-  float K = ff.dih_k[t], dd = ff.dih_d[t];
-  // E = K (1 + d cos phi): -dE/dphi = K d sin phi
-  float mdE = K * dd * sn;
-  float fg = (float)doti(Fi, Gi) * s40, hg = (float)doti(Hi, Gi) * s40;
-  float ia2 = __frcp_rn(A2), ib2 = __frcp_rn(B2);
-  // dphi/dr_A = -|G|/A^2 A ; dphi/dr_D = |G|/B^2 B
-  // dphi/dr_B = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B
-  // dphi/dr_C = -F.G/(A^2|G|) A + (H.G/(B^2|G|) - |G|/B^2) B
-  float3 dA = scale(-rg * ia2, A);
-  float3 dD = scale(rg * ib2, B);
-  float3 dB = axpy(-hg * ib2 * irg, B, scale(rg * ia2 + fg * ia2 * irg, A));
-  float3 dC = axpy(hg * ib2 * irg - rg * ib2, B, scale(-fg * ia2 * irg, A));
-  float3 Fa = scale(mdE, dA), Fb = scale(mdE, dB), Fc = scale(mdE, dC), Fd = scale(mdE, dD);
-  add_force(force, ia, Fa);
-  add_force(force, ib, Fb);
-  add_force(force, ic, Fc);
-  add_force(force, id, Fd);
-  e += K * (1.0f + dd * cs);
+  const int id = rec.w & 0x0FFFFFFF, t = (int)((unsigned)rec.w >> 28);
+  const DihedralTerm o = dihedral_term_forces(ff, t, P0, P1, P2, P3, L);
+  add_force(force, rec.x, o.Fa);
+  add_force(force, rec.y, o.Fb);
+  add_force(force, rec.z, o.Fc);
+  add_force(force, id, o.Fd);
+  e += o.E;
   // virial relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
-  float3 mg = make_float3(-G.x, -G.y, -G.z), hm = make_float3(H.x - G.x, H.y - G.y, H.z - G.z);
-  w[0] += F.x * Fa.x + mg.x * Fc.x + hm.x * Fd.x;
-  w[1] += F.y * Fa.y + mg.y * Fc.y + hm.y * Fd.y;
-  w[2] += F.z * Fa.z + mg.z * Fc.z + hm.z * Fd.z;
-  w[3] += F.x * Fa.y + mg.x * Fc.y + hm.x * Fd.y;
-  w[4] += F.x * Fa.z + mg.x * Fc.z + hm.x * Fd.z;
-  w[5] += F.y * Fa.z + mg.y * Fc.z + hm.y * Fd.z;
+  const float3 F = o.F, mg = make_float3(-o.G.x, -o.G.y, -o.G.z);
+  const float3 hm = make_float3(o.H.x - o.G.x, o.H.y - o.G.y, o.H.z - o.G.z);
+  w[0] += F.x * o.Fa.x + mg.x * o.Fc.x + hm.x * o.Fd.x;
+  w[1] += F.y * o.Fa.y + mg.y * o.Fc.y + hm.y * o.Fd.y;
+  w[2] += F.z * o.Fa.z + mg.z * o.Fc.z + hm.z * o.Fd.z;
+  w[3] += F.x * o.Fa.y + mg.x * o.Fc.y + hm.x * o.Fd.y;
+  w[4] += F.x * o.Fa.z + mg.x * o.Fc.z + hm.x * o.Fd.z;
+  w[5] += F.y * o.Fa.z + mg.y * o.Fc.z + hm.y * o.Fd.z;
 }
 
 // A work item of the angle / dihedral launch: tiles [0, tb_fang[R]) of the

@@ -47,30 +47,161 @@ inline bool make_ff(const dynbond_forcefield& in, FF& out) {
   return true;
 }
 
-// Coefficient c and energy of an angle term of type t (centre bead B, ends A
-// and C; cos theta = cs, inv = 1 / (|r_A - r_B| |r_C - r_B|) in sigma^-2):
-// F_A = c dcos/dr_A, F_C = c dcos/dr_C.  Cosine: E = K (1 + cos), c = -K.
-// Harmonic: E = K (theta - theta0)^2, c = 2 K (theta - theta0) / sin theta
-// (d theta / d cos = -1 / sin), sin clamped below at 1e-3.  For the harmonic
-// form pi - theta = atan2(|u x v|, -u.v) is taken from the exact integer
-// cross and dot products of the displacements u, v, so nearly straight
-// angles keep FP32 relative accuracy.
-__device__ __forceinline__ float angle_coef(const FF& ff, int t, const int4& pa, const int4& pb, const int4& pc, int L,
-                                            float cs, float inv, float* E) {
+// ---------------------------------------------------------------------------
+// Per-term force arithmetic shared by the context's force kernels and the
+// allocation-free entry point.  Every term starts from exact integer
+// minimum-image displacements (quantized units, 2^-20 sigma); cross, dot and
+// triple products are formed exactly in 64 / 128-bit integers and rounded
+// once, the rest is FP32.
+// ---------------------------------------------------------------------------
+struct L3 {
+  long long x, y, z;
+};
+__device__ __forceinline__ int3 reli(const int4& a, const int4& b, int L) {
+  return make_int3(wrap_dx(a.x - b.x, L), wrap_dx(a.y - b.y, L), wrap_dx(a.z - b.z, L));
+}
+__device__ __forceinline__ L3 crossi(int3 a, int3 b) {
+  return L3{(long long)a.y * b.z - (long long)a.z * b.y, (long long)a.z * b.x - (long long)a.x * b.z,
+            (long long)a.x * b.y - (long long)a.y * b.x};
+}
+__device__ __forceinline__ long long doti(int3 a, int3 b) {
+  return (long long)a.x * b.x + (long long)a.y * b.y + (long long)a.z * b.z;
+}
+// a . b formed exactly in 128 bits, returned as FP32 times 2^e2
+__device__ __forceinline__ float triplei(int3 a, L3 b, int e2) {
+  __int128 t = (__int128)a.x * b.x + (__int128)a.y * b.y + (__int128)a.z * b.z;
+  const __int128 lim = (__int128)0x3FFFFFFFFFFFFFFFll;
+  while (t > lim || t < -lim) {  // drop low bits: relative change below 2^-54
+    t >>= 8;
+    e2 += 8;
+  }
+  return ldexpf((float)(long long)t, e2);
+}
+__device__ __forceinline__ float3 tof(int3 v, float s) {
+  return make_float3((float)v.x * s, (float)v.y * s, (float)v.z * s);
+}
+__device__ __forceinline__ float3 tof(L3 v, float s) {
+  return make_float3((float)v.x * s, (float)v.y * s, (float)v.z * s);
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 axpy(float a, float3 x, float3 y) {
+  return make_float3(a * x.x + y.x, a * x.y + y.y, a * x.z + y.z);
+}
+__device__ __forceinline__ float3 scale(float a, float3 x) { return make_float3(a * x.x, a * x.y, a * x.z); }
+
+// One end of a bond, seen from the bead that stores type t (rij = r_i - r_j,
+// sigma): the end feels the full force of E = K (r - r0)^2 of the type IT
+// stores and books half the energy (directional bonds, Sec. 2).
+struct BondHalf {
+  float3 f;
+  float E;
+};
+__device__ __forceinline__ BondHalf bond_half_force(const FF& ff, int t, float3 rij) {
+  const float rr2 = dot3(rij, rij), ir = rsqrtf(rr2);
+  const float dr = rr2 * ir - ff.bond_r0[t];
+  BondHalf o;
+  o.f = scale(-2.0f * ff.bond_k[t] * dr * ir, rij);
+  o.E = 0.5f * ff.bond_k[t] * dr * dr;
+  return o;
+}
+
+// One angle term of type t (ends A and C, centre B): end forces Fa, Fc
+// (F_B = -(Fa + Fc)), the relative vectors ra = r_A - r_B, rc = r_C - r_B
+// for the virial, and the energy.
+//   cosine    E = K (1 + cos theta): F_A = -K dcos/dr_A, F_C likewise.
+//   harmonic  E = K (theta - theta0)^2 (the DNA angles of Sec. 3), with theta
+//             = atan2(|ra x rc|, ra . rc) from the exact integer products.
+//             The gradient of theta is taken through the unit normal n of the
+//             plane ABC: dtheta/dr_A = (ra x n) / |ra|^2 and dtheta/dr_C =
+//             -(rc x n) / |rc|^2, which has magnitude 1 / |r| at every angle
+//             (no division by sin theta), so F_A = -2K (theta - theta0)
+//             (ra x n) / |ra|^2 and F_C = 2K (theta - theta0) (rc x n) /
+//             |rc|^2 are exact up to rounding arbitrarily close to 0 and
+//             180 degrees.  Exactly collinear beads (ra x rc = 0) have no
+//             plane and get no angle force (for theta0 = 180 deg that is the
+//             exact force).
+struct AngleTerm {
+  float3 ra, rc, Fa, Fc;
+  float E;
+};
+__device__ __forceinline__ AngleTerm angle_term_forces(const FF& ff, int t, const int4& pa, const int4& pb,
+                                                       const int4& pc, int L) {
+  const float s20 = 1.0f / 1048576.0f;
+  const int3 u = reli(pa, pb, L), v = reli(pc, pb, L);
+  AngleTerm o;
+  o.ra = tof(u, s20);
+  o.rc = tof(v, s20);
   const float K = ff.angle_k[t];
   if (!((ff.angle_harm >> t) & 1u)) {
-    *E = K * (1.0f + cs);
-    return -K;
+    const float ia = rsqrtf(dot3(o.ra, o.ra)), ic = rsqrtf(dot3(o.rc, o.rc));
+    const float inv = ia * ic;
+    const float cs = dot3(o.ra, o.rc) * inv;
+    // F_A = -K dcos/dr_A = -K (rc / (|ra||rc|) - cos ra / |ra|^2), F_C likewise
+    o.Fa = scale(-K, axpy(-cs * ia * ia, o.ra, scale(inv, o.rc)));
+    o.Fc = scale(-K, axpy(-cs * ic * ic, o.rc, scale(inv, o.ra)));
+    o.E = K * (1.0f + cs);
+    return o;
   }
-  const long long ux = wrap_dx(pa.x - pb.x, L), uy = wrap_dx(pa.y - pb.y, L), uz = wrap_dx(pa.z - pb.z, L);
-  const long long vx = wrap_dx(pc.x - pb.x, L), vy = wrap_dx(pc.y - pb.y, L), vz = wrap_dx(pc.z - pb.z, L);
-  const float cx = (float)(uy * vz - uz * vy), cy = (float)(uz * vx - ux * vz), cz = (float)(ux * vy - uy * vx);
-  const float sr = sqrtf(cx * cx + cy * cy + cz * cz);          // |u x v|, units^2
-  const float pth = atan2f(sr, -(float)(ux * vx + uy * vy + uz * vz));  // pi - theta
-  const float dth = ff.angle_pt0[t] - pth;                         // theta - theta0
-  const float s = fmaxf(sr * (1.0f / 1099511627776.0f) * inv, 1e-3f);  // sin theta (units^2 -> sigma^2)
-  *E = K * dth * dth;
-  return 2.0f * K * dth / s;
+  const L3 w = crossi(u, v);  // |w| = |ra||rc| sin theta (units^2), exact
+  const float wx = (float)w.x, wy = (float)w.y, wz = (float)w.z;
+  const float wn = sqrtf(wx * wx + wy * wy + wz * wz);
+  const float pth = atan2f(wn, -(float)doti(u, v));  // pi - theta
+  const float dth = ff.angle_pt0[t] - pth;          // theta - theta0
+  o.E = K * dth * dth;
+  if (wn == 0.0f) {
+    o.Fa = o.Fc = make_float3(0.f, 0.f, 0.f);
+    return o;
+  }
+  const float3 n = make_float3(wx / wn, wy / wn, wz / wn);
+  const float ga = -2.0f * K * dth / dot3(o.ra, o.ra), gc = 2.0f * K * dth / dot3(o.rc, o.rc);
+  o.Fa = scale(ga, cross3(o.ra, n));
+  o.Fc = scale(gc, cross3(o.rc, n));
+  return o;
+}
+
+// One dihedral term of type t: E = K (1 + d cos phi), phi = 180 deg trans
+// (Sec. 3).  Blondel-Karplus (J. Comput. Chem. 17, 1132 (1996)): F = r_A -
+// r_B, G = r_B - r_C, H = r_D - r_C, A = F x G, B = H x G; cos phi = A.B /
+// (|A||B|), sin phi = -|G| (F.B) / (|A||B|) since (B x A).G = -|G|^2 F.B; the
+// derivatives of phi carry no 1 / sin phi.  Returns the four forces, the
+// energy and the vectors F, G, H for the virial (r_A - r_B = F, r_C - r_B =
+// -G, r_D - r_B = H - G).
+struct DihedralTerm {
+  float3 F, G, H, Fa, Fb, Fc, Fd;
+  float E;
+};
+__device__ __forceinline__ DihedralTerm dihedral_term_forces(const FF& ff, int t, const int4& P0, const int4& P1,
+                                                             const int4& P2, const int4& P3, int L) {
+  const int3 Fi = reli(P0, P1, L), Gi = reli(P1, P2, L), Hi = reli(P3, P2, L);
+  const L3 Ai = crossi(Fi, Gi), Bi = crossi(Hi, Gi);
+  const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
+  DihedralTerm o;
+  o.F = tof(Fi, s20);
+  o.G = tof(Gi, s20);
+  o.H = tof(Hi, s20);
+  const float3 A = tof(Ai, s40), B = tof(Bi, s40);
+  const float A2 = dot3(A, A), B2 = dot3(B, B);
+  const float gg = (float)doti(Gi, Gi) * s40;
+  const float irg = rsqrtf(gg), rg = gg * irg;
+  const float rab = rsqrtf(A2 * B2);
+  const float cs = dot3(A, B) * rab;
+  const float sn = -rg * triplei(Fi, Bi, -60) * rab;
+  const float K = ff.dih_k[t], dd = ff.dih_d[t];
+  const float mdE = K * dd * sn;  // -dE/dphi = K d sin phi
+  const float fg = (float)doti(Fi, Gi) * s40, hg = (float)doti(Hi, Gi) * s40;
+  const float ia2 = __frcp_rn(A2), ib2 = __frcp_rn(B2);
+  // dphi/dr_A = -|G|/A^2 A ; dphi/dr_D = |G|/B^2 B
+  // dphi/dr_B = (|G|/A^2 + F.G/(A^2|G|)) A - H.G/(B^2|G|) B
+  // dphi/dr_C = -F.G/(A^2|G|) A + (H.G/(B^2|G|) - |G|/B^2) B
+  o.Fa = scale(mdE, scale(-rg * ia2, A));
+  o.Fd = scale(mdE, scale(rg * ib2, B));
+  o.Fb = scale(mdE, axpy(-hg * ib2 * irg, B, scale(rg * ia2 + fg * ia2 * irg, A)));
+  o.Fc = scale(mdE, axpy(hg * ib2 * irg - rg * ib2, B, scale(-fg * ia2 * irg, A)));
+  o.E = K * (1.0f + dd * cs);
+  return o;
 }
 
 __global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);

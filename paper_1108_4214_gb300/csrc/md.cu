@@ -118,12 +118,14 @@ __device__ __forceinline__ bool md_excluded(const uint4* __restrict__ slots, con
 }
 
 // Gaussian of pair (lo, hi) at a step: Box-Muller on two Philox words; the
-// key is symmetric in the pair so both beads draw the same number
+// counter is symmetric in the pair so both beads draw the same number.  The
+// uniforms u1 = ((x0 >> 9) + 1/2) 2^-23 in (0, 1) and u2 = (x1 >> 9) 2^-23
+// are exact in FP32.
 __device__ __forceinline__ float md_gauss(const MdDev& m, int lo, int hi, unsigned long long step) {
   uint4 u = philox4x32_10(make_uint4((unsigned)lo, (unsigned)hi, (unsigned)step, (unsigned)(step >> 32) ^ 0x3D000000u),
                           make_uint2(m.key0, m.key1));
-  float u1 = ((float)(u.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
-  float u2 = (float)(u.y >> 8) * (1.0f / 16777216.0f);
+  float u1 = ((float)(u.x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+  float u2 = (float)(u.y >> 9) * (1.0f / 8388608.0f);
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
@@ -276,7 +278,8 @@ dynbond_status dynbond_md_create(dynbond_ctx* ctx, const dynbond_dpd* prm, dynbo
 }
 
 namespace {
-dynbond_status md_forces(dynbond_md* md, int32_t* d_pos, const float* d_vel, unsigned long long step) {
+// DPD pair forces of step `step` into m.fdpd (cell binning, scan, scatter, pairs)
+dynbond_status md_pair(dynbond_md* md, const int32_t* d_pos, const float* d_vel, unsigned long long step) {
   const MdDev& m = md->m;
   cudaStream_t s = md->stream;
   int g = std::max(1, std::min<int>((int)((m.N + 255) / 256), md->nsm * 8));
@@ -285,10 +288,35 @@ dynbond_status md_forces(dynbond_md* md, int32_t* d_pos, const float* d_vel, uns
   md_scan<<<md->nsm * 4, 256, 0, s>>>(m);
   md_scatter<<<g, 256, 0, s>>>(m, (const int4*)d_pos);
   md_dpd<<<g, 256, 0, s>>>(m, (const int4*)d_pos, (const float4*)d_vel, md->slots, step);
-  if (cudaGetLastError() != cudaSuccess) return DYNBOND_ECUDA;
+  return cudaGetLastError() != cudaSuccess ? DYNBOND_ECUDA : DYNBOND_OK;
+}
+
+dynbond_status md_forces(dynbond_md* md, int32_t* d_pos, const float* d_vel, unsigned long long step) {
+  dynbond_status st = md_pair(md, d_pos, d_vel, step);
+  if (st) return st;
   return dynbond_forces(md->ctx, d_pos, (float*)md->fbond, md->ev);
 }
+
+dynbond_status md_wait(dynbond_md* md) {
+  unsigned err = 0;
+  if (cudaMemcpyAsync(&err, md->m.err, 4, cudaMemcpyDeviceToHost, md->stream) != cudaSuccess ||
+      cudaStreamSynchronize(md->stream) != cudaSuccess)
+    return DYNBOND_ECUDA;
+  return err ? DYNBOND_ETIMEOUT : DYNBOND_OK;
+}
 }  // namespace
+
+dynbond_status dynbond_md_pair_forces(dynbond_md* md, const int32_t* d_pos, const float* d_vel, uint64_t step,
+                                      float* d_force) {
+  if (!md || !d_pos || !d_vel || !d_force) return DYNBOND_EINVAL;
+  if (((uintptr_t)d_pos | (uintptr_t)d_vel | (uintptr_t)d_force) & 15u) return DYNBOND_EINVAL;
+  dynbond_status st = md_pair(md, d_pos, d_vel, step);
+  if (st) return st;
+  if (cudaMemcpyAsync(d_force, md->m.fdpd, 16 * (size_t)md->m.N, cudaMemcpyDeviceToDevice, md->stream) !=
+      cudaSuccess)
+    return DYNBOND_ECUDA;
+  return md_wait(md);
+}
 
 dynbond_status dynbond_md_advance(dynbond_md* md, int32_t* d_pos, float* d_vel, int64_t n_steps, uint64_t first_step,
                                   double* d_ev) {
@@ -306,10 +334,7 @@ dynbond_status dynbond_md_advance(dynbond_md* md, int32_t* d_pos, float* d_vel, 
     md_kick<<<g, 256, 0, s>>>(m, (float4*)d_vel, md->fbond, (int4*)d_pos, 0);
   }
   if (d_ev && cudaMemcpyAsync(d_ev, md->ev, 8 * 7, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return DYNBOND_ECUDA;
-  unsigned err = 0;
-  if (cudaMemcpyAsync(&err, m.err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-    return DYNBOND_ECUDA;
-  return err ? DYNBOND_ETIMEOUT : DYNBOND_OK;
+  return md_wait(md);
 }
 
 }  // extern "C"

@@ -19,10 +19,13 @@ namespace dynbond {
 namespace {
 
 constexpr int NA_MAX_R = DYNBOND_NOALLOC_MAX_REPLICAS;
+constexpr int NA_ERR_SLOT = NA_MAX_R * 7;  // the call's error word, after the accumulators
 
-// Per-replica energy / virial accumulators (7 doubles each), shared by every
-// call on a device; each call clears the part it uses before accumulating.
-static __device__ __align__(256) double g_noalloc_ev[NA_MAX_R * 7];
+// The scratch shared by every call on a device: per-replica energy / virial
+// accumulators (7 doubles each) and, in the slot after them, the error word
+// of the call (nonzero when a term named a bead outside its replica or a type
+// outside 0..15).  Each call clears what it uses before accumulating.
+static __device__ __align__(256) double g_noalloc_scratch[NA_ERR_SLOT + 1];
 
 // replica of bead x: largest r with off[r] <= x
 __device__ __forceinline__ int na_rep(const long long* off, int R, long long x) {
@@ -35,12 +38,19 @@ __device__ __forceinline__ int na_rep(const long long* off, int R, long long x) 
   return lo;
 }
 
+// bead id x lies in [0, N) and in the bead range [lo, hi) of the replica
+__device__ __forceinline__ bool na_in(long long x, long long lo, long long hi, long long N) {
+  return x >= 0 && x < N && x >= lo && x < hi;
+}
+__device__ __forceinline__ void na_flag(double* scratch) {
+  atomicOr(reinterpret_cast<unsigned long long*>(scratch + NA_ERR_SLOT), 1ull);
+}
+
 __device__ __forceinline__ float3 na_rel(const int4& a, const int4& b, int L) {
   const float q = 1.0f / 1048576.0f;
   return make_float3((float)wrap_dx(a.x - b.x, L) * q, (float)wrap_dx(a.y - b.y, L) * q,
                      (float)wrap_dx(a.z - b.z, L) * q);
 }
-__device__ __forceinline__ float na_dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
 // Per-lane FP64 accumulation of one replica's energy and virial; flushed
 // with atomics to the scratch when the lane moves to another replica.
@@ -88,130 +98,107 @@ struct NaAcc {
   }
 };
 
-__global__ void na_clear(double* ev, int n) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) ev[k] = 0.0;
+// zero the accumulators of n_ev values and the error word
+__global__ void na_clear(double* scratch, int n_ev) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_ev; k += gridDim.x * blockDim.x) scratch[k] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *reinterpret_cast<unsigned long long*>(scratch + NA_ERR_SLOT) = 0ull;
 }
 
 // bonds: each bead applies the force of the type it stores (directional
-// bonds, Sec. 2) and books half the energy; plain stores initialize force[]
+// bonds, Sec. 2) and books half the energy; plain stores initialize force[].
+// A slot whose partner lies outside the bead's replica is skipped and flagged.
 __global__ void na_bonds(const int4* __restrict__ pos, const uint4* __restrict__ slots, const long long* off,
-                         const long long* box, int R, long long N, FF ff, float4* force, double* ev) {
+                         const long long* box, int R, long long N, FF ff, float4* force, double* scratch) {
   NaAcc acc;
   acc.flush(nullptr);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    int r = na_rep(off, R, i);
-    acc.to(r, ev);
-    int L = (int)box[r];
-    int4 p = pos[i];
-    uint4 s = slots[i];
+    const int r = na_rep(off, R, i);
+    acc.to(r, scratch);
+    const long long lo = off[r], hi = off[r + 1];
+    const int L = (int)box[r];
+    const int4 p = pos[i];
+    const uint4 s = slots[i];
     float3 f = make_float3(0.f, 0.f, 0.f);
     for (int q = 0; q < SLOTS; ++q) {
-      unsigned v = s_get(s, q);
+      const unsigned v = s_get(s, q);
       if (!v) continue;
-      int t = s_type(v);
-      float3 rij = na_rel(p, pos[s_partner(v)], L);
-      float rr = sqrtf(na_dot(rij, rij));
-      float dr = rr - ff.bond_r0[t];
-      float fs = -2.0f * ff.bond_k[t] * dr / rr;
-      float3 fq = make_float3(fs * rij.x, fs * rij.y, fs * rij.z);
-      f = make_float3(f.x + fq.x, f.y + fq.y, f.z + fq.z);
-      acc.e[0] += (double)(0.5f * ff.bond_k[t] * dr * dr);
-      acc.vir(rij, fq, 0.5f);
+      const long long j = s_partner(v);
+      if (!na_in(j, lo, hi, N)) {
+        na_flag(scratch);
+        continue;
+      }
+      const float3 rij = na_rel(p, pos[j], L);
+      const BondHalf h = bond_half_force(ff, s_type(v), rij);
+      f = make_float3(f.x + h.f.x, f.y + h.f.y, f.z + h.f.z);
+      acc.e[0] += (double)h.E;
+      acc.vir(rij, h.f, 0.5f);
     }
     force[i] = make_float4(f.x, f.y, f.z, 0.f);
   }
-  acc.flush_warp(ev);
+  acc.flush_warp(scratch);
 }
 
 __device__ __forceinline__ void na_add(float4* f, int i, float3 v) { red_add_f4(f, i, v.x, v.y, v.z); }
 
-// angles E = K (1 + cos theta); dihedrals E = K (1 + d cos phi) with the
-// Blondel-Karplus derivatives of phi
+// angles and dihedrals (angle_term_forces, dihedral_term_forces); a record
+// naming a bead outside the replica of its centre bead b, or a type outside
+// 0..15, is skipped and flagged
 __global__ void na_angles_dihedrals(const int4* __restrict__ pos, const long long* off, const long long* box, int R,
-                                    const int* __restrict__ ang, long long na, const int* __restrict__ dih,
-                                    long long nd, FF ff, float4* force, double* ev) {
+                                    long long N, const int* __restrict__ ang, long long na,
+                                    const int* __restrict__ dih, long long nd, FF ff, float4* force,
+                                    double* scratch) {
   NaAcc acc;
   acc.flush(nullptr);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < na + nd; k += stride) {
     if (k < na) {
-      int a = ang[4 * k], b = ang[4 * k + 1], c = ang[4 * k + 2], t = ang[4 * k + 3];
-      int r = na_rep(off, R, b);
-      acc.to(r, ev);
-      int L = (int)box[r];
-      int4 pb = pos[b];
-      float3 ra = na_rel(pos[a], pb, L), rc = na_rel(pos[c], pb, L);
-      float la2 = na_dot(ra, ra), lc2 = na_dot(rc, rc);
-      float inv = rsqrtf(la2 * lc2);
-      float cs = na_dot(ra, rc) * inv;
-      float Ea;
-      const float cf = angle_coef(ff, t, pos[a], pb, pos[c], L, cs, inv, &Ea);
-      float3 Fa = make_float3(cf * (rc.x * inv - cs * ra.x / la2), cf * (rc.y * inv - cs * ra.y / la2),
-                              cf * (rc.z * inv - cs * ra.z / la2));
-      float3 Fc = make_float3(cf * (ra.x * inv - cs * rc.x / lc2), cf * (ra.y * inv - cs * rc.y / lc2),
-                              cf * (ra.z * inv - cs * rc.z / lc2));
-      na_add(force, a, Fa);
-      na_add(force, b, make_float3(-Fa.x - Fc.x, -Fa.y - Fc.y, -Fa.z - Fc.z));
-      na_add(force, c, Fc);
-      acc.e[0] += (double)Ea;
-      acc.vir(ra, Fa, 1.f);
-      acc.vir(rc, Fc, 1.f);
-    } else {
-      long long m = k - na;
-      int ia = dih[5 * m], ib = dih[5 * m + 1], ic = dih[5 * m + 2], id = dih[5 * m + 3], t = dih[5 * m + 4];
-      int r = na_rep(off, R, ib);
-      acc.to(r, ev);
-      int L = (int)box[r];
-      int4 pb = pos[ib], pc = pos[ic], pa = pos[ia], pd = pos[id];
-      // F = r_A - r_B, G = r_B - r_C, H = r_D - r_C; A = F x G, B = H x G,
-      // products formed exactly from the integer displacements
-      int3 Fi = make_int3(wrap_dx(pa.x - pb.x, L), wrap_dx(pa.y - pb.y, L), wrap_dx(pa.z - pb.z, L));
-      int3 Gi = make_int3(wrap_dx(pb.x - pc.x, L), wrap_dx(pb.y - pc.y, L), wrap_dx(pb.z - pc.z, L));
-      int3 Hi = make_int3(wrap_dx(pd.x - pc.x, L), wrap_dx(pd.y - pc.y, L), wrap_dx(pd.z - pc.z, L));
-      long long Ax = (long long)Fi.y * Gi.z - (long long)Fi.z * Gi.y, Ay = (long long)Fi.z * Gi.x - (long long)Fi.x * Gi.z,
-                Az = (long long)Fi.x * Gi.y - (long long)Fi.y * Gi.x;
-      long long Bx = (long long)Hi.y * Gi.z - (long long)Hi.z * Gi.y, By = (long long)Hi.z * Gi.x - (long long)Hi.x * Gi.z,
-                Bz = (long long)Hi.x * Gi.y - (long long)Hi.y * Gi.x;
-      const float s20 = 1.0f / 1048576.0f, s40 = s20 * s20;
-      float3 F = make_float3(Fi.x * s20, Fi.y * s20, Fi.z * s20), G = make_float3(Gi.x * s20, Gi.y * s20, Gi.z * s20);
-      float3 H = make_float3(Hi.x * s20, Hi.y * s20, Hi.z * s20);
-      float3 A = make_float3((float)Ax * s40, (float)Ay * s40, (float)Az * s40);
-      float3 B = make_float3((float)Bx * s40, (float)By * s40, (float)Bz * s40);
-      float A2 = na_dot(A, A), B2 = na_dot(B, B);
-      float rg = sqrtf((float)((long long)Gi.x * Gi.x + (long long)Gi.y * Gi.y + (long long)Gi.z * Gi.z) * s40);
-      float rab = rsqrtf(A2 * B2);
-      float cs = na_dot(A, B) * rab;
-      // sin phi = -|G| (F . B) / (|A||B|), with F . B exact in 128 bits
-      __int128 tp = (__int128)Fi.x * Bx + (__int128)Fi.y * By + (__int128)Fi.z * Bz;
-      int e2 = -60;
-      while (tp > (__int128)0x3FFFFFFFFFFFFFFFll || tp < -(__int128)0x3FFFFFFFFFFFFFFFll) {
-        tp >>= 8;
-        e2 += 8;
+      const int a = ang[4 * k], b = ang[4 * k + 1], c = ang[4 * k + 2], t = ang[4 * k + 3];
+      if (b < 0 || b >= N) {
+        na_flag(scratch);
+        continue;
       }
-      float sn = -rg * ldexpf((float)(long long)tp, e2) * rab;
-      float K = ff.dih_k[t], dd = ff.dih_d[t];
-      float mdE = K * dd * sn;
-      float fg = (float)((long long)Fi.x * Gi.x + (long long)Fi.y * Gi.y + (long long)Fi.z * Gi.z) * s40;
-      float hg = (float)((long long)Hi.x * Gi.x + (long long)Hi.y * Gi.y + (long long)Hi.z * Gi.z) * s40;
-      float c1 = -rg / A2, c4 = rg / B2, cbA = rg / A2 + fg / (A2 * rg), cbB = -hg / (B2 * rg);
-      float ccA = -fg / (A2 * rg), ccB = hg / (B2 * rg) - rg / B2;
-      float3 Fa = make_float3(mdE * c1 * A.x, mdE * c1 * A.y, mdE * c1 * A.z);
-      float3 Fd = make_float3(mdE * c4 * B.x, mdE * c4 * B.y, mdE * c4 * B.z);
-      float3 Fb = make_float3(mdE * (cbA * A.x + cbB * B.x), mdE * (cbA * A.y + cbB * B.y),
-                              mdE * (cbA * A.z + cbB * B.z));
-      float3 Fc = make_float3(mdE * (ccA * A.x + ccB * B.x), mdE * (ccA * A.y + ccB * B.y),
-                              mdE * (ccA * A.z + ccB * B.z));
-      na_add(force, ia, Fa);
-      na_add(force, ib, Fb);
-      na_add(force, ic, Fc);
-      na_add(force, id, Fd);
-      acc.e[0] += (double)(K * (1.0f + dd * cs));
-      acc.vir(F, Fa, 1.f);
-      acc.vir(make_float3(-G.x, -G.y, -G.z), Fc, 1.f);
-      acc.vir(make_float3(H.x - G.x, H.y - G.y, H.z - G.z), Fd, 1.f);
+      const int r = na_rep(off, R, b);
+      const long long lo = off[r], hi = off[r + 1];
+      if (!na_in(a, lo, hi, N) || !na_in(b, lo, hi, N) || !na_in(c, lo, hi, N) || (unsigned)t >= 16u) {
+        na_flag(scratch);
+        continue;
+      }
+      acc.to(r, scratch);
+      const AngleTerm o = angle_term_forces(ff, t, pos[a], pos[b], pos[c], (int)box[r]);
+      na_add(force, a, o.Fa);
+      na_add(force, b, make_float3(-o.Fa.x - o.Fc.x, -o.Fa.y - o.Fc.y, -o.Fa.z - o.Fc.z));
+      na_add(force, c, o.Fc);
+      acc.e[0] += (double)o.E;
+      acc.vir(o.ra, o.Fa, 1.f);
+      acc.vir(o.rc, o.Fc, 1.f);
+    } else {
+      const long long m = k - na;
+      const int ia = dih[5 * m], ib = dih[5 * m + 1], ic = dih[5 * m + 2], id = dih[5 * m + 3], t = dih[5 * m + 4];
+      if (ib < 0 || ib >= N) {
+        na_flag(scratch);
+        continue;
+      }
+      const int r = na_rep(off, R, ib);
+      const long long lo = off[r], hi = off[r + 1];
+      if (!na_in(ia, lo, hi, N) || !na_in(ib, lo, hi, N) || !na_in(ic, lo, hi, N) || !na_in(id, lo, hi, N) ||
+          (unsigned)t >= 16u) {
+        na_flag(scratch);
+        continue;
+      }
+      acc.to(r, scratch);
+      const DihedralTerm o = dihedral_term_forces(ff, t, pos[ia], pos[ib], pos[ic], pos[id], (int)box[r]);
+      na_add(force, ia, o.Fa);
+      na_add(force, ib, o.Fb);
+      na_add(force, ic, o.Fc);
+      na_add(force, id, o.Fd);
+      acc.e[0] += (double)o.E;
+      // relative to B: r_A - r_B = F, r_C - r_B = -G, r_D - r_B = H - G
+      acc.vir(o.F, o.Fa, 1.f);
+      acc.vir(make_float3(-o.G.x, -o.G.y, -o.G.z), o.Fc, 1.f);
+      acc.vir(make_float3(o.H.x - o.G.x, o.H.y - o.G.y, o.H.z - o.G.z), o.Fd, 1.f);
     }
   }
-  acc.flush_warp(ev);
+  acc.flush_warp(scratch);
 }
 
 __global__ void na_copy(const double* src, double* dst, int n) {
@@ -219,7 +206,9 @@ __global__ void na_copy(const double* src, double* dst, int n) {
 }
 
 // Device address of the scratch array, looked up once per device (host code
-// may not use the array's name as a device pointer).
+// may not use the array's name as a device pointer).  The address belongs to
+// the device's primary context: no call may follow a cudaDeviceReset of that
+// device in the same process.
 std::mutex g_mu;
 double* g_scratch[256] = {};
 
@@ -231,7 +220,7 @@ cudaError_t scratch_for_current_device(double** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_ev);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch[dev] = (double*)p;
   }
@@ -257,6 +246,10 @@ extern "C" dynbond_status dynbond_forces_noalloc(const int32_t* d_pos, const uin
   if (!ff || !d_ev || !d_bead_offset || !d_box_q || (n_beads && (!d_pos || !d_slots || !d_force)) ||
       (n_angles && !d_angles) || (n_dihedrals && !d_dihedrals))
     return DYNBOND_EINVAL;
+  if ((n_beads && (((uintptr_t)d_pos | (uintptr_t)d_slots | (uintptr_t)d_force) & 15u)) ||
+      ((uintptr_t)d_bead_offset | (uintptr_t)d_box_q | (uintptr_t)d_ev) & 7u ||
+      ((uintptr_t)d_angles | (uintptr_t)d_dihedrals) & 3u)
+    return DYNBOND_EINVAL;
   double* scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return DYNBOND_ECUDA;
@@ -271,10 +264,15 @@ extern "C" dynbond_status dynbond_forces_noalloc(const int32_t* d_pos, const uin
         n_replicas, n_beads, f, (float4*)d_force, scratch);
   if (n_angles + n_dihedrals)
     na_angles_dihedrals<<<(int)std::min<long long>((n_angles + n_dihedrals + 255) / 256, 1024), 256, 0, s>>>(
-        (const int4*)d_pos, (const long long*)d_bead_offset, (const long long*)d_box_q, n_replicas, d_angles,
-        n_angles, d_dihedrals, n_dihedrals, f, (float4*)d_force, scratch);
+        (const int4*)d_pos, (const long long*)d_bead_offset, (const long long*)d_box_q, n_replicas, n_beads,
+        d_angles, n_angles, d_dihedrals, n_dihedrals, f, (float4*)d_force, scratch);
   na_copy<<<(nev + 255) / 256, 256, 0, s>>>(scratch, d_ev, nev);
   e = cudaGetLastError();
   if (e != cudaSuccess) return DYNBOND_ECUDA;
-  return DYNBOND_OK;
+  // the error word: read back once the kernels are done
+  unsigned long long bad = 0;
+  e = cudaMemcpyAsync(&bad, scratch + NA_ERR_SLOT, sizeof(bad), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return DYNBOND_ECUDA;
+  return bad ? DYNBOND_EINVAL : DYNBOND_OK;
 }

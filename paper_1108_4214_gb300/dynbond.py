@@ -29,7 +29,7 @@ STAT_NAMES = [
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
            "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
            "dynbond_forces_noalloc", "dynbond_autotune", "dynbond_md_create", "dynbond_md_advance",
-           "dynbond_md_destroy", "dynbond_topology_hash", "dynbond_get_tuning"]
+           "dynbond_md_destroy", "dynbond_topology_hash", "dynbond_get_tuning", "dynbond_md_pair_forces"]
 NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
@@ -123,6 +123,8 @@ def load() -> ctypes.CDLL:
     L.dynbond_md_create.argtypes = [c_p, c_p, ctypes.POINTER(c_p)]
     L.dynbond_md_advance.restype = c_i32
     L.dynbond_md_advance.argtypes = [c_p, c_p, c_p, c_i64, c_u64, c_p]
+    L.dynbond_md_pair_forces.restype = c_i32
+    L.dynbond_md_pair_forces.argtypes = [c_p, c_p, c_p, c_u64, c_p]
     L.dynbond_md_destroy.restype = None
     L.dynbond_md_destroy.argtypes = [c_p]
     L.dynbond_topology_hash.restype = c_i32
@@ -342,24 +344,36 @@ def forcefield_struct(f) -> ForceField:
 
 def forces_noalloc(pos, slots, bead_offset, box_q, angles, dihedrals, forcefield, force=None, ev=None, stream=None):
     """dynbond_forces_noalloc: bonded forces of a caller-supplied topology
-    without any allocation inside the library.  All tensors are CUDA tensors:
-    pos int32 [N, 4], slots uint32-as-int32 [N, 4] (partner << 4 | stored
-    type, 0 = empty), bead_offset int64 [R+1], box_q int64 [R], angles int32
-    [na, 4], dihedrals int32 [nd, 5].  Returns (force float32 [N, 4], ev
-    float64 [R, 7]); the outputs may be preallocated by the caller."""
+    without any allocation inside the library.  All tensors are contiguous
+    CUDA tensors on one device: pos int32 [N, 4], slots int32 [N, 4] (the
+    uint32 words partner << 4 | stored type, 0 = empty), bead_offset int64
+    [R+1], box_q int64 [R], angles int32 [na, 4], dihedrals int32 [nd, 5].
+    Returns (force float32 [N, 4], ev float64 [R, 7]); the outputs may be
+    preallocated by the caller (same shapes and dtypes).  Raises DynbondError
+    with status EINVAL when a bead id or type of the topology is out of range
+    (those terms are skipped by the library)."""
     import torch
     L = load()
-    N, R = pos.shape[0], box_q.shape[0]
+    N, R = int(pos.shape[0]), int(box_q.shape[0])
     if force is None:
         force = torch.empty((N, 4), dtype=torch.float32, device=pos.device)
     if ev is None:
         ev = torch.empty((R, 7), dtype=torch.float64, device=pos.device)
+    want = ((pos, torch.int32, (N, 4)), (slots, torch.int32, (N, 4)), (bead_offset, torch.int64, (R + 1,)),
+            (box_q, torch.int64, (R,)), (angles, torch.int32, (int(angles.shape[0]), 4)),
+            (dihedrals, torch.int32, (int(dihedrals.shape[0]), 5)), (force, torch.float32, (N, 4)),
+            (ev, torch.float64, (R, 7)))
+    for k, (t, dt, shape) in enumerate(want):
+        if not (t.is_cuda and t.device == pos.device and t.dtype == dt and tuple(t.shape) == shape
+                and t.is_contiguous()):
+            raise ValueError(f"forces_noalloc argument {k}: need a contiguous {dt} CUDA tensor of shape {shape} "
+                             f"on {pos.device}, got {t.dtype} {tuple(t.shape)} on {t.device}")
     ff = forcefield_struct(forcefield)
     st = L.dynbond_forces_noalloc(c_p(_ptr(pos)), c_p(_ptr(slots)), c_p(_ptr(bead_offset)), c_p(_ptr(box_q)), R, N,
                                   c_p(_ptr(angles)), angles.shape[0], c_p(_ptr(dihedrals)), dihedrals.shape[0],
                                   ctypes.byref(ff), c_p(_ptr(force)), c_p(_ptr(ev)), _stream_handle(stream))
     if st != 0:
-        raise DynbondError(st, "dynbond_forces_noalloc failed")
+        raise DynbondError(st, "dynbond_forces_noalloc failed (sizes, alignment, or a bead id / type out of range)")
     return force, ev
 
 
@@ -381,6 +395,17 @@ class MD:
                                        c_p(_ptr(ev)))
         if st != 0:
             raise DynbondError(st, "dynbond_md_advance failed")
+
+    def pair_forces(self, pos, vel, step: int, force=None):
+        """dynbond_md_pair_forces: the DPD pair forces (float32 [N, 4]) at
+        pos, vel for step index `step`."""
+        torch = self.ctx._torch
+        if force is None:
+            force = torch.empty((pos.shape[0], 4), dtype=torch.float32, device=pos.device)
+        st = self.L.dynbond_md_pair_forces(self.h, c_p(_ptr(pos)), c_p(_ptr(vel)), int(step), c_p(_ptr(force)))
+        if st != 0:
+            raise DynbondError(st, "dynbond_md_pair_forces failed")
+        return force
 
     def close(self):
         if getattr(self, "h", None):

@@ -517,6 +517,29 @@ def config3(n_replicas: int = 512, seed: int = 3) -> System:
     )
 
 
+def replica_batch(n_replicas: int, n_strands: int = 2, n_nt: int = 8, n_duplex: int = 1, density: float = 0.5,
+                  seed: int = 9) -> System:
+    """n_replicas equal replicas of n_strands strands of n_nt nucleotides at
+    the given bead density, the first 2 n_duplex strands of each paired into
+    hybridized duplexes; the 2-bead DNA rules.  Many tiny replicas exercise
+    per-replica bookkeeping at its limits."""
+    rng = np.random.default_rng(seed)
+    n = 2 * n_nt * n_strands
+    box = (n / density) ** (1.0 / 3.0)
+    pos, types, bonds = [], [], []
+    for r in range(n_replicas):
+        p, t, b = _replica_strands(rng, n_strands, n_nt, box, r * n, n_duplex=n_duplex)
+        pos.append(p)
+        types.append(t)
+        bonds.append(b)
+    return System(
+        name=f"batch-{n_replicas}x{n}", bead_offset=np.arange(n_replicas + 1, dtype=np.int64) * n,
+        box_q=np.full(n_replicas, int(np.rint(box * QSCALE)), np.int64), types=np.concatenate(types),
+        bonds=np.concatenate(bonds), rules=rules_dna2(), pos0=np.concatenate(pos), seed=seed,
+        rng_stream=np.arange(n_replicas, dtype=np.uint32), params=default_params(seed),
+    )
+
+
 def sub_replicas(sysb: System, idx) -> System:
     """The replicas idx of a batched system as a batch of their own (same
     per-replica RNG streams and probability scales)."""

@@ -82,3 +82,29 @@ def test_dpd_loop_4m_beads_ten_thousand_steps():
     worst = replay(s, res)
     print("dpd-4M: kT %.4f, md %.1f s, dynbond_step %.1f s, max ev error %.3g, bonds first/last %s %s" % (
         res["kT"], res["seconds_md"], res["seconds_step"], worst, res["counts"][0], res["counts"][-1]))
+
+
+@pytest.mark.parametrize("step", [0, 7])
+def test_dpd_pair_forces_match_the_fp64_oracle(step):
+    """One evaluation of the DPD pair forces of Sec. 3 (F^C + F^D + F^R, w(r)
+    = 1 - r / r_c, sigma = sqrt(2 kT gamma), pairs fewer than 3 bonds apart
+    excluded) on a snapshot at the paper's solvent density 3 with random
+    velocities: the GPU's FP32 forces against the oracle's FP64 brute force,
+    same Gaussian numbers (Philox on pair and step)."""
+    from paper_1108_4214_gb300 import dynbond as D
+    from parity import FORCE_TOL, force_error
+    s = W.dna_system("dpd-4k", 64, 32, 3.0, 33, W.rules_dna2(), n_duplex=16)
+    ctx = D.Context(s)
+    md = D.MD(ctx, a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.01, seed=987654321)
+    snap = s.snapshot(0)
+    rng = np.random.default_rng(step)
+    vel = np.zeros((s.n_beads, 4), np.float32)
+    vel[:, :3] = rng.normal(size=(s.n_beads, 3))
+    f = md.pair_forces(torch.from_numpy(snap).cuda(), torch.from_numpy(vel).cuda(), step).cpu().numpy()
+    fr = O.Oracle(s).dpd_forces(snap, vel[:, :3].astype(np.float64), a=25.0, gamma=4.5, kT=1.0, rc=1.0, dt=0.01,
+                                seed=987654321, step=step)
+    assert np.all(f[:, 3] == 0)
+    err = force_error(f, fr)
+    assert err <= FORCE_TOL, err
+    md.close()
+    ctx.close()

@@ -1,10 +1,7 @@
-"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
-
-Topology (bonds with the type each end stores, angles, dihedrals) and every
-per-replica statistic must match bit for bit after every call; bonded forces
-(FP32 per term) must match the FP64 oracle within
-|f_gpu - f_ref| <= FORCE_TOL * (|f_ref| + f_rms) per component, and the FP64-
-reduced energy / virial within EV_TOL of the largest magnitude."""
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle (the
+bar is stated in tests/parity.py: topology and statistics bit for bit,
+forces within 1e-5 max(|f_ref|, f_rms) per component, energy / virial within
+2e-6 of the largest magnitude per replica)."""
 
 import ctypes
 import os
@@ -16,67 +13,10 @@ from oracle import oracle as O
 from paper_1108_4214_gb300 import workloads as W
 
 from helpers import golden, golden_rules, half_bond_pair, ladder_1bead_positions, make_system
+from parity import compare_forces, compare_topology, dynbond, run_parity
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-FORCE_TOL = 2e-5
-EV_TOL = 2e-6
-
-
-def dynbond():
-    from paper_1108_4214_gb300 import dynbond as D
-    return D
-
-
-def assert_same(a, b, what):
-    if a.shape != b.shape or not np.array_equal(a, b):
-        sa = {tuple(x) for x in a.tolist()}
-        sb = {tuple(x) for x in b.tolist()}
-        raise AssertionError(f"{what}: gpu {a.shape} vs oracle {b.shape}; only gpu {sorted(sa - sb)[:5]} "
-                             f"only oracle {sorted(sb - sa)[:5]}")
-
-
-def compare_topology(ctx, o, where):
-    for name, g, r in zip(("bonds", "angles", "dihedrals"), ctx.topology(), o.topology()):
-        assert_same(g, r, f"{where}: {name}")
-
-
-def compare_forces(ctx, o, snap, where):
-    pos = torch.from_numpy(snap).cuda()
-    f, ev = ctx.forces(pos)
-    f = f.cpu().numpy()
-    ev = ev.cpu().numpy()
-    fr, evr = o.forces(snap)
-    assert np.all(f[:, 3] == 0)
-    err = np.abs(f[:, :3].astype(np.float64) - fr)
-    rms = np.sqrt(np.mean(fr ** 2))
-    worst = (err / (np.abs(fr) + rms)).max()
-    assert worst <= FORCE_TOL, f"{where}: force error {worst:.3g} (x (|f| + rms))"
-    scale = np.abs(evr).max(axis=1, keepdims=True)
-    evw = (np.abs(ev - evr) / scale).max()
-    assert evw <= EV_TOL, f"{where}: energy/virial error {evw:.3g}"
-    return worst, evw
-
-
-def run_parity(system, n_calls, snaps=None, params=None, flags=0, forces=True, start=0):
-    o = O.Oracle(system, params=params)
-    ctx = dynbond().Context(system, params=params, flags=flags)
-    compare_topology(ctx, o, "initial")
-    worst = []
-    for k in range(n_calls):
-        snap = snaps[k] if snaps is not None else system.snapshot(k)
-        st_g = ctx.step(torch.from_numpy(snap).cuda(), start + k, stats=True)
-        st_o = o.step(snap, start + k)
-        if not np.array_equal(st_g, st_o):
-            diff = {O.STAT_NAMES[j]: (st_g[:, j].tolist(), st_o[:, j].tolist())
-                    for j in range(len(O.STAT_NAMES)) if not np.array_equal(st_g[:, j], st_o[:, j])}
-            raise AssertionError(f"call {k}: statistics differ {diff}")
-        compare_topology(ctx, o, f"call {k}")
-        if forces:
-            worst.append(compare_forces(ctx, o, snap, f"call {k}"))
-    ctx.close()
-    return o, worst
 
 
 # ---------------------------------------------------------------------------

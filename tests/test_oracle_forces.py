@@ -53,6 +53,69 @@ def test_harmonic_angle_closed_forms():
         assert (np.cross(ra, Fa)[2] < 0) == (th < th0)
 
 
+def _bent(delta, rng, la=1.1, lc=0.9):
+    """ra, rc of an angle theta = pi - delta at the centre bead, randomly
+    oriented (ra along a random unit vector, rc bent away from -ra by delta
+    within a random plane)."""
+    M = rot(rng)
+    ra = la * np.array([1.0, 0.0, 0.0])
+    rc = lc * np.array([-np.cos(delta), np.sin(delta), 0.0])
+    return M @ ra, M @ rc
+
+
+@pytest.mark.parametrize("delta", [1e-2, 1e-4, 1e-6])
+def test_harmonic_angle_near_straight_with_theta0_180(delta):
+    """The backbone angle of Sec. 3 (theta0 = 180 deg) close to straight: E =
+    K (pi - theta)^2 is smooth there, |F_A| = 2 K (pi - theta) / |r_A| exactly
+    (tangential), and the forces are minus the finite-difference gradient of
+    the energy at pi - theta = 1e-2, 1e-4 and 1e-6 (a division by a clamped
+    sin theta would shrink them by up to three orders of magnitude)."""
+    rng = np.random.default_rng(int(-np.log10(delta)))
+    K = 20.0
+    ra, rc = _bent(delta, rng)
+    E, Fa, Fc = O.angle_harmonic(ra, rc, K, np.pi)
+    assert E == pytest.approx(K * delta ** 2, rel=1e-8)
+    assert np.linalg.norm(Fa) == pytest.approx(2 * K * delta / 1.1, rel=1e-8)
+    assert np.linalg.norm(Fc) == pytest.approx(2 * K * delta / 0.9, rel=1e-8)
+    P = np.stack([ra, np.zeros(3), rc]) + 5.0
+
+    def Eharm(x):
+        x = x.reshape(3, 3)
+        return O.angle_harmonic(x[0] - x[1], x[2] - x[1], K, np.pi)[0]
+    g = _fd(Eharm, P.ravel(), h=1e-6).reshape(3, 3)
+    F = np.stack([Fa, -(Fa + Fc), Fc])
+    assert np.allclose(F, -g, rtol=1e-5, atol=1e-5 * np.abs(F).max())
+
+
+@pytest.mark.parametrize("delta", [1e-2, 1e-4])
+def test_harmonic_angle_near_straight_with_theta0_90(delta):
+    """The backbone-hybridization angle of Sec. 3 (theta0 = 90 deg) close to
+    straight: |F_A| = 2 K (theta - theta0) / |r_A| stays finite and the forces
+    are minus the energy gradient (finite differences with a step well below
+    the bend, where the energy is smooth)."""
+    rng = np.random.default_rng(7)
+    K = 1.0
+    ra, rc = _bent(delta, rng)
+    E, Fa, Fc = O.angle_harmonic(ra, rc, K, np.pi / 2)
+    assert E == pytest.approx(K * (np.pi / 2 - delta) ** 2, rel=1e-12)
+    assert np.linalg.norm(Fa) == pytest.approx(2 * K * (np.pi / 2 - delta) / 1.1, rel=1e-8)
+    P = np.stack([ra, np.zeros(3), rc]) + 5.0
+
+    def Eharm(x):
+        x = x.reshape(3, 3)
+        return O.angle_harmonic(x[0] - x[1], x[2] - x[1], K, np.pi / 2)[0]
+    g = _fd(Eharm, P.ravel(), h=delta * 1e-3).reshape(3, 3)
+    F = np.stack([Fa, -(Fa + Fc), Fc])
+    assert np.allclose(F, -g, rtol=1e-5, atol=1e-6)
+
+
+def test_harmonic_angle_exactly_straight_has_no_plane():
+    E, Fa, Fc = O.angle_harmonic([1.0, 0, 0], [-2.0, 0, 0], 20.0, np.pi)
+    assert E == 0.0 and not Fa.any() and not Fc.any()
+    E, Fa, Fc = O.angle_harmonic([1.0, 0, 0], [-2.0, 0, 0], 1.0, np.pi / 2)
+    assert E == pytest.approx((np.pi / 2) ** 2) and not Fa.any() and not Fc.any()
+
+
 def _fd(fun, x, h=1e-6):
     g = np.zeros_like(x)
     for i in range(x.size):
@@ -81,7 +144,7 @@ def test_finite_differences_and_newton3(seed):
     g = _fd(Eang, P.ravel()).reshape(3, 3)
     Fb = -(Fa + Fc)
     assert np.allclose(np.stack([Fa, Fb, Fc]), -g, rtol=1e-6, atol=1e-7)
-    # harmonic angle (random configurations stay far from the straight-angle clamp)
+    # harmonic angle
 
     def Eharm(x):
         x = x.reshape(3, 3)
