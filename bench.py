@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-baseline-seconds", type=float, default=12.0)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-melt", action="store_true", help="skip the 16M-bead melting leg")
     ap.add_argument("--cell-scale", type=int, default=0,
                     help="fixed cell edge (x the creation reach) instead of autotuning, e.g. for profiler runs, "
                          "under which the autotuner's timings mean nothing")
@@ -208,12 +209,52 @@ def kernel_bytes(phase, N, st, na_before, nd_before):
         return 16 * N + 16 * N + 16 * N  # positions, slots, forces
     if phase == "angle_dihedral_forces":  # records + one force read-modify-write per role
         return 16 * (st["n_angles"] + st["n_dihedrals"]) + 2 * 16 * (3 * st["n_angles"] + 4 * st["n_dihedrals"])
-    if phase == "candidates":  # per reactive bead (N / 2 bases, an upper bound on the binned ones): its
-        # sorted entry and its slots (16 B each); per candidate pair: one 16-B list entry at each end
-        return 16 * N // 2 + 16 * N // 2 + 16 * 2 * st["candidates"]
+    if phase == "candidates":  # the search step's bytes: positions for the search (16 B per bead), the
+        # reactive beads' slots for the exclusion and maxbond tests (16 B per base, N / 2 of them), and
+        # the candidate edges written and read (16 B at each end of each pair)
+        return 16 * N + 16 * (N // 2) + 32 * st["candidates"]
     if phase == "cells":  # per reactive bead: position read and sorted entry written (16 B each); the cell of every bead
         return 16 * N // 2 * 2 + 8 * N
     return None
+
+
+def dominant_roofline(phases, N, stats, na_before, nd_before, tuning, peak, peak_kind, traffic_ok=True):
+    """Roofline of the phase with the longest device time (setup excluded):
+    its algorithmic bytes per launch over its event time."""
+    if not phases:
+        return None
+    dom = max((k for k in phases if not k.endswith("setup")), key=lambda k: phases[k])
+    kb = kernel_bytes(dom, N, stats, na_before, nd_before)
+    if kb is None or phases[dom] <= 0:
+        return dict(kernel=phase_kernel(dom, tuning), ms_per_launch=phases[dom], bytes_per_launch=None)
+    ach = kb / (phases[dom] * 1e-3) / 1e9
+    return dict(bound="hbm", kernel=phase_kernel(dom, tuning), achieved=ach, peak=peak, unit="GB/s",
+                frac=ach / peak, peak_source=peak_kind, bytes_per_launch=kb, ms_per_launch=phases[dom],
+                traffic=recorded_traffic(dom, tuning) if traffic_ok else None)
+
+
+def profiled_phases(system, snaps, warmup, steps, flush, stream, geo=None):
+    """Mean per-phase device times (ms) of a context created with
+    DYNBOND_FLAG_PROFILE over the timed calls (events between the phases)."""
+    import torch
+
+    from paper_1108_4214_gb300 import dynbond
+    dev = snaps[0].device
+    ctx = dynbond.Context(system, flags=dynbond.FLAG_PROFILE, stream=stream, params=geo)
+    if not geo:
+        ctx.autotune(snaps[0])
+    f = torch.empty((system.n_beads, 4), dtype=torch.float32, device=dev)
+    ev = torch.empty((system.n_replicas, 7), dtype=torch.float64, device=dev)
+    phases = {}
+    for k in range(warmup + steps):
+        flush.zero_()
+        ctx.step(snaps[k], k)
+        ctx.forces(snaps[k], f, ev)
+        if k >= warmup:
+            for name, ms in ctx.phase_times().items():
+                phases.setdefault(name, []).append(ms)
+    ctx.close()
+    return {k: float(np.mean(v)) for k, v in phases.items()}
 
 
 def run_gpu(args):
@@ -244,10 +285,7 @@ def run_gpu(args):
         ctx.step(snaps[k], k)
         ctx.forces(snaps[k], force, ev)
     ctx.sync()
-    phases = {}
-    stats_all = []
     times = []
-    prev_counts = None
     with ClockSampler(dev.index) as clk:
         if world > 1:
             dist.barrier()
@@ -269,17 +307,7 @@ def run_gpu(args):
     # per-phase device times from a second context that records events
     # between the phases (events inside the replayed work serialize the
     # kernels, so the headline above is timed without them)
-    ctx_p = dynbond.Context(s, flags=dynbond.FLAG_PROFILE, stream=stream, params=geo)
-    if not geo:
-        ctx_p.autotune(snaps[0])
-    for k in range(Wm + K):
-        flush.zero_()
-        ctx_p.step(snaps[k], k)
-        ctx_p.forces(snaps[k], force, ev)
-        if k >= Wm:
-            for name, ms in ctx_p.phase_times().items():
-                phases.setdefault(name, []).append(ms)
-    ctx_p.close()
+    phases = profiled_phases(s, snaps, Wm, K, flush, stream, geo)
     # statistics of one more (untimed) call for the algorithmic byte counts
     na_before, nd_before = ctx.topology()[1].shape[0], ctx.topology()[2].shape[0]
     st = ctx.step(snaps[-1], Wm + K, stats=True)
@@ -287,7 +315,7 @@ def run_gpu(args):
     ctx.forces(snaps[-1], force, ev)
     ctx.sync()
     value = whole_job_value(N, K, world, total_ms / 1e3)
-    result = dict(value=value, ms=total_ms / K, N=N, R=R, phases={k: float(np.mean(v)) for k, v in phases.items()},
+    result = dict(value=value, ms=total_ms / K, N=N, R=R, phases=phases,
                   stats=stats, na_before=na_before, nd_before=nd_before, clocks=clk.summary(), rank=rank,
                   world=world, name=s.name, tuning=tuning)
 
@@ -392,10 +420,65 @@ def run_batched(steps: int, warmup: int):
     alg = algorithmic_bytes((na0, nd0), stats, N, full.n_replicas)
     peak, peak_kind = peaks()
     ach = alg / (t_b / steps * 1e-3) / 1e9
+    phases = profiled_phases(full, pos_all, warmup, steps, flush, stream)
     return dict(workload=full.name, replicas=full.n_replicas, beads=N, steps=steps, warmup=warmup,
                 value=vb, ms_per_step=t_b / steps, plain_value=vp, plain_ms_per_step=t_p / steps,
                 speedup=vb / vp, tuning=tuning, unit=UNIT,
                 plain="one context per replica, called one after another on one stream",
+                phases_ms=phases,
+                roofline=dominant_roofline(phases, N, stats, na0, nd0, tuning, peak, peak_kind, traffic_ok=False),
+                step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=ach, peak=peak, unit="GB/s",
+                                   frac=ach / peak, peak_source=peak_kind))
+
+
+def run_melt(steps: int, warmup: int):
+    """The high-turnover melting workload at its full size (16,777,216 beads,
+    131,072 strands x 64 nt, half of them in duplexes; form p 0.9, break p
+    0.5): step + forces per call with CUDA events, L2 flushed between calls,
+    per-phase times from a profiled context, roofline of the dominant phase."""
+    import torch
+
+    from paper_1108_4214_gb300 import dynbond
+    from paper_1108_4214_gb300 import workloads as W
+    s = W.config4()
+    N, R = s.n_beads, s.n_replicas
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    snaps = [torch.from_numpy(x).to(dev) for x in s.snapshots(0, steps + warmup)]
+    ctx = dynbond.Context(s, stream=stream)
+    tuning = ctx.autotune(snaps[0])
+    f = torch.empty((N, 4), dtype=torch.float32, device=dev)
+    ev = torch.empty((R, 7), dtype=torch.float64, device=dev)
+    for k in range(warmup):
+        ctx.step(snaps[k], k)
+        ctx.forces(snaps[k], f, ev)
+    torch.cuda.synchronize()
+    total = 0.0
+    for k in range(warmup, warmup + steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.step(snaps[k], k)
+        ctx.forces(snaps[k], f, ev)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    topo = ctx.topology()
+    na0, nd0 = topo[1].shape[0], topo[2].shape[0]
+    st = ctx.step(snaps[-1], warmup + steps, stats=True)
+    ctx.forces(snaps[-1], f, ev)
+    stats = {n: int(st[:, j].sum()) for j, n in enumerate(dynbond.STAT_NAMES)}
+    ctx.sync()
+    ctx.close()
+    phases = profiled_phases(s, snaps, warmup, steps, flush, stream)
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes((na0, nd0), stats, N, R)
+    ach = alg / (total / steps * 1e-3) / 1e9
+    return dict(workload=s.name, beads=N, steps=steps, warmup=warmup, value=N * steps / (total / 1e3), unit=UNIT,
+                ms_per_step=total / steps, tuning=tuning, phases_ms=phases, stats_last_call=stats,
+                roofline=dominant_roofline(phases, N, stats, na0, nd0, tuning, peak, peak_kind, traffic_ok=False),
                 step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=ach, peak=peak, unit="GB/s",
                                    frac=ach / peak, peak_source=peak_kind))
 
@@ -462,16 +545,11 @@ def main():
     if res["rank"] != 0:
         return
     batched = None if args.no_batched or res["world"] > 1 else run_batched(10, 3)
+    melt = None if args.no_melt or res["world"] > 1 else run_melt(5, 3)
     peak, peak_kind = peaks()
     ph = res["phases"]
-    dom = max((k for k in ph if not k.endswith("setup")), key=lambda k: ph[k])
-    kb = kernel_bytes(dom, res["N"], res["stats"], res["na_before"], res["nd_before"])
-    roof = None
-    if kb is not None and ph[dom] > 0:
-        ach = kb / (ph[dom] * 1e-3) / 1e9
-        roof = dict(bound="hbm", kernel=phase_kernel(dom, res["tuning"]), achieved=ach, peak=peak, unit="GB/s",
-                    frac=ach / peak, peak_source=peak_kind, bytes_per_launch=kb, ms_per_launch=ph[dom],
-                    traffic=recorded_traffic(dom, res["tuning"]))
+    roof = dominant_roofline(ph, res["N"], res["stats"], res["na_before"], res["nd_before"], res["tuning"], peak,
+                             peak_kind)
     alg = algorithmic_bytes((res["na_before"], res["nd_before"]), res["stats"], res["N"], res["R"])
     step_gbs = alg / (res["ms"] * 1e-3) / 1e9
     rank, world, _ = dist_env()
@@ -488,7 +566,7 @@ def main():
         step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=step_gbs, peak=peak, unit="GB/s",
                            frac=step_gbs / peak, peak_source=peak_kind),
         phases_ms=ph, cpu_baseline=cpu, e2e=res["e2e"], gpu_launches=kernels_per_step * args.steps,
-        clocks=res["clocks"], stats_last_call=res["stats"], batched=batched,
+        clocks=res["clocks"], stats_last_call=res["stats"], batched=batched, melt=melt,
     )
     print(json.dumps(line), flush=True)
 

@@ -106,8 +106,10 @@ enum {
   DYNBOND_FLAG_NO_GRAPH = 1,    /* launch kernels one by one instead of replaying a CUDA graph */
   DYNBOND_FLAG_PROFILE = 2,     /* record CUDA events between phases (dynbond_phase_times) */
   DYNBOND_FLAG_NO_AUTOTUNE = 4, /* with cell_scale 0: use cells as wide as the reach, never autotune */
-  DYNBOND_FLAG_NO_PDL = 8       /* launch each kernel only after the previous one ends (no programmatic
+  DYNBOND_FLAG_NO_PDL = 8,      /* launch each kernel only after the previous one ends (no programmatic
                                    dependent launch); results are identical either way */
+  DYNBOND_FLAG_GLOBAL_SEARCH = 16 /* candidate search walks the cell lists in global memory instead of
+                                   staging tiles of cell columns in shared memory; results are identical */
 };
 
 /*
@@ -315,8 +317,10 @@ dynbond_status dynbond_topology_hash(dynbond_ctx* ctx, uint64_t* h_out);
  * Autotuning of launch geometry (not part of the paper): the cell edge along x
  * and y (1, 1.25, 1.5, 2 or 3 x the largest creation distance), the z edge (the
  * x / y edge divided by 1, 2 or 4; grids larger than the one allocated at
- * creation are skipped) and the bead-pass grid size (4, 8 or 16 blocks per
- * SM) are chosen by timing the front of a call (cell binning,
+ * creation are skipped), the candidate search (tiles of cell columns staged
+ * in shared memory, or the per-bead search in global memory) and the
+ * bead-pass grid size (4, 8 or 16 blocks per SM) are chosen by timing the
+ * front of a call (cell binning,
  * breakage nomination and candidate search, which write scratch only; best of
  * three runs) on the positions d_pos; the fastest is kept and the captured work
  * is rebuilt.  No choice changes results.
@@ -331,6 +335,7 @@ typedef struct dynbond_tuning {
   int32_t tuned;
   int32_t cell_zdiv; /* z edge = x / y edge / cell_zdiv */
   int32_t octant;    /* 1: columns at least twice the reach wide, the search reads 2 x 2 columns */
+  int32_t tiles;     /* 1: the search stages tiles of cell columns in shared memory */
 } dynbond_tuning;
 
 dynbond_status dynbond_autotune(dynbond_ctx* ctx, const int32_t* d_pos, dynbond_tuning* out);

@@ -60,6 +60,15 @@ struct dynbond_ctx {
   long long* d_cb = nullptr;
   dynbond_tuning tuning{};
   unsigned long long* d_hash = nullptr;  // per-replica topology hashes
+  // candidate search by staged tiles (k_candidates_tile): work items of the
+  // current geometry, or none (global-memory search)
+  int4* d_ctile = nullptr;
+  long long ctile_cap = 0;
+  bool cand_tiles = false;      // the search runs on staged tiles (tiles_avail && tiles_on)
+  bool tiles_avail = false;     // the current geometry has staged work items
+  bool tiles_on = false;        // autotuner's choice between staged and global search (global until timed)
+  bool global_search = false;   // DYNBOND_FLAG_GLOBAL_SEARCH
+  int grid_ctile = 0;
   bool tuned = false;
 };
 
@@ -293,7 +302,7 @@ cudaError_t launch(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, 
 cudaError_t launch_match(dynbond_ctx* c) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->grid_match);
-  cfg.blockDim = dim3(1024);
+  cfg.blockDim = dim3(MATCH_THREADS);
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -301,6 +310,15 @@ cudaError_t launch_match(dynbond_ctx* c) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_match, c->d, (const RuleTab*)c->d_rt);
+}
+
+// the candidate search: staged tiles when the geometry has them, else the
+// per-bead search in global memory
+cudaError_t launch_candidates(dynbond_ctx* c) {
+  if (c->cand_tiles)
+    return launch_smem(c, c->octant ? k_candidates_tile_oct : k_candidates_tile, c->grid_ctile, 256,
+                       (size_t)CAND_TILE_SMEM, c->d, (const RuleTab*)c->d_rt);
+  return launch(c, c->octant ? k_candidates_oct : k_candidates, c->grid_cand, 256, c->d, (const RuleTab*)c->d_rt);
 }
 
 cudaError_t enqueue_step(dynbond_ctx* c) {
@@ -314,7 +332,7 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
   E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
   mark(c, c->ev_step, k++);
-  E(launch(c, c->octant ? k_candidates_oct : k_candidates, c->grid_cand, 256, d, c->d_rt));
+  E(launch_candidates(c));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   mark(c, c->ev_step, k++);
   E(launch_match(c));
@@ -427,6 +445,31 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
   if (c->max_cells && cb[R] > c->max_cells) return fail(c, DYNBOND_ECAPACITY, "cell geometry larger than allocated");
   if (cb[R] * c->rt.n_cls >= 0x7FFFFFFFll)
     return fail(c, DYNBOND_EINVAL, "cell grid too large: boxes over 2^31 cell keys (cell classes x cells)");
+  // work items of the staged search: per replica and class with partner
+  // classes, tiles of CT x CT columns and Z z cells; along z the stage adds hz
+  // cells on each side, hz = floor(reach nz / L) + 1 >= the cells a reach
+  // interval extends beyond its bead's cell
+  std::vector<int4> tiles;
+  bool tiles_ok = !c->global_search && c->reach > 0;
+  for (int r = 0; r < R && tiles_ok; ++r) {
+    const long long L = c->h_box[r];
+    const long long hz = c->reach * nz[r] / L + 1;
+    if (2 * hz >= CZS_MAX) {
+      tiles_ok = false;
+      break;
+    }
+    const int Z = nz[r] <= CZS_MAX ? nz[r] : (int)std::min<long long>(16, CZS_MAX - 2 * hz);
+    const int ntx = (nc[r] + CT - 1) / CT, ntz = (nz[r] + Z - 1) / Z;
+    for (int t = 0; t < 16; ++t) {
+      const int cls = c->rt.cls_of[t];
+      const unsigned pm = c->rt.cls_mask[t];
+      if (cls < 0 || !pm) continue;
+      for (int tx = 0; tx < ntx; ++tx)
+        for (int ty = 0; ty < ntx; ++ty)
+          for (int tz = 0; tz < ntz; ++tz)
+            tiles.push_back(make_int4(r, cls | (int)(hz << 8) | (int)(pm << 16), tx | ty << 16, tz | Z << 16));
+    }
+  }
   c->n_cells = cb[R];
   c->octant = octant;
   c->d.n_cells = c->n_cells;
@@ -438,9 +481,27 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cb, cb.data(), 8 * (R + 1), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
+  c->tiles_avail = tiles_ok && !tiles.empty();
+  c->cand_tiles = c->tiles_avail && c->tiles_on;
+  c->d.n_ctile = c->tiles_avail ? (int)tiles.size() : 0;
+  if (c->tiles_avail && c->d_nc) {
+    if ((long long)tiles.size() > c->ctile_cap) {  // outside any captured work: the graphs are recaptured after
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      if (c->d_ctile) cudaFree(c->d_ctile);
+      c->d_ctile = nullptr;
+      c->ctile_cap = 0;
+      CUDA_TRY(c, cudaMalloc(&c->d_ctile, sizeof(int4) * tiles.size()));
+      c->ctile_cap = (long long)tiles.size();
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ctile, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  c->d.ctile = c->d_ctile;
   c->tuning.cell_scale = scale;
   c->tuning.cell_zdiv = zdiv;
   c->tuning.octant = octant ? 1 : 0;
+  c->tuning.tiles = c->cand_tiles ? 1 : 0;
   return DYNBOND_OK;
 }
 
@@ -468,7 +529,7 @@ cudaError_t enqueue_front(dynbond_ctx* c) {
   E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
   E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
-  E(launch(c, c->octant ? k_candidates_oct : k_candidates, c->grid_cand, 256, d, c->d_rt));
+  E(launch_candidates(c));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   return cudaGetLastError();
 }
@@ -512,6 +573,7 @@ void dynbond_destroy(dynbond_ctx* c) {
   for (cudaEvent_t e : c->ev_step) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_forces) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
+  if (c->d_ctile) cudaFree(c->d_ctile);
   delete c;
 }
 
@@ -528,6 +590,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->profile = (params->flags & DYNBOND_FLAG_PROFILE) != 0;
   c->use_graph = (params->flags & DYNBOND_FLAG_NO_GRAPH) == 0;
   c->pdl = (params->flags & DYNBOND_FLAG_NO_PDL) == 0;
+  c->global_search = (params->flags & DYNBOND_FLAG_GLOBAL_SEARCH) != 0;
   if (params->max_rounds < 0 || params->prob_mode < 0 || params->prob_mode > 1 || params->cell_scale < 0)
     return (fail(c, DYNBOND_EINVAL, "bad max_rounds, prob_mode or cell_scale"));
   dynbond_status st = build_rules(c, rules, n_rules);
@@ -658,6 +721,11 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.bm_bk, c->W);
   ALLOC(d.bm_elig, c->W);
   ALLOC(d.bm_dirty, c->W);
+  // coarse dirty bitmap: one bit per 2^dc_shift words, at most PURGE_COARSE_WORDS words
+  d.dc_shift = 0;
+  while (((c->W >> d.dc_shift) + 31) / 32 > PURGE_COARSE_WORDS) ++d.dc_shift;
+  d.Wc = ((c->W >> d.dc_shift) + 1 + 31) / 32;
+  ALLOC(d.bm_dirtyc, d.Wc);
   ALLOC(d.bm_new, c->W);
   ALLOC(d.live[0], 2 * N);
   ALLOC(d.live[1], 2 * N);
@@ -681,7 +749,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   // per-call counters zeroed together: removed / added counts, k_fill
   // counters and items, round flags, statistics
   {
-    size_t ints = 11 * (size_t)R;
+    size_t ints = 13 * (size_t)R;
     size_t bytes = ((ints * sizeof(int) + 15) / 16) * 16 + (size_t)R * NSTAT * sizeof(long long);
     char* base;
     ALLOC(base, bytes);
@@ -695,8 +763,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
     d.added_ang = ip + 2 * R;
     d.added_dih = ip + 3 * R;
     d.fill_items = ip + 4 * R;
-    d.round_hit = ip + 5 * R;  // 2R
-    d.fillc = ip + 7 * R;      // 4R
+    d.fillc = ip + 5 * R;      // 4R
+    d.round_hit = ip + 9 * R;  // 4R: two buffers of (creation, breakage) x R
     d.stats = (long long*)(base + ((ints * sizeof(int) + 15) / 16) * 16);
   }
   {
@@ -762,6 +830,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaMemsetAsync(d.err, 0, sizeof(unsigned), s));
   for (unsigned* bm : {d.bm_ca, d.bm_ba, d.bm_bn, d.bm_bk, d.bm_elig, d.bm_dirty, d.bm_new})
     CUDA_TRY(c, cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)c->W, s));
+  CUDA_TRY(c, cudaMemsetAsync(d.bm_dirtyc, 0, sizeof(unsigned) * (size_t)d.Wc, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_ang, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.n_dih, 0, 4 * R, s));
   CUDA_TRY(c, cudaMemsetAsync(d.args, 0, sizeof(CallArgs), s));
@@ -779,10 +848,15 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->tuning.bead_blocks_per_sm = 8;
   c->tuning.candidate_blocks_per_sm = 8;
   c->grid_cand = bounded_grid(N, 256, c->nsm * 8);
+  for (auto fn : {(const void*)k_candidates_tile, (const void*)k_candidates_tile_oct})
+    CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, CAND_TILE_SMEM));
+  c->grid_ctile = occupancy_grid(c, (const void*)k_candidates_tile, 256, 8, CAND_TILE_SMEM);
   c->grid_seg = c->nsm * 4;
-  // one 1024-thread block per SM: full latency hiding with few barrier arrivals
-  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, 1024, 1),
-                                       bounded_grid(N, 1024, c->nsm)));
+  // matching: co-resident blocks (cooperative launch), at most two per SM so
+  // the grid barriers between rounds stay short; round 0 gives each lane one
+  // 32-bead bitmap word
+  c->grid_match = std::max(1, std::min(occupancy_grid(c, (const void*)k_match, MATCH_THREADS, 2),
+                                       bounded_grid((N + 31) / 32, MATCH_THREADS, c->nsm * 2)));
 
   // ---- initial interactions: the typed set of every path of the initial graph
   CUDA_TRY(c, cudaMemsetAsync(d.cnt, 0, sizeof(Counters), s));
@@ -901,6 +975,7 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
     float best = 1e30f;
     double best_scale = 1.0;
     int best_grid = 8, best_zdiv = 1;
+    bool best_tiles = false;
     for (int g = 0; g < 15; ++g) {
       const double sc = scales[g / 3];
       const int zd = zdivs[g % 3];
@@ -910,28 +985,33 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
         continue;
       }
       if (st) break;
-      for (int gm : grids) {
-        c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * gm);
-        float ms = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {  // the first run warms caches and clocks; best of three
-          cudaEventRecord(e0, c->stream);
-          enqueue_front(c);
-          cudaEventRecord(e1, c->stream);
-          if (cudaEventSynchronize(e1) != cudaSuccess) break;
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
-          if (rep) ms = std::min(ms, t);
-        }
-        if (ms < best) {
-          best = ms;
-          best_scale = sc;
-          best_zdiv = zd;
-          best_grid = gm;
+      for (int mode = 0; mode < (c->tiles_avail ? 2 : 1); ++mode) {  // staged tiles, then the global search
+        c->cand_tiles = c->tiles_avail && mode == 0;
+        for (int gm : grids) {
+          c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * gm);
+          float ms = 1e30f;
+          for (int rep = 0; rep < 4; ++rep) {  // the first run warms caches and clocks; best of three
+            cudaEventRecord(e0, c->stream);
+            enqueue_front(c);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep) ms = std::min(ms, t);
+          }
+          if (ms < best) {
+            best = ms;
+            best_scale = sc;
+            best_zdiv = zd;
+            best_grid = gm;
+            best_tiles = c->cand_tiles;
+          }
         }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c->tiles_on = best_tiles;  // kept: later geometry changes stay with the timed choice
     if (!st) st = set_geometry(c, best_scale, best_zdiv);
     c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * best_grid);
     c->tuning.bead_blocks_per_sm = c->tuning.candidate_blocks_per_sm = best_grid;

@@ -102,6 +102,8 @@ struct Dev {
   long long reach;              // smallest integer >= the largest creation distance (quantised units)
   const long long* cell_base;  // [R+1]
   long long n_cells;            // cells of one class (all replicas)
+  const int4* ctile;           // [n_ctile] work items of the staged candidate search
+  int n_ctile;
   long long n_keys;             // n_cls * n_cells binned keys
   const int* rep;              // [N]
   const unsigned char* type;   // [N]
@@ -149,6 +151,9 @@ struct Dev {
   unsigned* bm_bk;             // [W] beads holding a bond of a type named by a breakage rule (kept current)
   unsigned* bm_elig;           // [W] beads that can form a bond (creation_eligible; kept current)
   unsigned* bm_dirty;          // [W] beads that lost or retyped a bond
+  unsigned* bm_dirtyc;         // [Wc] coarse: bit b set if a bead of words [b << dc_shift, (b + 1) << dc_shift) is dirty
+  long long Wc;                // coarse words (at most PURGE_COARSE_WORDS)
+  int dc_shift;
   unsigned* bm_new;            // [W] beads with a formed or retyped bond
   int* live[2];                // [2*N] each: active (system << 31 | bead) entries between rounds
   long long* mate;             // [2*N] creation / breakage match: partner | round << 32, -1 = none
@@ -226,22 +231,21 @@ __device__ __forceinline__ long long dist2(const int4& a, const int4& b, int L) 
   return x * x + y * y + z * z;
 }
 
-__device__ __forceinline__ int find_rep(const long long* base, int R, long long x) {
-  // largest r with base[r] <= x (base[R] > x)
+// Largest r in [0, R) with base[r] <= x (base non-decreasing, base[0] <= x),
+// for a warp whose 32 lanes all ask for the same x (every lane must call
+// it): each round probes 32 evenly spaced entries of [lo, hi] at once and
+// keeps the part between the last probe at or below x and the next one, so
+// R segments take ceil(log32 R) dependent loads (two for 512 replicas)
+// instead of log2 R.
+__device__ __forceinline__ int find_seg_warp(const int* base, int R, int x) {
+  const int lane = threadIdx.x & 31;
   int lo = 0, hi = R - 1;
   while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (base[mid] <= x) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-__device__ __forceinline__ int find_seg(const int* base, int R, int x) {
-  int lo = 0, hi = R - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (base[mid] <= x) lo = mid;
-    else hi = mid - 1;
+    const int step = (hi - lo + 31) >> 5;  // 32 probes cover (lo, hi]
+    const int idx = lo + (lane + 1) * step;
+    const bool le = idx <= hi && base[idx] <= x;
+    lo += __popc(__ballot_sync(FULL, le)) * step;  // the true probes are a prefix of the lanes
+    hi = min(hi, lo + step - 1);
   }
   return lo;
 }

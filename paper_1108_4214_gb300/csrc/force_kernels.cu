@@ -8,18 +8,13 @@
 //   dihedrals E = K (1 + d cos phi) (Sec. 3), forces from the
 //             Blondel-Karplus (J. Comput. Chem. 17, 1132 (1996)) derivatives
 //             of phi, free of the sin(phi) = 0 singularity.
-// Work items are (replica, tile) pairs; a block reduces its energy / virial
-// when it moves to another replica and at its end.
+// Work items are (replica, tile) pairs; each warp adds its energy / virial
+// partials to the replica's sums when its block moves to another replica and
+// at its end.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace dynbond {
-
-__device__ __forceinline__ float3 relq(const int4& a, const int4& b, int L) {
-  const float q = 1.0f / 1048576.0f;
-  return make_float3((float)wrap_dx(a.x - b.x, L) * q, (float)wrap_dx(a.y - b.y, L) * q,
-                     (float)wrap_dx(a.z - b.z, L) * q);
-}
 
 // Energy / virial accumulators: a thread sums its own few terms (at most a
 // few tens: its beads' bonds or its records over the launch) in plain FP32;
@@ -62,33 +57,32 @@ struct EV {
   }
 };
 
-// block-reduce the 7 accumulators and add them to replica r
-__device__ void flush_ev(const Dev& d, EV& acc, int r) {
-  __shared__ double sh[7][32];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Add the warp's 7 accumulators to replica r and clear them: a TwoSum
+// butterfly over the lanes (every lane ends with the warp totals as float
+// pairs), then lane k adds component k with one FP64 atomic to one of
+// EV_COPIES striped copies (so the atomics of a launch do not all meet at
+// the same seven addresses).  No block barrier: a block whose consecutive
+// tiles belong to different replicas flushes at every change.  Every lane
+// of the warp must call it.
+__device__ __forceinline__ void flush_ev(const Dev& d, EV& acc, int r) {
+  const int lane = threadIdx.x & 31;
+  double mine = 0.0;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     float h = acc.hi[k], l = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      float h2 = __shfl_down_sync(FULL, h, o), l2 = __shfl_down_sync(FULL, l, o);
-      float s, e;
-      two_sum(h, h2, s, e);
-      h = s;
+      const float h2 = __shfl_xor_sync(FULL, h, o), l2 = __shfl_xor_sync(FULL, l, o);
+      float s2, e;
+      two_sum(h, h2, s2, e);
+      h = s2;
       l = __fadd_rn(__fadd_rn(l, l2), e);
     }
-    if (lane == 0) sh[k][wid] = (double)h + (double)l;
+    if (lane == k) mine = (double)h + (double)l;
     acc.hi[k] = 0.f;
   }
-  __syncthreads();
-  if (threadIdx.x < 7) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
-    // striped: blocks add to one of EV_COPIES copies, so the FP64 atomics
-    // of a launch do not all meet at the same seven addresses
-    atomicAdd(&d.ev_acc[((long long)r * EV_COPIES + blockIdx.x % EV_COPIES) * 7 + threadIdx.x], s);
-  }
-  __syncthreads();
+  const long long copy = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % EV_COPIES;
+  if (lane < 7 && mine != 0.0) atomicAdd(&d.ev_acc[((long long)r * EV_COPIES + copy) * 7 + lane], mine);
 }
 
 // Bonds: each bead sums, over its occupied slots, the harmonic force of the
@@ -113,35 +107,58 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ff) {
   const int R = d.R, nitems = d.tb_beads[R];
   const unsigned N = (unsigned)d.N;
   const int tid = threadIdx.x;
-  // first bead and end of work item k of this block (beg = end when none)
-  auto tile = [&](int k, long long& beg, long long& end, int& r) {
-    const int it = blockIdx.x + k * gridDim.x;
-    beg = end = 0;
-    r = 0;
-    if (it >= nitems) return;
-    r = find_seg(d.tb_beads, R, it);
-    beg = d.off[r] + (long long)(it - d.tb_beads[r]) * BEAD_TILE;
-    end = min(beg + BEAD_TILE, d.off[r + 1]);
+  // work items blockIdx.x, + gridDim.x, ...: at any time the grid works on
+  // neighbouring tiles (shared partner positions stay in L2); each tile's
+  // replica is looked up once, when its slots are issued
+  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  struct Tile {
+    long long beg = 0, end = 0;
+    int r = 0, L = 0;
   };
-  auto issue_slots = [&](int k) {
-    long long beg, end;
-    int r;
-    tile(k, beg, end, r);
+  // the block's tiles are looked up before the pipeline starts, a warp per
+  // tile (the lookups are independent), so no tile waits on a lookup
+  __shared__ int4 s_tiles[FORCE_TILE_TABLE];
+  const int nlook = min(ntiles, FORCE_TILE_TABLE);
+  for (int k = tid >> 5; k < nlook; k += BF_THREADS >> 5) {
+    const int it = (int)blockIdx.x + k * (int)gridDim.x;
+    const int r = find_seg_warp(d.tb_beads, R, it);
+    if ((tid & 31) == 0) {
+      const long long beg = d.off[r] + (long long)(it - d.tb_beads[r]) * BEAD_TILE;
+      s_tiles[k] = make_int4(r, (int)beg, (int)min(beg + BEAD_TILE, d.off[r + 1]), (int)d.box[r]);
+    }
+  }
+  __syncthreads();
+  auto tile = [&](int k) {
+    Tile t;
+    if (k >= ntiles) return t;
+    if (k < FORCE_TILE_TABLE) {
+      const int4 e = s_tiles[k];
+      t.r = e.x;
+      t.beg = e.y;
+      t.end = e.z;
+      t.L = e.w;
+      return t;
+    }
+    const int it = (int)blockIdx.x + k * (int)gridDim.x;
+    t.r = find_seg_warp(d.tb_beads, R, it);
+    t.beg = d.off[t.r] + (long long)(it - d.tb_beads[t.r]) * BEAD_TILE;
+    t.end = min(t.beg + BEAD_TILE, d.off[t.r + 1]);
+    t.L = (int)d.box[t.r];
+    return t;
+  };
+  auto issue_slots = [&](const Tile& t, int k) {
 #pragma unroll
     for (int u = 0; u < BF_PER_THREAD; ++u) {
-      const long long i = beg + tid + u * BF_THREADS;
-      cp_async16(&sm.slot[k % 3][u][tid], i < end ? (const void*)(d.slots + i) : (const void*)d.slots, i < end);
+      const long long i = t.beg + tid + u * BF_THREADS;
+      cp_async16(&sm.slot[k % 3][u][tid], i < t.end ? (const void*)(d.slots + i) : (const void*)d.slots, i < t.end);
     }
     cp_async_commit();
   };
-  auto issue_pos = [&](int k) {
-    long long beg, end;
-    int r;
-    tile(k, beg, end, r);
+  auto issue_pos = [&](const Tile& t, int k) {
 #pragma unroll
     for (int u = 0; u < BF_PER_THREAD; ++u) {
-      const long long i = beg + tid + u * BF_THREADS;
-      const bool ok = i < end;
+      const long long i = t.beg + tid + u * BF_THREADS;
+      const bool ok = i < t.end;
       const uint4 sl = sm.slot[k % 3][u][tid];
       cp_async16(&sm.pos[k & 1][u][0][tid], pos + (ok ? i : 0), ok);
 #pragma unroll
@@ -153,28 +170,29 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ff) {
     }
     cp_async_commit();
   };
-  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   EV acc;
   int racc = -1;
   // commit order: S0 S1 P0 | S2 P1 | S3 P2 ...; wait_group 2 leaves the two
-  // newest groups in flight
-  issue_slots(0);
-  issue_slots(1);
+  // newest groups in flight.  t0, t1, t2: tiles k, k + 1, k + 2.
+  Tile t0 = tile(0), t1 = tile(1);
+  issue_slots(t0, 0);
+  issue_slots(t1, 1);
   cp_async_wait<1>();
-  issue_pos(0);
+  issue_pos(t0, 0);
   for (int k = 0; k < ntiles; ++k) {
-    issue_slots(k + 2);  // past the last tile: an empty group
-    cp_async_wait<2>();  // slots of tile k + 1 have landed
-    issue_pos(k + 1);
-    cp_async_wait<2>();  // positions of tile k have landed
-    long long beg, end;
-    int r;
-    tile(k, beg, end, r);
+    const Tile t2 = tile(k + 2);
+    issue_slots(t2, k + 2);  // past the last tile: an empty group
+    cp_async_wait<2>();      // slots of tile k + 1 have landed
+    issue_pos(t1, k + 1);
+    cp_async_wait<2>();      // positions of tile k have landed
+    const long long beg = t0.beg, end = t0.end;
+    const int r = t0.r, L = t0.L;
+    t0 = t1;
+    t1 = t2;
     if (r != racc) {
       if (racc >= 0) flush_ev(d, acc, racc);
       racc = r;
     }
-    const int L = (int)d.box[r];
     float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < BF_PER_THREAD; ++u) {
@@ -191,9 +209,8 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ff) {
           atomicOr(d.err, ERR_INTERNAL);
           continue;
         }
-        const float3 rij = relq(p, sm.pos[k & 1][u][1 + q][tid], L);
-        const BondHalf h = bond_half_force(ff, s_type(v), rij);
-        const float3 fq = h.f;
+        const BondHalf h = bond_half_force(ff, s_type(v), reli(p, sm.pos[k & 1][u][1 + q][tid], L));
+        const float3 rij = h.rij, fq = h.f;
         f = make_float3(f.x + fq.x, f.y + fq.y, f.z + fq.z);
         e += h.E;
         w[0] += rij.x * fq.x;
@@ -261,7 +278,7 @@ __device__ __forceinline__ void dihedral_term(float4* force, const int4& rec, co
 // angle lists, then the dihedral tiles.
 struct AdTile {
   bool valid = false, dih = false;
-  int r = 0, beg = 0, end = 0;
+  int r = 0, beg = 0, end = 0, L = 0;
   const int4* recs = nullptr;
 };
 __device__ __forceinline__ AdTile ad_tile(const Dev& d, int it, int na_items, int nitems) {
@@ -271,10 +288,11 @@ __device__ __forceinline__ AdTile ad_tile(const Dev& d, int it, int na_items, in
   t.dih = it >= na_items;
   const int* tb = t.dih ? d.tb_fdih : d.tb_fang;
   const int t0 = t.dih ? it - na_items : it;
-  t.r = find_seg(tb, d.R, t0);
+  t.r = find_seg_warp(tb, d.R, t0);
   t.recs = t.dih ? d.dih + 18 * d.off[t.r] : d.ang + 6 * d.off[t.r];
   t.beg = (t0 - tb[t.r]) * FORCE_TILE;
   t.end = min(t.beg + FORCE_TILE, (t.dih ? d.n_dih : d.n_ang)[t.r]);
+  t.L = (int)d.box[t.r];
   return t;
 }
 
@@ -302,8 +320,22 @@ __global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF 
   const int na_items = d.tb_fang[d.R], nitems = na_items + d.tb_fdih[d.R];
   const unsigned N = (unsigned)d.N;
   const int tid = threadIdx.x;
-  auto issue_rec = [&](int k) {
-    const AdTile t = ad_tile(d, blockIdx.x + k * gridDim.x, na_items, nitems);
+  // work items blockIdx.x, + gridDim.x, ... (neighbouring records in flight
+  // together); each tile is looked up once, when its records are issued
+  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  // the block's tiles looked up first, a warp per tile (independent lookups)
+  __shared__ AdTile s_tiles[FORCE_TILE_TABLE];
+  const int nlook = min(ntiles, FORCE_TILE_TABLE);
+  for (int k = tid >> 5; k < nlook; k += AD_THREADS >> 5) {
+    const AdTile t = ad_tile(d, (int)blockIdx.x + k * (int)gridDim.x, na_items, nitems);
+    if ((tid & 31) == 0) s_tiles[k] = t;
+  }
+  __syncthreads();
+  auto tile = [&](int k) {
+    if (k < nlook) return s_tiles[k];
+    return ad_tile(d, k < ntiles ? (int)blockIdx.x + k * (int)gridDim.x : nitems, na_items, nitems);
+  };
+  auto issue_rec = [&](const AdTile& t, int k) {
 #pragma unroll
     for (int u = 0; u < AD_PER_THREAD; ++u) {
       const int q = t.beg + tid + u * AD_THREADS;
@@ -312,8 +344,7 @@ __global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF 
     }
     cp_async_commit();
   };
-  auto issue_pos = [&](int k) {
-    const AdTile t = ad_tile(d, blockIdx.x + k * gridDim.x, na_items, nitems);
+  auto issue_pos = [&](const AdTile& t, int k) {
 #pragma unroll
     for (int u = 0; u < AD_PER_THREAD; ++u) {
       const int q = t.beg + tid + u * AD_THREADS;
@@ -330,26 +361,29 @@ __global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF 
     }
     cp_async_commit();
   };
-  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
   EV acc;
   int racc = -1;
   // commit order: R0 R1 P0 | R2 P1 | R3 P2 ...; wait_group 2 leaves the two
-  // newest groups in flight
-  issue_rec(0);
-  issue_rec(1);
+  // newest groups in flight.  t0, t1: tiles k, k + 1.
+  AdTile t0 = tile(0), t1 = tile(1);
+  issue_rec(t0, 0);
+  issue_rec(t1, 1);
   cp_async_wait<1>();
-  issue_pos(0);
+  issue_pos(t0, 0);
   for (int k = 0; k < ntiles; ++k) {
-    issue_rec(k + 2);  // past the last tile: an empty group
-    cp_async_wait<2>();  // records of tile k + 1 have landed
-    issue_pos(k + 1);
-    cp_async_wait<2>();  // positions of tile k have landed
-    const AdTile t = ad_tile(d, blockIdx.x + k * gridDim.x, na_items, nitems);
+    const AdTile t2 = tile(k + 2);
+    issue_rec(t2, k + 2);  // past the last tile: an empty group
+    cp_async_wait<2>();    // records of tile k + 1 have landed
+    issue_pos(t1, k + 1);
+    cp_async_wait<2>();    // positions of tile k have landed
+    const AdTile t = t0;
+    t0 = t1;
+    t1 = t2;
     if (t.r != racc) {
       if (racc >= 0) flush_ev(d, acc, racc);
       racc = t.r;
     }
-    const int L = (int)d.box[t.r];
+    const int L = t.L;
     float e = 0.f, w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < AD_PER_THREAD; ++u) {

@@ -2,12 +2,15 @@
 // and the host context.
 #pragma once
 
+#include <cmath>
+
 #include "common.cuh"
 
 namespace dynbond {
 
 constexpr int PURGE_TILE = 1024;   // 256 threads x 4 records (small tiles balance the blocks)
 constexpr int PURGE_PER_THREAD = 4;
+constexpr int PURGE_COARSE_WORDS = 4096;  // coarse dirty bitmap of the purge, held in shared memory (16 KB)
 constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
 constexpr int SCAN_PER_THREAD = 32;  // cell keys per thread in the histogram scan (a multiple of 4)
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
@@ -23,10 +26,20 @@ constexpr int BF_PER_THREAD = BEAD_TILE / BF_THREADS;
 // positions of two tiles, 16 bytes each
 constexpr int BF_SMEM_BYTES = 16 * BF_THREADS * BF_PER_THREAD * (3 + 2 * (1 + DYNBOND_SLOTS));
 constexpr int EV_COPIES = 32;      // striped copies of each replica's energy / virial sums
+constexpr int FORCE_TILE_TABLE = 256;  // work items per force block looked up ahead (shared memory)
+constexpr int MATCH_THREADS = 256; // threads of the (cooperative) matching blocks
+// candidate search by staged tiles (k_candidates_tile): cell columns per tile
+// side, staged z cells per column, and the stage's capacities
+constexpr int CT = 8;
+constexpr int CZS_MAX = 24;
+constexpr int C_COL_CAP = 200;     // staged columns
+constexpr int C_ENT_CAP = 2048;    // staged entries (16 bytes each)
+constexpr int CAND_TILE_SMEM = 48 * 1024;
 
 // bonded force-field tables in FP32 (kernel parameter space)
 struct FF {
   float bond_k[16], bond_r0[16], angle_k[16], dih_k[16], dih_d[16];
+  long long bond_r0q2[16];  // (r0 2^20)^2 rounded: r0^2 in quantized units^2
   float angle_pt0[16];  // pi - theta0 of the harmonic angle types
   unsigned angle_harm;  // bit t: angle type t is harmonic in theta
 };
@@ -37,6 +50,8 @@ inline bool make_ff(const dynbond_forcefield& in, FF& out) {
   for (int t = 0; t < 16; ++t) {
     out.bond_k[t] = (float)in.bond_k[t];
     out.bond_r0[t] = (float)in.bond_r0[t];
+    const double r0q = in.bond_r0[t] * 1048576.0;
+    out.bond_r0q2[t] = (long long)std::llround(r0q * r0q);
     out.angle_k[t] = (float)in.angle_k[t];
     out.dih_k[t] = (float)in.dihedral_k[t];
     out.dih_d[t] = (float)in.dihedral_d[t];
@@ -92,18 +107,26 @@ __device__ __forceinline__ float3 axpy(float a, float3 x, float3 y) {
 }
 __device__ __forceinline__ float3 scale(float a, float3 x) { return make_float3(a * x.x, a * x.y, a * x.z); }
 
-// One end of a bond, seen from the bead that stores type t (rij = r_i - r_j,
-// sigma): the end feels the full force of E = K (r - r0)^2 of the type IT
-// stores and books half the energy (directional bonds, Sec. 2).
+// One end of a bond, seen from the bead that stores type t, from the exact
+// integer displacement d = r_i - r_j (quantized units): the end feels the
+// full force of E = K (r - r0)^2 of the type IT stores and books half the
+// energy (directional bonds, Sec. 2).  r - r0 is formed as (|d|^2 - r0^2) /
+// (r + r0) with the difference of squares exact in 64-bit integers, so a bond
+// near its rest length keeps FP32 relative accuracy in r - r0 (sqrt(|d|^2) -
+// r0 in FP32 would cancel down to the rounding of r).
 struct BondHalf {
-  float3 f;
+  float3 rij, f;
   float E;
 };
-__device__ __forceinline__ BondHalf bond_half_force(const FF& ff, int t, float3 rij) {
-  const float rr2 = dot3(rij, rij), ir = rsqrtf(rr2);
-  const float dr = rr2 * ir - ff.bond_r0[t];
+__device__ __forceinline__ BondHalf bond_half_force(const FF& ff, int t, int3 d) {
+  const float s20 = 1.0f / 1048576.0f;
   BondHalf o;
-  o.f = scale(-2.0f * ff.bond_k[t] * dr * ir, rij);
+  o.rij = tof(d, s20);
+  const long long q2 = doti(d, d);
+  const float q2f = (float)q2, rs = rsqrtf(q2f);  // 1 / |d| in quantized units
+  const float r = q2f * rs * s20;
+  const float dr = (float)(q2 - ff.bond_r0q2[t]) * (s20 * s20) * __frcp_rn(r + ff.bond_r0[t]);
+  o.f = scale(-2.0f * ff.bond_k[t] * dr * (rs * 1048576.0f), o.rij);
   o.E = 0.5f * ff.bond_k[t] * dr * dr;
   return o;
 }
@@ -210,6 +233,8 @@ __global__ void k_scan_cells(Dev d);
 __global__ void k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks);
 __global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_candidates_tile(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_candidates_tile_oct(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_match(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_edit(Dev d, const RuleTab* __restrict__ rtp);

@@ -46,12 +46,6 @@ __device__ __forceinline__ void na_flag(double* scratch) {
   atomicOr(reinterpret_cast<unsigned long long*>(scratch + NA_ERR_SLOT), 1ull);
 }
 
-__device__ __forceinline__ float3 na_rel(const int4& a, const int4& b, int L) {
-  const float q = 1.0f / 1048576.0f;
-  return make_float3((float)wrap_dx(a.x - b.x, L) * q, (float)wrap_dx(a.y - b.y, L) * q,
-                     (float)wrap_dx(a.z - b.z, L) * q);
-}
-
 // Per-lane FP64 accumulation of one replica's energy and virial; flushed
 // with atomics to the scratch when the lane moves to another replica.
 struct NaAcc {
@@ -127,11 +121,10 @@ __global__ void na_bonds(const int4* __restrict__ pos, const uint4* __restrict__
         na_flag(scratch);
         continue;
       }
-      const float3 rij = na_rel(p, pos[j], L);
-      const BondHalf h = bond_half_force(ff, s_type(v), rij);
+      const BondHalf h = bond_half_force(ff, s_type(v), reli(p, pos[j], L));
       f = make_float3(f.x + h.f.x, f.y + h.f.y, f.z + h.f.z);
       acc.e[0] += (double)h.E;
-      acc.vir(rij, h.f, 0.5f);
+      acc.vir(h.rij, h.f, 0.5f);
     }
     force[i] = make_float4(f.x, f.y, f.z, 0.f);
   }

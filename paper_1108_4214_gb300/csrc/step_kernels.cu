@@ -33,7 +33,7 @@ struct IntC {
   static constexpr int value = N;
 };
 constexpr int FO_BATCH = 4;     // list entries examined together by first_open
-constexpr int SOLO_LIVE = 2048;  // live beads below which block 0 finishes the matching alone
+constexpr int SOLO_LIVE = 512;   // live beads below which block 0 finishes the matching alone
 
 __device__ __forceinline__ void stat_add(const Dev& d, int r, int k, long long v) {
   if (v) atomicAdd((unsigned long long*)&d.stats[(long long)r * NSTAT + k], (unsigned long long)v);
@@ -648,6 +648,33 @@ __device__ __forceinline__ void load_type_masks(const RuleTab& rt, unsigned* s_m
   __syncthreads();
 }
 
+// The sorted candidate list of sorted entry e (bead i; i < 0: no bead): lists
+// of up to CAND_FAST entries go to the entry's own slots, longer ones (rare)
+// take room from the shared pool behind them; a bead with more than MAXC
+// candidates is queued for k_cand_overflow.  Every lane of the warp must call it.
+__device__ __forceinline__ void emit_list(const Dev& d, int e, int i, const LocalList& ll) {
+  const int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
+  if (ll.overflow) d.ovf[oslot] = e;
+  int cnt = ll.overflow ? 0 : ll.cnt;
+  if (cnt > 0) {
+    long long at = (long long)e * CAND_FAST;
+    if (cnt > CAND_FAST) {
+      const int a = atomicAdd(&d.cnt->cand_used, cnt);
+      at = d.cand_fixed + a;
+      if ((long long)a + cnt > d.cand_pool) {
+        atomicOr(d.err, ERR_CAND_CAP);
+        cnt = 0;
+      }
+    }
+    if (cnt > 0) {
+      for (int q = 0; q < cnt; ++q)
+        d.cand[at + q] =
+            make_int4(ll.kp[q], ll.ki[q], (int)(unsigned)(unsigned long long)ll.kd[q], (int)(ll.kd[q] >> 32));
+      activate_creator(d, i, (int)at, cnt);
+    }
+  }
+}
+
 template <int GEO>
 __device__ __forceinline__ void candidates_body(const Dev& d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
@@ -680,29 +707,7 @@ __device__ __forceinline__ void candidates_body(const Dev& d, const RuleTab* __r
       if (np) si = d.slots[i];
     }
     warp_survivors(d, rtp, i, ti, si, pj, pd, np, &ll, s_q[threadIdx.x >> 5]);
-    // beads with more than MAXC candidates are finished by k_cand_overflow
-    int oslot = warp_alloc(&d.cnt->n_ovf, ll.overflow ? 1 : 0);
-    if (ll.overflow) d.ovf[oslot] = e;
-    // lists of up to CAND_FAST entries go to the sorted entry's own slots;
-    // longer ones (rare) take room from the shared pool behind them
-    int cnt = ll.overflow ? 0 : ll.cnt;
-    if (cnt > 0) {
-      long long at = (long long)e * CAND_FAST;
-      if (cnt > CAND_FAST) {
-        const int a = atomicAdd(&d.cnt->cand_used, cnt);
-        at = d.cand_fixed + a;
-        if ((long long)a + cnt > d.cand_pool) {
-          atomicOr(d.err, ERR_CAND_CAP);
-          cnt = 0;
-        }
-      }
-      if (cnt > 0) {
-        for (int q = 0; q < cnt; ++q)
-          d.cand[at + q] =
-              make_int4(ll.kp[q], ll.ki[q], (int)(unsigned)(unsigned long long)ll.kd[q], (int)(ll.kd[q] >> 32));
-        activate_creator(d, i, (int)at, cnt);
-      }
-    }
+    emit_list(d, e, i, ll);
     if (e < n && !ll.overflow) pairs.add(tg, r, 0, ll.pairs);
   }
   pairs.end_warp(tg);
@@ -713,6 +718,318 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
 }
 __global__ void __launch_bounds__(256, 3) k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp) {
   candidates_body<1>(d, rtp);
+}
+
+// ---------------------------------------------------------------------------
+// k_candidates_tile: the same search by tiles of cell columns staged in
+// shared memory.  A work item is one replica's cell-list class c over CT x CT
+// cell columns and a window of z cells.  The block stages, for every partner
+// class of c, the entries of the columns one step around the tile (x and y,
+// periodic, distinct) over the z window widened by hz cells on each side
+// (the whole column when that covers it): first the cell counts (one pass
+// over the cell ends, a block scan gives each staged cell its place), then
+// the entries themselves with 16-byte cp.async.  Every owned bead of the tile
+// then runs the search of scan_candidates on the staged copy, so its
+// neighbour-cell loop walks shared memory instead of issuing dependent global
+// loads.  Survivors are tested and listed exactly as by k_candidates.  Tiles
+// whose staged data would not fit (dense cells, many partner classes) run the
+// global-memory search for their beads.  Work items are taken from a ticket.
+// ---------------------------------------------------------------------------
+struct CandStage {
+  int4 ent[C_ENT_CAP];
+  unsigned short off[C_COL_CAP][CZS_MAX + 1];  // column-relative start of staged cell lz; [Zs] = column total
+  int cbase[C_COL_CAP + 1];                    // first staged entry of each column; [n_cols] = total
+  int colA[C_COL_CAP], colLenA[C_COL_CAP], colB[C_COL_CAP];  // per staged column: its run up to the
+                                                             // end of the column, then from z cell 0
+  int own_g[CT * CT], own_pre[CT * CT + 1];                  // owned column runs of sorted entries
+  int r, c, pmask, P, nc, nz, L, hx0, hy0, HX, HY, hz0, Zs, whole, n_cols, n_own_cols, x0, y0, Ty, z0, Tz, fallback;
+};
+static_assert(sizeof(CandStage) <= CAND_TILE_SMEM, "candidate tile shared memory layout");
+
+// Tile parameters from the work item and its replica's geometry.  Tile
+// record: x = replica, y = class | hz << 8 | partner classes << 16, z = tile
+// x | tile y << 16, w = tile z | z cells per tile << 16.
+__device__ __forceinline__ void tile_params(const int4& t, int nc, int nz, int L, CandStage& S) {
+  S.r = t.x;
+  S.c = t.y & 0xFF;
+  const int hz = (t.y >> 8) & 0xFF;
+  S.pmask = (int)((unsigned)t.y >> 16);
+  S.P = __popc(S.pmask);
+  S.nc = nc;
+  S.nz = nz;
+  S.L = L;
+  const int x0 = (t.z & 0xFFFF) * CT, y0 = ((unsigned)t.z >> 16) * CT;
+  const int Tx = min(CT, nc - x0), Ty = min(CT, nc - y0);
+  const int Z = (unsigned)t.w >> 16;
+  S.z0 = (t.w & 0xFFFF) * Z;
+  S.Tz = min(Z, nz - S.z0);
+  S.x0 = x0;
+  S.y0 = y0;
+  S.Ty = Ty;
+  // halo columns: one step around the tile, distinct; all of them when that wraps
+  S.HX = Tx + 2 >= nc ? nc : Tx + 2;
+  S.hx0 = Tx + 2 >= nc ? 0 : (x0 == 0 ? nc - 1 : x0 - 1);
+  S.HY = Ty + 2 >= nc ? nc : Ty + 2;
+  S.hy0 = Ty + 2 >= nc ? 0 : (y0 == 0 ? nc - 1 : y0 - 1);
+  S.whole = S.Tz + 2 * hz >= nz;
+  S.Zs = S.whole ? nz : S.Tz + 2 * hz;
+  S.hz0 = S.whole ? 0 : (S.z0 >= hz ? S.z0 - hz : S.z0 - hz + nz);
+  S.n_cols = S.P * S.HX * S.HY;
+  S.n_own_cols = Tx * Ty;
+  S.fallback = S.n_cols > C_COL_CAP || S.Zs > CZS_MAX;
+}
+
+// a - b for two indices in [0, n): in [0, n)
+__device__ __forceinline__ int cyc(int a, int b, int n) { return a >= b ? a - b : a - b + n; }
+
+// The owned bead's candidates from the staged columns: the same neighbour
+// columns and z cells as scan_candidates, read from shared memory.
+template <int GEO>
+__device__ __forceinline__ void scan_staged(const CandStage& S, long long r2max, long long reach, const int4& me,
+                                            int i, int* pj, long long* pd, int& np, bool& more) {
+  const int L = S.L, nc = S.nc, nz = S.nz;
+  const float f = (float)nc / (float)L;
+  const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f);
+  int nx = nc >= 3 ? 3 : nc;
+  int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
+  int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
+  auto lower = [&](int x, int cc) { return 2 * ((long long)x * nc - (long long)cc * L) < (long long)L; };
+  if (GEO == 1) {
+    nx = 2;
+    if (lower(me.x, cx)) xs[1] = xs[2];
+    if (lower(me.y, cy)) ys[1] = ys[2];
+  }
+  // z runs in staged (local) cells
+  int ra0, ra1, rb0 = 0, rb1 = -1;
+  {
+    const float fz = (float)nz / (float)L;
+    const long long zlo = (long long)me.z - reach, zhi = (long long)me.z + reach;
+    if (!S.whole) {
+      // the window holds every cell within hz of the bead's: one local run
+      const int cz = cell_of(me.z, nz, L, fz);
+      const int lo = cell_of((int)(zlo < 0 ? zlo + L : zlo), nz, L, fz);
+      const int hi = cell_of((int)(zhi >= L ? zhi - L : zhi), nz, L, fz);
+      const int lzb = cyc(cz, S.hz0, nz);
+      ra0 = lzb - cyc(cz, lo, nz);
+      ra1 = lzb + cyc(hi, cz, nz);
+    } else if (zlo >= 0 && zhi < L) {
+      ra0 = cell_of((int)zlo, nz, L, fz);
+      ra1 = cell_of((int)zhi, nz, L, fz);
+    } else if (zlo < 0 && zhi < L) {
+      const int a = cell_of((int)(zlo + L), nz, L, fz), b = cell_of((int)zhi, nz, L, fz);
+      ra0 = 0;
+      ra1 = a > b ? b : nz - 1;
+      if (a > b) {
+        rb0 = a;
+        rb1 = nz - 1;
+      }
+    } else if (zlo >= 0 && zhi >= L) {
+      const int a = cell_of((int)zlo, nz, L, fz), b = cell_of((int)(zhi - L), nz, L, fz);
+      ra0 = b < a ? a : 0;
+      ra1 = nz - 1;
+      if (b < a) {
+        rb0 = 0;
+        rb1 = b;
+      }
+    } else {
+      ra0 = 0;
+      ra1 = nz - 1;
+    }
+  }
+  for (int pi = 0; pi < S.P; ++pi)
+    for (int a = 0; a < nx; ++a) {
+      const int colx = (pi * S.HX + cyc(xs[a], S.hx0, nc)) * S.HY;
+      for (int b = 0; b < nx; ++b) {
+        const int col = colx + cyc(ys[b], S.hy0, nc);
+        const int base = S.cbase[col];
+        const unsigned short* off = S.off[col];
+        for (int run = 0; run < 2; ++run) {
+          const int la = run ? rb0 : ra0, lb = run ? rb1 : ra1;
+          if (lb < la) continue;
+          const int q1 = base + off[lb + 1];
+          for (int q = base + off[la]; q < q1; ++q) {
+            const int4 o = S.ent[q];
+            const long long dd = dist2(me, o, L);
+            if (dd > r2max || (o.w >> 4) == i) continue;
+            if (np < MAXC) {
+              pj[np] = o.w;
+              pd[np] = dd;
+              ++np;
+            } else {
+              more = true;
+            }
+          }
+        }
+      }
+    }
+}
+
+// largest k in [0, n) with a[k] <= x (a non-decreasing, a[0] <= x), shared memory
+__device__ __forceinline__ int smem_upper(const int* a, int n, int x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int GEO>
+__device__ __forceinline__ void cand_tile_body(const Dev& d, const RuleTab* __restrict__ rtp, CandStage& S) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  __shared__ unsigned s_mask[16];
+  load_type_masks(*rtp, s_mask);
+  __shared__ SurvQueue s_q[8];  // one per warp (256 threads)
+  __shared__ long long s_scan[33];
+  __shared__ int s_tile;
+  const long long r2max = rtp->r2max;
+  const CountTargets<1> tg{{d.stats + ST_CANDIDATES}, {NSTAT}};
+  ReplicaCounts<1> pairs;
+  ReplicaCounts<1>::begin_block();
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  const int* cs = d.cell_start;
+  // thread 0 holds the next work item and its replica's geometry, loaded
+  // while the current tile is processed
+  int4 nxt = make_int4(0, 0, 0, 0);
+  int nxt_id = 0, nxt_nc = 0, nxt_nz = 0, nxt_L = 0;
+  auto fetch = [&]() {
+    nxt_id = atomicAdd(&d.cnt->ticket[1], 1);
+    if (nxt_id < d.n_ctile) {
+      nxt = d.ctile[nxt_id];
+      nxt_nc = d.nc[nxt.x];
+      nxt_nz = d.ncz[nxt.x];
+      nxt_L = (int)d.box[nxt.x];
+    }
+  };
+  if (tid == 0) fetch();
+  while (true) {
+    if (tid == 0) {
+      s_tile = nxt_id;
+      if (nxt_id < d.n_ctile) {
+        tile_params(nxt, nxt_nc, nxt_nz, nxt_L, S);
+        fetch();
+      }
+    }
+    __syncthreads();
+    if (s_tile >= d.n_ctile) break;
+    const int r = S.r, nc = S.nc, nz = S.nz, Zs = S.Zs, HX = S.HX, HY = S.HY;
+    const int cb = (int)d.cell_base[r], ncl = (int)d.n_cells;
+    // owned column runs of class c: one contiguous run of sorted entries each
+    if (tid < S.n_own_cols) {
+      const int gx = S.x0 + tid / S.Ty, gy = S.y0 + tid % S.Ty;
+      const int k0 = S.c * ncl + cb + (gx * nc + gy) * nz + S.z0;
+      const int g = cs[k0 - 1];
+      S.own_g[tid] = g;
+      S.own_pre[tid + 1] = cs[k0 + S.Tz - 1] - g;
+    }
+    bool fb = S.fallback;
+    if (!fb) {
+      // staged columns, a warp each: lane lz reads the end of cell lz - 1 of
+      // the column's run from hz0 (and, past the end of the column, of its
+      // run from z cell 0), so one coalesced load per run gives every staged
+      // cell's offset within the column
+      const int nA = min(Zs, nz - S.hz0), nB = Zs - nA;
+      for (int col = warp; col < S.n_cols; col += nwarps) {
+        const int pi = col / (HX * HY), rem = col - pi * HX * HY, lx = rem / HY, ly = rem - lx * HY;
+        const int p = nth_set_bit((unsigned)S.pmask, pi);
+        int gx = S.hx0 + lx, gy = S.hy0 + ly;
+        if (gx >= nc) gx -= nc;
+        if (gy >= nc) gy -= nc;
+        const int kb = p * ncl + cb + (gx * nc + gy) * nz;
+        const int rawA = lane <= nA ? cs[kb + S.hz0 + lane - 1] : 0;
+        const int rawB = nB > 0 && lane <= nB ? cs[kb + lane - 1] : 0;
+        const int colA = __shfl_sync(FULL, rawA, 0), endA = __shfl_sync(FULL, rawA, nA);
+        const int colB = __shfl_sync(FULL, rawB, 0), endB = __shfl_sync(FULL, rawB, nB);
+        const int fromB = __shfl_sync(FULL, rawB, lane > nA ? lane - nA : 0);
+        const int lenA = endA - colA;
+        const int off = lane <= nA ? rawA - colA : lenA + fromB - colB;
+        const int tot = lenA + (nB > 0 ? endB - colB : 0);
+        if (lane <= Zs) S.off[col][lane] = (unsigned short)min(off, 65535);
+        if (lane == 0) {
+          S.colA[col] = colA;
+          S.colLenA[col] = lenA;
+          S.colB[col] = colB;
+          S.cbase[col] = min(tot, C_ENT_CAP + 1);  // column totals, scanned below
+        }
+      }
+    }
+    __syncthreads();
+    if (!fb) {
+      // column totals -> first staged entry of each column (n_cols <= blockDim)
+      const int v = tid < S.n_cols ? S.cbase[tid] : 0;
+      long long tot;
+      const long long ex = block_excl_scan((long long)v, s_scan, &tot);
+      if (tid < S.n_cols) S.cbase[tid] = (int)ex;
+      if (tid == 0) S.cbase[S.n_cols] = (int)min(tot, (long long)C_ENT_CAP + 1);
+      fb = tot > C_ENT_CAP;
+    }
+    if (warp == 0) {  // owned column runs: exclusive prefix of their lengths
+      const int n = S.n_own_cols;
+      const int v0 = 2 * lane < n ? S.own_pre[2 * lane + 1] : 0, v1 = 2 * lane + 1 < n ? S.own_pre[2 * lane + 2] : 0;
+      const int inc = warp_incl_scan(v0 + v1);
+      __syncwarp();
+      if (2 * lane < n) S.own_pre[2 * lane] = inc - v0 - v1;
+      if (2 * lane + 1 < n) S.own_pre[2 * lane + 1] = inc - v1;
+      if (lane == 31) S.own_pre[n] = inc;
+    }
+    __syncthreads();
+    if (!fb) {
+      // the staged entries, 16 bytes each, a warp per column
+      for (int col = warp; col < S.n_cols; col += nwarps) {
+        const int base = S.cbase[col], len = S.cbase[col + 1] - base;
+        const int a = S.colA[col], la = S.colLenA[col], bq = S.colB[col];
+        for (int q = lane; q < len; q += 32) cp_async16(&S.ent[base + q], d.sorted + (q < la ? a + q : bq + (q - la)), true);
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // the owned beads, one per thread
+    const int n_own = S.own_pre[S.n_own_cols];
+    for (int base = 0; base < n_own; base += nthr) {
+      const int fo = base + tid;
+      int e = -1, i = -1, ti = 0, np = 0;
+      int pj[MAXC];
+      long long pd[MAXC];
+      uint4 si = make_uint4(0, 0, 0, 0);
+      LocalList ll;
+      ll.cnt = ll.pairs = 0;
+      ll.overflow = false;
+      if (fo < n_own) {
+        const int oc = smem_upper(S.own_pre, S.n_own_cols, fo);
+        e = S.own_g[oc] + (fo - S.own_pre[oc]);
+        const int4 me = d.sorted[e];
+        i = me.w >> 4;
+        ti = me.w & 15;
+        ll.me = i;
+        if (fb) {
+          scan_candidates<GEO>(d, rtp, s_mask[ti], r2max, me, i, &ll, 0, nullptr, pj, pd, &np);
+        } else {
+          bool more = false;
+          scan_staged<GEO>(S, r2max, d.reach, me, i, pj, pd, np, more);
+          ll.overflow = more;  // finished exactly by k_cand_overflow
+          if (more) np = 0;
+        }
+        if (np) si = d.slots[i];
+      }
+      warp_survivors(d, rtp, i, ti, si, pj, pd, np, &ll, s_q[warp]);
+      emit_list(d, e, i, ll);
+      if (fo < n_own && !ll.overflow) pairs.add(tg, r, 0, ll.pairs);
+    }
+    __syncthreads();  // the stage is reused by the next tile
+  }
+  pairs.end_warp(tg);
+}
+
+__global__ void __launch_bounds__(256, 3) k_candidates_tile(Dev d, const RuleTab* __restrict__ rtp) {
+  extern __shared__ __align__(16) unsigned char ct_smem[];
+  cand_tile_body<0>(d, rtp, *reinterpret_cast<CandStage*>(ct_smem));
+}
+__global__ void __launch_bounds__(256, 3) k_candidates_tile_oct(Dev d, const RuleTab* __restrict__ rtp) {
+  extern __shared__ __align__(16) unsigned char ct_smem[];
+  cand_tile_body<1>(d, rtp, *reinterpret_cast<CandStage*>(ct_smem));
 }
 
 // Exact path for beads with more than MAXC candidates: count, allocate,
@@ -756,7 +1073,10 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
       }
       lst[b] = x;
     }
-    activate_creator(d, i, (int)at, cv.cnt);
+    // more than MAXC beads within the reach need not leave any candidate
+    // once the rule, maxbond and graph-distance tests run: such a bead takes
+    // no part in the matching (its nomination would read a stale entry)
+    if (cv.cnt > 0) activate_creator(d, i, (int)at, cv.cnt);
     stat_add(d, rep_of(d, i), ST_CANDIDATES, pairs);
   }
 }
@@ -794,18 +1114,25 @@ __device__ __forceinline__ int first_open(const Dev& d, int sys, int i, int& p, 
   return -1;
 }
 
-__global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict__ rtp) {
+// Flag replica r (-1: none) as having matched in this round (flags of round
+// k live in buffer k & 1, so block 0 can count and clear one round's flags
+// while the next round sets the other buffer's).
+__device__ __forceinline__ void flag_round(const Dev& d, int round, int sys, int r) {
+  if (r >= 0) d.round_hit[(round & 1) * 2 * d.R + sys * d.R + r] = 1;
+}
+
+// Rounds run over the grid with warp-level list appends and counters (no
+// block barrier inside a round) and one bounded grid barrier between rounds;
+// once few beads are left, block 0 finishes alone with block barriers.
+__global__ void __launch_bounds__(MATCH_THREADS) k_match(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_wait();  // cooperative: its successor is scheduled only when it ends
   if (aborted(d.err)) return;
   const RuleTab& rt = *rtp;
   const long long N = d.N;
   const int R = d.R;
+  const int lane = threadIdx.x & 31;
   const CountTargets<2> tg{{d.stats + ST_CREATE_MATCHED, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
   ReplicaCounts<2> matched_pairs;
-  // round 0 enumerates the nominators from the activity bitmaps; later rounds
-  // read the compacted list of beads that were still unmatched and nominated
-  // someone.  Once few remain, block 0 finishes the rounds alone with block
-  // barriers instead of grid barriers.
   int n = 0, round = 0;
   bool solo = false;
   int nb = gridDim.x, bi = blockIdx.x;  // participating blocks, this block's rank
@@ -813,48 +1140,64 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
     const int* src = round ? d.live[(round - 1) & 1] : nullptr;
     int* dst = d.live[round & 1];
     int hits = 0;            // pairs (i < j) this thread matched in this round
-    int hr[2] = {-1, -1};    // replica of those pairs, per system
-    // a mutual nomination is a match; an unmatched nominator carries over
-    auto match_one = [&](int sys, int i, bool& keep) {
-      const long long o = sys ? N : 0;
-      const int j = d.nom[o + i];
-      if (j >= 0 && ld_cg(d.nom + o + j) == i) {
-        d.mate[o + i] = mate_pack(0, j);
-        if (i < j) {
-          const int r = rep_of(d, i);
-          ++hits;
-          matched_pairs.add(tg, r, sys, 1);
-          if (hr[sys] != r) {
-            if (hr[sys] >= 0) d.round_hit[sys * R + hr[sys]] = 1;
-            hr[sys] = r;
-          }
-        }
-      } else {
-        keep = j >= 0;
+    int hr[2] = {-1, -1};    // replica of those pairs, per system (flagged when it changes)
+    auto count_hit = [&](int sys, int i) {
+      const int r = rep_of(d, i);
+      ++hits;
+      matched_pairs.add(tg, r, sys, 1);
+      if (hr[sys] != r) {
+        flag_round(d, round, sys, hr[sys]);
+        hr[sys] = r;
       }
     };
+    const int tthreads = nb * blockDim.x, tid = bi * blockDim.x + threadIdx.x;
     if (round == 0) {
-      // nominations were written by the list producers
-      const long long nchunks = (d.W + CHUNK_WORDS - 1) / CHUNK_WORDS;
-      const long long cpb = (nchunks + nb - 1) / nb;
-      const long long c0 = (long long)bi * cpb, c1 = min(nchunks, c0 + cpb);
-      for_bits_block(d.bm_ca, d.bm_bn, d.W, N, c0, c1, [&](bool valid, long long i, bool ca, bool bn) {
-        bool k0 = false, k1 = false;
-        if (ca) match_one(0, (int)i, k0);
-        if (bn) match_one(1, (int)i, k1);
-        int at = block_alloc(&d.cnt->round_live[0], (int)k0 + (int)k1);
-        if (k0) dst[at++] = (int)i;
-        if (k1) dst[at] = (int)(1u << 31 | (unsigned)i);
-        (void)valid;
-      });
+      // nominations were written by the list producers; a mutual pair is a
+      // match, an unmatched nominator carries over.  Each lane walks one
+      // bitmap word at a time, bead by bead; the warp appends its carries
+      // with one atomic per pass.
+      for (long long w0 = (long long)tid - lane; w0 < d.W; w0 += tthreads) {
+        const long long w = w0 + lane;
+        unsigned ca = 0, bn = 0;
+        if (w < d.W) {
+          const long long b0 = 32 * w;  // the last word may extend past N
+          const unsigned vmask = b0 + 32 <= N ? FULL : (b0 >= N ? 0u : (1u << (N - b0)) - 1u);
+          ca = d.bm_ca[w] & vmask;
+          bn = d.bm_bn[w] & vmask;
+        }
+        unsigned todo = ca | bn;
+        while (__any_sync(FULL, todo != 0)) {
+          bool k0 = false, k1 = false;
+          int i = 0;
+          if (todo) {
+            const int bit = __ffs(todo) - 1;
+            todo &= todo - 1;
+            i = (int)(32 * w + bit);
+            for (int sys = 0; sys < 2; ++sys) {
+              if (!(((sys ? bn : ca) >> bit) & 1u)) continue;
+              const long long o = sys ? N : 0;
+              const int j = d.nom[o + i];
+              if (j >= 0 && ld_cg(d.nom + o + j) == i) {
+                d.mate[o + i] = mate_pack(0, j);
+                if (i < j) count_hit(sys, i);
+              } else if (j >= 0) {
+                (sys ? k1 : k0) = true;
+              }
+            }
+          }
+          int at = warp_alloc(&d.cnt->round_live[0], (int)k0 + (int)k1);
+          if (k0) dst[at++] = i;
+          if (k1) dst[at] = (int)(1u << 31 | (unsigned)i);
+        }
+      }
     } else {
       // One phase per round: a live bead's nominee is its first list entry
       // that was unmatched when the round began (a match stamped with this
       // round does not count yet), and the nominee's own nominee is found
       // the same way from the nominee's list; a mutual pair is a match.  The
       // two ends decide alike, so a round needs a single barrier.
-      for (int base = bi * blockDim.x; base < n; base += nb * blockDim.x) {
-        const int idx = base + threadIdx.x;
+      for (int base = tid - lane; base < n; base += tthreads) {
+        const int idx = base + lane;
         bool keep = false;
         int e = 0;
         if (idx < n) {
@@ -870,37 +1213,30 @@ __global__ void __launch_bounds__(1024) k_match(Dev d, const RuleTab* __restrict
             int pj = ld_cg(d.ptr + o + j);
             if (first_open(d, sys, j, pj, round) == i) {
               d.mate[o + i] = mate_pack(round, j);
-              if (i < j) {
-                const int r = rep_of(d, i);
-                ++hits;
-                matched_pairs.add(tg, r, sys, 1);
-                if (hr[sys] != r) {
-                  if (hr[sys] >= 0) d.round_hit[sys * R + hr[sys]] = 1;
-                  hr[sys] = r;
-                }
-              }
+              if (i < j) count_hit(sys, i);
             } else {
               keep = true;
             }
           }
         }
-        int at = block_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
+        const int at = warp_alloc(&d.cnt->round_live[round], keep ? 1 : 0);
         if (keep) dst[at] = e;
       }
     }
-    // per block: pairs matched in the round, replicas that matched any
-    block_alloc(&d.cnt->round_matched[round], hits);
-    block_flag(d.round_hit, hr[0]);
-    block_flag(d.round_hit + R, hr[1]);
+    // pairs matched in the round (one atomic per warp), replicas that matched any
+    const int wh = __reduce_add_sync(FULL, hits);
+    if (lane == 0 && wh) atomicAdd(&d.cnt->round_matched[round], wh);
+    flag_round(d, round, 0, hr[0]);
+    flag_round(d, round, 1, hr[1]);
     if (solo) __syncthreads();
     else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
     const int matched = ld_cg(&d.cnt->round_matched[round]);
     if (blockIdx.x == 0) {
+      int* flags = d.round_hit + (round & 1) * 2 * R;
       for (int k = threadIdx.x; k < 2 * R; k += blockDim.x) {
-        if (ld_cg(d.round_hit + k)) {
-          int r = k % R;
-          d.stats[(long long)r * NSTAT + (k < R ? ST_CREATE_ROUNDS : ST_BREAK_ROUNDS)] += 1;
-          d.round_hit[k] = 0;
+        if (ld_cg(flags + k)) {
+          d.stats[(long long)(k % R) * NSTAT + (k < R ? ST_CREATE_ROUNDS : ST_BREAK_ROUNDS)] += 1;
+          flags[k] = 0;
         }
       }
     }
@@ -982,6 +1318,10 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
         o.n_formed += j > i;
       }
     }
+    if (form_partner == (int)i) {  // a matching that paired a bead with itself: report, never form it
+      atomicOr(d.err, ERR_INTERNAL);
+      form_partner = -1;
+    }
   }
   if (!(removed | changed | (unsigned)(form_partner >= 0))) return;
   uint4 ns = make_uint4(0, 0, 0, 0);
@@ -1045,7 +1385,11 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__
       counts.add(tg, r, 2, o.n_conv);
       counts.add(tg, r, 3, o.n_formed);
       counts.add(tg, r, 4, (long long)o.n_formed - (long long)o.n_broken - (long long)o.n_killed);
-      if (o.dirty) atomicOr(&d.bm_dirty[i >> 5], 1u << (i & 31));
+      if (o.dirty) {
+        atomicOr(&d.bm_dirty[i >> 5], 1u << (i & 31));
+        const long long cb = (i >> 5) >> d.dc_shift;
+        atomicOr(&d.bm_dirtyc[cb >> 5], 1u << (cb & 31));
+      }
       if (o.fresh) atomicOr(&d.bm_new[i >> 5], 1u << (i & 31));
     }
     // new-bond list for the rebuild: bonds formed or retyped, listed by
@@ -1149,9 +1493,16 @@ __device__ __forceinline__ bool bond_gone(const Dev& d, int a, int b) {
   return rp.x == b || rp.y == b || rp.z == b || rp.w == b;
 }
 
+// Might bead x be dirty?  The coarse bitmap in shared memory (one bit per
+// 32 << dc_shift beads) is clear for every bead range without a dirty bead.
+__device__ __forceinline__ bool maybe_dirty(const unsigned* s_coarse, int shift, int x) {
+  const int b = (x >> 5) >> shift;
+  return (s_coarse[b >> 5] >> (b & 31)) & 1u;
+}
+
 // Does the record hold a bond removed or retyped in this call (step 6)?
 // Every bond of an angle contains its middle bead, every bond of a dihedral
-// one of its two middle beads, so those bitmap bits decide most records.
+// one of its two middle beads, so those beads' dirty bits decide most records.
 __device__ __forceinline__ bool record_gone(const Dev& d, const int4& v, bool dih) {
   if (!dih) return is_dirty(d, v.y) && (bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z));
   const bool db = is_dirty(d, v.y), dc = is_dirty(d, v.z);
@@ -1159,9 +1510,20 @@ __device__ __forceinline__ bool record_gone(const Dev& d, const int4& v, bool di
   return bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z) || bond_gone(d, v.z, v.w & 0x0FFFFFFF);
 }
 
+// the same, the coarse bits in shared memory checked first
+__device__ __forceinline__ bool record_gone(const Dev& d, const unsigned* s_coarse, const int4& v, bool dih) {
+  if (!dih) return maybe_dirty(s_coarse, d.dc_shift, v.y) && is_dirty(d, v.y) &&
+                   (bond_gone(d, v.x, v.y) || bond_gone(d, v.y, v.z));
+  if (!maybe_dirty(s_coarse, d.dc_shift, v.y) && !maybe_dirty(s_coarse, d.dc_shift, v.z)) return false;
+  return record_gone(d, v, dih);
+}
+
 __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) {
   pdl_enter();
   if (aborted(d.err)) return;
+  __shared__ unsigned s_coarse[PURGE_COARSE_WORDS];
+  for (long long k = threadIdx.x; k < d.Wc; k += blockDim.x) s_coarse[k] = d.bm_dirtyc[k];
+  __syncthreads();
   const int R = d.R;
   const int na_tiles = d.tb_ang[R];
   const int ntiles = na_tiles + d.tb_dih[R];
@@ -1172,7 +1534,7 @@ __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) 
     const bool dih = tg >= na_tiles;
     const int t = dih ? tg - na_tiles : tg;
     const int* tb = dih ? d.tb_dih : d.tb_ang;
-    const int r = find_seg(tb, R, t);
+    const int r = find_seg_warp(tb, R, t);
     const long long base = (dih ? 18 : 6) * d.off[r];
     const int4* recs = (dih ? d.dih : d.ang) + base;
     const int n = (dih ? d.n_dih : d.n_ang)[r];
@@ -1188,7 +1550,7 @@ __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) 
 #pragma unroll
     for (int k = 0; k < PURGE_PER_THREAD; ++k) {
       int idx = beg + k * (int)blockDim.x;
-      bal[k] = __ballot_sync(FULL, idx < n && record_gone(d, v[k], dih));
+      bal[k] = __ballot_sync(FULL, idx < n && record_gone(d, s_coarse, v[k], dih));
       tot += __popc(bal[k]);
     }
     // one atomic per tile (the tile lies in one replica)
@@ -1220,7 +1582,7 @@ __global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
   const int R = d.R;
   const int ntiles = d.tb_fill[R];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int r = find_seg(d.tb_fill, R, t);
+    const int r = find_seg_warp(d.tb_fill, R, t);
     const int k = (t - d.tb_fill[r]) * FILL_TILE + threadIdx.x;
     const int ma = d.m_ang[r], md = d.m_dih[r];
     // item k: [0, ma) removed angles, [ma, 2 ma) the angle tail, then the
@@ -1469,6 +1831,7 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
     d.bm_ba[k] = 0;
     d.bm_bn[k] = 0;
     d.bm_dirty[k] = 0;
+    if (k < d.Wc) d.bm_dirtyc[k] = 0;
     d.bm_new[k] = 0;
   }
   for (long long k = g; k < d.small_words; k += stride) d.small[k] = 0;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdynbond.
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOTCONVERGED"}
 KINDS = dict(createbond=1, createdirbond=2, breakbond=3, convertbond=4, killbond=5, createangle=6,
              createdihedral=7, maxbond=8)
-FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_NO_AUTOTUNE, FLAG_NO_PDL = 1, 2, 4, 8
+FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_NO_AUTOTUNE, FLAG_NO_PDL, FLAG_GLOBAL_SEARCH = 1, 2, 4, 8, 16
 STAT_NAMES = [
     "candidates", "create_matched", "bonds_formed", "break_candidates", "break_matched", "bonds_broken",
     "bonds_killed", "bonds_converted", "angles_removed", "angles_added", "dihedrals_removed", "dihedrals_added",
@@ -73,7 +73,7 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("cell_scale", c_dbl), ("bead_blocks_per_sm", c_i32), ("candidate_blocks_per_sm", c_i32),
                 ("front_ms", ctypes.c_float), ("tuned", c_i32), ("cell_zdiv", c_i32),
-                ("octant", c_i32)]
+                ("octant", c_i32), ("tiles", c_i32)]
 
 
 class DPD(ctypes.Structure):

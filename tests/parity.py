@@ -51,13 +51,21 @@ def force_error(f, fr):
     return float((np.abs(f - fr) / np.maximum(np.abs(fr), rms)).max())
 
 
-def ev_error(ev, evr):
-    scale = np.abs(evr).max(axis=1, keepdims=True)
+def ev_error(ev, evr, scale=None):
+    """Largest |ev - ev_ref| over a replica's 7 values, relative to the
+    replica's largest magnitude (or to a given per-replica scale, e.g. the
+    size of the terms when the sums cancel)."""
+    if scale is None:
+        scale = np.abs(evr).max(axis=1)
+    scale = np.asarray(scale, np.float64).reshape(-1, 1).copy()
+    err = np.abs(ev - evr)
+    if np.any((scale == 0) & (err > 0).any(axis=1, keepdims=True)):
+        return np.inf
     scale[scale == 0] = 1.0
-    return float((np.abs(ev - evr) / scale).max())
+    return float((err / scale).max())
 
 
-def compare_forces(ctx, o, snap, where):
+def compare_forces(ctx, o, snap, where, ev_scale=None):
     pos = torch().from_numpy(snap).cuda()
     f, ev = ctx.forces(pos)
     f = f.cpu().numpy()
@@ -65,8 +73,12 @@ def compare_forces(ctx, o, snap, where):
     fr, evr = o.forces(snap)
     assert np.all(f[:, 3] == 0)
     worst = force_error(f, fr)
-    assert worst <= FORCE_TOL, f"{where}: force error {worst:.3g} (x max(|f|, rms))"
-    evw = ev_error(ev, evr)
+    if not worst <= FORCE_TOL:
+        bad_g = np.where(~np.isfinite(f[:, :3]).all(axis=1))[0]
+        bad_r = np.where(~np.isfinite(fr).all(axis=1))[0]
+        raise AssertionError(f"{where}: force error {worst:.3g} (x max(|f|, rms)); non-finite gpu rows "
+                             f"{bad_g[:8].tolist()} oracle rows {bad_r[:8].tolist()}")
+    evw = ev_error(ev, evr, ev_scale)
     assert evw <= EV_TOL, f"{where}: energy/virial error {evw:.3g}"
     return worst, evw
 

@@ -203,6 +203,18 @@ def test_batched_ladder_parity_and_replica_independence():
     assert np.array_equal(mapped[np.lexsort(mapped.T[::-1])], bs)
 
 
+@pytest.mark.slow
+def test_batched_ladder_512_replicas_full_size():
+    """The whole 512-replica temperature ladder (5,266,816 beads, uneven
+    replicas of 2k-64k beads, per-replica probability scales and streams):
+    statistics and topology of every replica bit for bit against the oracle
+    for three calls, forces within the parity bar."""
+    full = W.config3()
+    snaps = full.snapshots(0, 3)
+    _, worst = run_parity(full, 3, snaps=snaps)
+    print("ladder-512: max force / ev error", max(w[0] for w in worst), max(w[1] for w in worst))
+
+
 @pytest.mark.parametrize("flags", ["NO_GRAPH", "NO_PDL", "NO_GRAPH|NO_PDL"])
 def test_graph_and_direct_launches_agree(flags):
     s = W.config1()
@@ -369,3 +381,22 @@ def test_bounded_wait_gives_up_with_a_status_and_leaves_the_device_usable():
     ok = D.Context(s1)
     st = ok.step(torch.from_numpy(s1.snapshot(0)).cuda(), 0, stats=True)
     assert st[0, 12] > 0
+
+
+@pytest.mark.parametrize("cell_scale,cell_zdiv", [(1, 1), (2, 1), (2, 2), (1, 4), (3, 1), (2, 4)])
+def test_staged_and_global_candidate_search_agree(cell_scale, cell_zdiv):
+    """The candidate search over tiles of cell columns staged in shared memory
+    and the per-bead search in global memory give identical statistics and
+    topology (here on the 16M-bead melting recipe scaled to 1M beads: dense
+    turnover, duplexes and free strands), at several cell geometries."""
+    s = W.scaled_config4(8192)
+    D = dynbond()
+    geo = dict(cell_scale=cell_scale, cell_zdiv=cell_zdiv)
+    a = D.Context(s, params=geo)
+    b = D.Context(s, params=geo, flags=D.FLAG_GLOBAL_SEARCH)
+    assert a.tuning()["tiles"] == 1 and b.tuning()["tiles"] == 0
+    for k in range(3):
+        p = torch.from_numpy(s.snapshot(k)).cuda()
+        assert np.array_equal(a.step(p, k, stats=True), b.step(p, k, stats=True)), k
+    for x, y in zip(a.topology(), b.topology()):
+        assert np.array_equal(x, y)

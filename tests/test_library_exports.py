@@ -53,7 +53,7 @@ def test_binding_matches_header(lib_path):
     # bond_k, bond_r0, angle_k, dihedral_k, angle_theta0 (double); dihedral_d, angle_style (int32)
     assert ctypes.sizeof(dynbond.ForceField) == 5 * 16 * 8 + 2 * 16 * 4
     # cell_scale (double); bead / candidate blocks, front_ms, tuned, cell_zdiv, octant (4 bytes each)
-    assert ctypes.sizeof(dynbond.Tuning) == 8 + 6 * 4
+    assert ctypes.sizeof(dynbond.Tuning) == 8 + 8 * 4
 
 
 def test_create_rejects_bad_input_without_touching_the_device(lib_path):
