@@ -108,8 +108,11 @@ enum {
   DYNBOND_FLAG_NO_AUTOTUNE = 4, /* with cell_scale 0: use cells as wide as the reach, never autotune */
   DYNBOND_FLAG_NO_PDL = 8,      /* launch each kernel only after the previous one ends (no programmatic
                                    dependent launch); results are identical either way */
-  DYNBOND_FLAG_GLOBAL_SEARCH = 16 /* candidate search walks the cell lists in global memory instead of
-                                   staging tiles of cell columns in shared memory; results are identical */
+  DYNBOND_FLAG_GLOBAL_SEARCH = 16, /* candidate search always walks the cell lists in global memory */
+  DYNBOND_FLAG_STAGED_SEARCH = 32  /* candidate search always stages tiles of cell columns in shared memory
+                                      where the geometry allows it (without either flag the autotuner
+                                      times both; untuned contexts use the global search); results are
+                                      identical either way */
 };
 
 /*

@@ -68,6 +68,7 @@ struct dynbond_ctx {
   bool tiles_avail = false;     // the current geometry has staged work items
   bool tiles_on = false;        // autotuner's choice between staged and global search (global until timed)
   bool global_search = false;   // DYNBOND_FLAG_GLOBAL_SEARCH
+  bool staged_search = false;   // DYNBOND_FLAG_STAGED_SEARCH
   int grid_ctile = 0;
   bool tuned = false;
 };
@@ -591,6 +592,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->use_graph = (params->flags & DYNBOND_FLAG_NO_GRAPH) == 0;
   c->pdl = (params->flags & DYNBOND_FLAG_NO_PDL) == 0;
   c->global_search = (params->flags & DYNBOND_FLAG_GLOBAL_SEARCH) != 0;
+  c->staged_search = !c->global_search && (params->flags & DYNBOND_FLAG_STAGED_SEARCH) != 0;
+  c->tiles_on = c->staged_search;
   if (params->max_rounds < 0 || params->prob_mode < 0 || params->prob_mode > 1 || params->cell_scale < 0)
     return (fail(c, DYNBOND_EINVAL, "bad max_rounds, prob_mode or cell_scale"));
   dynbond_status st = build_rules(c, rules, n_rules);
@@ -985,7 +988,9 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
         continue;
       }
       if (st) break;
-      for (int mode = 0; mode < (c->tiles_avail ? 2 : 1); ++mode) {  // staged tiles, then the global search
+      // staged tiles, then the global search (a flag fixes one of them)
+      const int mode0 = c->tiles_avail && !c->global_search ? 0 : 1, mode1 = c->staged_search ? 1 : 2;
+      for (int mode = mode0; mode < std::max(mode1, mode0 + 1); ++mode) {
         c->cand_tiles = c->tiles_avail && mode == 0;
         for (int gm : grids) {
           c->grid_bead = c->grid_cand = bounded_grid(c->N, 256, c->nsm * gm);

@@ -633,12 +633,14 @@ __device__ __forceinline__ void warp_survivors(const Dev& d, const RuleTab* __re
   __syncwarp();
 }
 
-__device__ __forceinline__ void activate_creator(const Dev& d, int i, int start, int len) {
+// first: the list's first partner (round 0: nobody is matched yet, so the
+// bead nominates its nearest partner)
+__device__ __forceinline__ void activate_creator(const Dev& d, int i, int start, int len, int first) {
   d.cand_start[i] = start;
   d.cand_len[i] = len;
   d.mate[i] = -1;
   d.ptr[i] = 0;
-  d.nom[i] = d.cand[start].x;  // round 0: nobody is matched yet, so the nearest partner
+  d.nom[i] = first;
   atomicOr(&d.bm_ca[i >> 5], 1u << (i & 31));
 }
 
@@ -670,7 +672,7 @@ __device__ __forceinline__ void emit_list(const Dev& d, int e, int i, const Loca
       for (int q = 0; q < cnt; ++q)
         d.cand[at + q] =
             make_int4(ll.kp[q], ll.ki[q], (int)(unsigned)(unsigned long long)ll.kd[q], (int)(ll.kd[q] >> 32));
-      activate_creator(d, i, (int)at, cnt);
+      activate_creator(d, i, (int)at, cnt, ll.kp[0]);
     }
   }
 }
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     // more than MAXC beads within the reach need not leave any candidate
     // once the rule, maxbond and graph-distance tests run: such a bead takes
     // no part in the matching (its nomination would read a stale entry)
-    if (cv.cnt > 0) activate_creator(d, i, (int)at, cv.cnt);
+    if (cv.cnt > 0) activate_creator(d, i, (int)at, cv.cnt, lst[0].x);
     stat_add(d, rep_of(d, i), ST_CANDIDATES, pairs);
   }
 }

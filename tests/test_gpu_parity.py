@@ -392,7 +392,7 @@ def test_staged_and_global_candidate_search_agree(cell_scale, cell_zdiv):
     s = W.scaled_config4(8192)
     D = dynbond()
     geo = dict(cell_scale=cell_scale, cell_zdiv=cell_zdiv)
-    a = D.Context(s, params=geo)
+    a = D.Context(s, params=geo, flags=D.FLAG_STAGED_SEARCH)
     b = D.Context(s, params=geo, flags=D.FLAG_GLOBAL_SEARCH)
     assert a.tuning()["tiles"] == 1 and b.tuning()["tiles"] == 0
     for k in range(3):
