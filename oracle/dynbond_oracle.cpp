@@ -20,6 +20,9 @@
 //   step 9  interaction creation -> typed records for every non-cyclic 3-/4-path
 //                                   of the new graph that contains a new bond
 //   step 10 statistics
+// Beside the call: the FP64 bonded forces of the resulting topology
+// (orc_forces) and the DPD pair forces of Sec. 3 on a snapshot
+// (orc_dpd_forces), each pinned by its own tests.
 // Readings taken where the paper is silent or ambiguous (all listed in the
 // design notes):
 //   * distances: positions are int32 on a 2^-20 sigma grid, squared distances
