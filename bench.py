@@ -257,6 +257,37 @@ def profiled_phases(system, snaps, warmup, steps, flush, stream, geo=None):
     return {k: float(np.mean(v)) for k, v in phases.items()}
 
 
+def tuning_params(tuning):
+    """Context parameters that reproduce a tuned geometry (cell edge and z
+    division) without running the autotuner again."""
+    if not tuning:
+        return {}
+    return dict(cell_scale=int(round(tuning["cell_scale"])) if float(tuning["cell_scale"]).is_integer() else 0,
+                cell_zdiv=int(tuning["cell_zdiv"]))
+
+
+def time_calls(ctx, snaps, warmup, steps, flush, stream, force, ev):
+    """Device time (ms, summed) of `steps` step + forces calls after `warmup`
+    untimed ones, L2 flushed before each, CUDA events on the stream."""
+    import torch
+    for k in range(warmup):
+        ctx.step(snaps[k], k)
+        ctx.forces(snaps[k], force, ev)
+    torch.cuda.synchronize()
+    total = 0.0
+    for k in range(warmup, warmup + steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.step(snaps[k], k)
+        ctx.forces(snaps[k], force, ev)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -304,6 +335,11 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
     total_ms = max_over_ranks(float(np.sum(times)), dev)
+    # the same calls with the whole step as one persistent launch
+    ctx_q = dynbond.Context(s, stream=stream, params=dict(geo or {}, **tuning_params(tuning)),
+                            flags=dynbond.FLAG_PERSISTENT)
+    persist_ms = time_calls(ctx_q, snaps, Wm, K, flush, stream, force, ev) / K
+    ctx_q.close()
     # per-phase device times from a second context that records events
     # between the phases (events inside the replayed work serialize the
     # kernels, so the headline above is timed without them)
@@ -315,7 +351,7 @@ def run_gpu(args):
     ctx.forces(snaps[-1], force, ev)
     ctx.sync()
     value = whole_job_value(N, K, world, total_ms / 1e3)
-    result = dict(value=value, ms=total_ms / K, N=N, R=R, phases=phases,
+    result = dict(value=value, ms=total_ms / K, N=N, R=R, phases=phases, persistent_ms=persist_ms,
                   stats=stats, na_before=na_before, nd_before=nd_before, clocks=clk.summary(), rank=rank,
                   world=world, name=s.name, tuning=tuning)
 
@@ -388,6 +424,13 @@ def run_batched(steps: int, warmup: int):
         ctx.step(pos_all[k], k)
         ctx.forces(pos_all[k], f, ev)
     t_b = timed(batched_call)
+    ctx_q = dynbond.Context(full, stream=stream, params=tuning_params(tuning), flags=dynbond.FLAG_PERSISTENT)
+
+    def persistent_call(k):
+        ctx_q.step(pos_all[k], k)
+        ctx_q.forces(pos_all[k], f, ev)
+    t_q = timed(persistent_call)
+    ctx_q.close()
     # one more (untimed) call for the algorithmic byte count of a call
     topo = ctx.topology()
     na0, nd0 = topo[1].shape[0], topo[2].shape[0]
@@ -423,6 +466,8 @@ def run_batched(steps: int, warmup: int):
     phases = profiled_phases(full, pos_all, warmup, steps, flush, stream)
     return dict(workload=full.name, replicas=full.n_replicas, beads=N, steps=steps, warmup=warmup,
                 value=vb, ms_per_step=t_b / steps, plain_value=vp, plain_ms_per_step=t_p / steps,
+                persistent=dict(ms_per_step=t_q / steps, value=N * steps / (t_q / 1e3),
+                                note="the same calls with each step one persistent cooperative launch"),
                 speedup=vb / vp, tuning=tuning, unit=UNIT,
                 plain="one context per replica, called one after another on one stream",
                 phases_ms=phases,
@@ -566,6 +611,8 @@ def main():
         step_roofline=dict(bound="hbm", algorithmic_bytes=alg, achieved=step_gbs, peak=peak, unit="GB/s",
                            frac=step_gbs / peak, peak_source=peak_kind),
         phases_ms=ph, cpu_baseline=cpu, e2e=res["e2e"], gpu_launches=kernels_per_step * args.steps,
+        persistent=dict(ms_per_step=res["persistent_ms"], value=res["N"] * res["world"] / (res["persistent_ms"] * 1e-3),
+                        note="the same calls with each step one persistent cooperative launch"),
         clocks=res["clocks"], stats_last_call=res["stats"], batched=batched, melt=melt,
     )
     print(json.dumps(line), flush=True)

@@ -109,10 +109,15 @@ enum {
   DYNBOND_FLAG_NO_PDL = 8,      /* launch each kernel only after the previous one ends (no programmatic
                                    dependent launch); results are identical either way */
   DYNBOND_FLAG_GLOBAL_SEARCH = 16, /* candidate search always walks the cell lists in global memory */
-  DYNBOND_FLAG_STAGED_SEARCH = 32  /* candidate search always stages tiles of cell columns in shared memory
+  DYNBOND_FLAG_STAGED_SEARCH = 32, /* candidate search always stages tiles of cell columns in shared memory
                                       where the geometry allows it (without either flag the autotuner
                                       times both; untuned contexts use the global search); results are
                                       identical either way */
+  DYNBOND_FLAG_PERSISTENT = 64     /* each dynbond_step is one persistent cooperative launch whose blocks run
+                                      the call's phases one after another with bounded grid barriers
+                                      (instead of a graph of one kernel per phase; not with
+                                      DYNBOND_FLAG_PROFILE, whose phase events need the kernels apart);
+                                      the candidate search is then the global one; results are identical */
 };
 
 /*

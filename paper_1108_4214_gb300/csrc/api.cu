@@ -69,6 +69,8 @@ struct dynbond_ctx {
   bool tiles_on = false;        // autotuner's choice between staged and global search (global until timed)
   bool global_search = false;   // DYNBOND_FLAG_GLOBAL_SEARCH
   bool staged_search = false;   // DYNBOND_FLAG_STAGED_SEARCH
+  bool persistent = false;      // DYNBOND_FLAG_PERSISTENT (and not profiling)
+  int grid_persist = 0;
   int grid_ctile = 0;
   bool tuned = false;
 };
@@ -322,9 +324,28 @@ cudaError_t launch_candidates(dynbond_ctx* c) {
   return launch(c, c->octant ? k_candidates_oct : k_candidates, c->grid_cand, 256, c->d, (const RuleTab*)c->d_rt);
 }
 
+// the whole call as one persistent cooperative launch (DYNBOND_FLAG_PERSISTENT)
+cudaError_t launch_persistent(dynbond_ctx* c) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(c->grid_persist);
+  cfg.blockDim = dim3(256);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, c->octant ? k_step_persistent_oct : k_step_persistent, c->d,
+                            (const RuleTab*)c->d_rt);
+}
+
 cudaError_t enqueue_step(dynbond_ctx* c) {
   const Dev& d = c->d;
   size_t k = 0;
+  if (c->persistent) {
+    E(launch_persistent(c));
+    return cudaGetLastError();
+  }
   mark(c, c->ev_step, k++);
   E(launch(c, k_setup, c->nsm * 2, 1024, d));
   mark(c, c->ev_step, k++);
@@ -592,6 +613,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->use_graph = (params->flags & DYNBOND_FLAG_NO_GRAPH) == 0;
   c->pdl = (params->flags & DYNBOND_FLAG_NO_PDL) == 0;
   c->global_search = (params->flags & DYNBOND_FLAG_GLOBAL_SEARCH) != 0;
+  c->persistent = (params->flags & DYNBOND_FLAG_PERSISTENT) != 0 && !c->profile;
   c->staged_search = !c->global_search && (params->flags & DYNBOND_FLAG_STAGED_SEARCH) != 0;
   c->tiles_on = c->staged_search;
   if (params->max_rounds < 0 || params->prob_mode < 0 || params->prob_mode > 1 || params->cell_scale < 0)
@@ -854,6 +876,9 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   for (auto fn : {(const void*)k_candidates_tile, (const void*)k_candidates_tile_oct})
     CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, CAND_TILE_SMEM));
   c->grid_ctile = occupancy_grid(c, (const void*)k_candidates_tile, 256, 8, CAND_TILE_SMEM);
+  // persistent call: every block resident (cooperative launch), at most two per SM
+  c->grid_persist = std::min(occupancy_grid(c, (const void*)k_step_persistent, 256, 2),
+                             occupancy_grid(c, (const void*)k_step_persistent_oct, 256, 2));
   c->grid_seg = c->nsm * 4;
   // matching: co-resident blocks (cooperative launch), at most two per SM so
   // the grid barriers between rounds stay short; round 0 gives each lane one
@@ -914,7 +939,8 @@ dynbond_status dynbond_step(dynbond_ctx* c, const int32_t* d_pos, uint64_t step,
     dynbond_status st = dynbond_autotune(c, d_pos, nullptr);
     if (st) return st;
   }
-  k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, step, 1, 0);
+  k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, step, 1, 0,
+                                     c->persistent ? &c->d.cnt->bar[1] : nullptr);
   cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_step, c->stream) : enqueue_step(c);
   if (e != cudaSuccess) {
     c->sticky = DYNBOND_ECUDA;
@@ -935,7 +961,7 @@ dynbond_status dynbond_forces(dynbond_ctx* c, const int32_t* d_pos, float* d_for
   if (!aligned16(d_pos) || !aligned16(d_force))
     return fail(c, DYNBOND_EINVAL, "d_pos and d_force must be 16-byte aligned (4-vectors per bead)");
   if (c->sticky) return c->sticky;
-  k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, (float4*)d_force, d_ev, 0, 0, 1);
+  k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, (float4*)d_force, d_ev, 0, 0, 1, nullptr);
   cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_forces, c->stream) : enqueue_forces(c);
   if (e != cudaSuccess) {
     c->sticky = DYNBOND_ECUDA;
@@ -973,7 +999,7 @@ dynbond_status dynbond_autotune(dynbond_ctx* c, const int32_t* d_pos, dynbond_tu
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
-    k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, 0, 1, 0);
+    k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, nullptr, nullptr, 0, 1, 0, nullptr);
     const int zdivs[] = {1, 2, 4};
     float best = 1e30f;
     double best_scale = 1.0;

@@ -243,8 +243,10 @@ __global__ void k_purge(Dev d);
 __global__ void k_fill(Dev d);
 __global__ void k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new);
 __global__ void k_setup(Dev d);
+__global__ void k_step_persistent(Dev d, const RuleTab* __restrict__ rtp);
+__global__ void k_step_persistent_oct(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
-                           int set_pos, int set_force);
+                           int set_pos, int set_force, unsigned* bar_reset);
 
 // the context's bond slots and geometry, for the MD harness (defined in api.cu)
 const uint4* internal_slots(const dynbond_ctx* ctx, long long* n_beads, long long* box_q, int* n_replicas,

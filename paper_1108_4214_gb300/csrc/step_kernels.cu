@@ -150,8 +150,7 @@ __device__ __forceinline__ unsigned bead_breakage(const Dev& d, const RuleTab& r
 // Which beads can form a bond, and which hold a breakable bond, depends on
 // their bonds only: both bitmaps are computed at creation (k_bead_flags) and
 // kept current by the edit, so this pass reads positions and the bitmap.
-__global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
-  pdl_enter();
+__device__ __forceinline__ void bead_body(const Dev& d, const RuleTab* __restrict__ rtp) {
   const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
@@ -176,6 +175,11 @@ __global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__
     }
     d.bead_cell[i] = cell;
   }
+}
+
+__global__ void __launch_bounds__(256) k_bead(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
+  bead_body(d, rtp);
 }
 
 // Both bead bitmaps from the bonds, for every bead (at creation).
@@ -203,9 +207,7 @@ __global__ void __launch_bounds__(256) k_bead_flags(Dev d, const RuleTab* __rest
 // ---------------------------------------------------------------------------
 // k_scan_cells: in-place exclusive scan of the cell histogram
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
-  pdl_enter();
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void scan_cells_body(const Dev& d) {
   __shared__ long long sh[33];
   __shared__ long long s_excl;
   __shared__ long long s_tile;
@@ -276,13 +278,17 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  scan_cells_body(d);
+}
+
 // The last scatter_blocks blocks: counting-sort scatter of the binned beads
 // into cell order.  The others: breakage nomination of the beads of the
 // breakage bitmap (independent work, run beside the scatter to share its
 // latency), with their edit / nomination bits OR-ed into the activity bitmaps.
-__global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
-  pdl_enter();
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void scatter_body(const Dev& d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
   const int4* __restrict__ pos = d.args->pos;
   // the breakage blocks come first, so their longer dependent chains start
   // with the first wave instead of trailing the scatter
@@ -334,6 +340,12 @@ __global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restric
   cnt.flush_block(tg);
   // settled pairs count as round-0 breakage matches of their replica
   block_flag(d.round_hit + d.R, hit_r);
+}
+
+__global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  scatter_body(d, rtp, scatter_blocks);
 }
 
 // ---------------------------------------------------------------------------
@@ -679,8 +691,6 @@ __device__ __forceinline__ void emit_list(const Dev& d, int e, int i, const Loca
 
 template <int GEO>
 __device__ __forceinline__ void candidates_body(const Dev& d, const RuleTab* __restrict__ rtp) {
-  pdl_enter();
-  if (aborted(d.err)) return;
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
   const long long r2max = rtp->r2max;
@@ -716,9 +726,13 @@ __device__ __forceinline__ void candidates_body(const Dev& d, const RuleTab* __r
 }
 
 __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
+  if (aborted(d.err)) return;
   candidates_body<0>(d, rtp);
 }
 __global__ void __launch_bounds__(256, 3) k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
+  if (aborted(d.err)) return;
   candidates_body<1>(d, rtp);
 }
 
@@ -1036,9 +1050,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates_tile_oct(Dev d, const Rul
 
 // Exact path for beads with more than MAXC candidates: count, allocate,
 // write, then sort the bead's list by (d2, partner) in place.
-__global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp) {
-  pdl_enter();
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void cand_overflow_body(const Dev& d, const RuleTab* __restrict__ rtp) {
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
   const long long r2max = rtp->r2max;
@@ -1081,6 +1093,12 @@ __global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __r
     if (cv.cnt > 0) activate_creator(d, i, (int)at, cv.cnt, lst[0].x);
     stat_add(d, rep_of(d, i), ST_CANDIDATES, pairs);
   }
+}
+
+__global__ void __launch_bounds__(128) k_cand_overflow(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  cand_overflow_body(d, rtp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1126,9 +1144,7 @@ __device__ __forceinline__ void flag_round(const Dev& d, int round, int sys, int
 // Rounds run over the grid with warp-level list appends and counters (no
 // block barrier inside a round) and one bounded grid barrier between rounds;
 // once few beads are left, block 0 finishes alone with block barriers.
-__global__ void __launch_bounds__(MATCH_THREADS) k_match(Dev d, const RuleTab* __restrict__ rtp) {
-  pdl_wait();  // cooperative: its successor is scheduled only when it ends
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void match_body(const Dev& d, const RuleTab* __restrict__ rtp, unsigned* bar) {
   const RuleTab& rt = *rtp;
   const long long N = d.N;
   const int R = d.R;
@@ -1231,7 +1247,7 @@ __global__ void __launch_bounds__(MATCH_THREADS) k_match(Dev d, const RuleTab* _
     flag_round(d, round, 0, hr[0]);
     flag_round(d, round, 1, hr[1]);
     if (solo) __syncthreads();
-    else if (!grid_sync(d.cnt->bar, d.spin_limit, d.err)) return;
+    else if (!grid_sync(bar, d.spin_limit, d.err)) return;
     const int matched = ld_cg(&d.cnt->round_matched[round]);
     if (blockIdx.x == 0) {
       int* flags = d.round_hit + (round & 1) * 2 * R;
@@ -1262,6 +1278,12 @@ __global__ void __launch_bounds__(MATCH_THREADS) k_match(Dev d, const RuleTab* _
   }
   matched_pairs.flush_block(tg);
   if (blockIdx.x == 0 && threadIdx.x == 0) d.cnt->rounds_done = round;
+}
+
+__global__ void __launch_bounds__(MATCH_THREADS) k_match(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_wait();  // cooperative: its successor is scheduled only when it ends
+  if (aborted(d.err)) return;
+  match_body(d, rtp, d.cnt->bar);
 }
 
 // ---------------------------------------------------------------------------
@@ -1365,9 +1387,7 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
   if (conv_partner > i) o.conv_hi = conv_partner;
 }
 
-__global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__ rtp) {
-  pdl_enter();
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void edit_body(const Dev& d, const RuleTab* __restrict__ rtp) {
   const RuleTab& rt = *rtp;
   const CountTargets<5> tg{{d.stats + ST_KILLED, d.stats + ST_BROKEN, d.stats + ST_CONVERTED, d.stats + ST_FORMED,
                             d.n_bonds},
@@ -1402,6 +1422,12 @@ __global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__
     if (nv) d.nbl[at] = make_int4((int)i, o.conv_hi, r, 0);
   });
   counts.flush_block(tg);
+}
+
+__global__ void __launch_bounds__(256) k_edit(Dev d, const RuleTab* __restrict__ rtp) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  edit_body(d, rtp);
 }
 
 // per-replica tile bases: base[r] = tiles of replicas before r, base[R] = all
@@ -1520,9 +1546,7 @@ __device__ __forceinline__ bool record_gone(const Dev& d, const unsigned* s_coar
   return record_gone(d, v, dih);
 }
 
-__global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) {
-  pdl_enter();
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void purge_body(const Dev& d) {
   __shared__ unsigned s_coarse[PURGE_COARSE_WORDS];
   for (long long k = threadIdx.x; k < d.Wc; k += blockDim.x) s_coarse[k] = d.bm_dirtyc[k];
   __syncthreads();
@@ -1578,9 +1602,13 @@ __global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) 
   block_tile_bases(d.fill_items, R, FILL_TILE, d.tb_fill, nullptr);
 }
 
-__global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
+__global__ void __launch_bounds__(PURGE_TILE / PURGE_PER_THREAD) k_purge(Dev d) {
   pdl_enter();
   if (aborted(d.err)) return;
+  purge_body(d);
+}
+
+__device__ __forceinline__ void fill_body(const Dev& d) {
   const int R = d.R;
   const int ntiles = d.tb_fill[R];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1619,6 +1647,12 @@ __global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
       recs[hole] = recs[mover];
     }
   }
+}
+
+__global__ void __launch_bounds__(FILL_TILE) k_fill(Dev d) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  fill_body(d);
 }
 
 // ---------------------------------------------------------------------------
@@ -1767,9 +1801,7 @@ __device__ __forceinline__ void reserve(const Dev& d, int r, int na, int nd, int
   *od = __shfl_sync(FULL, bd, leader) + pd;
 }
 
-__global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new) {
-  pdl_enter();
-  if (aborted(d.err)) return;
+__device__ __forceinline__ void rebuild_body(const Dev& d, const RuleTab* __restrict__ rtp, int all_new) {
   const RuleTab& rt = *rtp;
   const Rebuild rb{d, rt, all_new};
   // five independent parts per new bond, part-major: the lanes of a warp run
@@ -1818,15 +1850,25 @@ __global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restric
   block_tile_bases(d.n_dih, d.R, FORCE_TILE, d.tb_fdih, nullptr);
 }
 
+__global__ void __launch_bounds__(256) k_rebuild(Dev d, const RuleTab* __restrict__ rtp, int all_new) {
+  pdl_enter();
+  if (aborted(d.err)) return;
+  rebuild_body(d, rtp, all_new);
+}
+
 // Per-call setup (one launch): zero the counters, the cell histogram, the
 // creation-active bitmap, the per-replica scratch and the look-back status
 // words; block 0 also computes the purge tile bases from the list counts.
-__global__ void __launch_bounds__(1024) k_setup(Dev d) {
-  pdl_enter();
+// keep_bar: leave the persistent call's barrier counter (bar[1]) alone, for
+// the setup phase of k_step_persistent, whose blocks count on it
+__device__ __forceinline__ void setup_body(const Dev& d, bool keep_bar) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   int* cnt = reinterpret_cast<int*>(d.cnt);
-  for (long long k = g; k < (long long)(sizeof(Counters) / sizeof(int)); k += stride) cnt[k] = 0;
+  const long long bar1 = (reinterpret_cast<const char*>(&d.cnt->bar[1]) - reinterpret_cast<const char*>(d.cnt)) /
+                         (long long)sizeof(int);
+  for (long long k = g; k < (long long)(sizeof(Counters) / sizeof(int)); k += stride)
+    if (!keep_bar || k != bar1) cnt[k] = 0;
   for (long long k = g; k <= d.n_keys; k += stride) d.cell_start[k] = 0;
   for (long long k = g; k < d.W; k += stride) {
     d.bm_ca[k] = 0;
@@ -1845,8 +1887,59 @@ __global__ void __launch_bounds__(1024) k_setup(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(1024) k_setup(Dev d) {
+  pdl_enter();
+  setup_body(d, false);
+}
+
+// ---------------------------------------------------------------------------
+// k_step_persistent: the whole call as one cooperative launch.  The blocks
+// stay resident and run the phases of the launch sequence above one after
+// another -- setup, binning, scan, scatter and breakage nomination, candidate
+// search, overflow lists, matching rounds, edit, purge, hole filling,
+// rebuild -- each over all blocks' work items, separated by bounded grid
+// barriers on bar[1] (which keeps counting across calls: every call adds the
+// same number of arrivals per block).  After a device error every phase is
+// skipped but every barrier is still met.
+// ---------------------------------------------------------------------------
+template <int GEO>
+__device__ __forceinline__ void step_persistent_body(const Dev& d, const RuleTab* __restrict__ rtp) {
+  unsigned* bar = &d.cnt->bar[1];
+  setup_body(d, true);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  bead_body(d, rtp);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) scan_cells_body(d);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) scatter_body(d, rtp, gridDim.x / 2);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) candidates_body<GEO>(d, rtp);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) cand_overflow_body(d, rtp);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) match_body(d, rtp, bar);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) edit_body(d, rtp);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) purge_body(d);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) fill_body(d);
+  if (!grid_sync(bar, d.spin_limit, d.err)) return;
+  if (!aborted(d.err)) rebuild_body(d, rtp, 0);
+}
+
+__global__ void __launch_bounds__(256, 2) k_step_persistent(Dev d, const RuleTab* __restrict__ rtp) {
+  step_persistent_body<0>(d, rtp);
+}
+__global__ void __launch_bounds__(256, 2) k_step_persistent_oct(Dev d, const RuleTab* __restrict__ rtp) {
+  step_persistent_body<1>(d, rtp);
+}
+
+// bar_reset (nullable): the persistent call's barrier counter, restarted at
+// zero before each call (it counts every block's arrivals within a call)
 __global__ void k_set_args(CallArgs* a, const int4* pos, float4* force, double* ev, unsigned long long step,
-                           int set_pos, int set_force) {
+                           int set_pos, int set_force, unsigned* bar_reset) {
+  if (bar_reset) *bar_reset = 0u;
   if (set_pos) {
     a->pos = pos;
     a->step = step;

@@ -21,6 +21,7 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ETI
 KINDS = dict(createbond=1, createdirbond=2, breakbond=3, convertbond=4, killbond=5, createangle=6,
              createdihedral=7, maxbond=8)
 FLAG_NO_GRAPH, FLAG_PROFILE, FLAG_NO_AUTOTUNE, FLAG_NO_PDL, FLAG_GLOBAL_SEARCH, FLAG_STAGED_SEARCH = 1, 2, 4, 8, 16, 32
+FLAG_PERSISTENT = 64
 STAT_NAMES = [
     "candidates", "create_matched", "bonds_formed", "break_candidates", "break_matched", "bonds_broken",
     "bonds_killed", "bonds_converted", "angles_removed", "angles_added", "dihedrals_removed", "dihedrals_added",

@@ -400,3 +400,54 @@ def test_staged_and_global_candidate_search_agree(cell_scale, cell_zdiv):
         assert np.array_equal(a.step(p, k, stats=True), b.step(p, k, stats=True)), k
     for x, y in zip(a.topology(), b.topology()):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("cell_scale,cell_zdiv", [(0, 0), (1, 1), (2, 1), (1, 4)])
+def test_persistent_call_matches_the_oracle(cell_scale, cell_zdiv):
+    """The whole call as one persistent cooperative launch (phases separated
+    by bounded grid barriers): bit-exact against the oracle on plain-2048."""
+    D = dynbond()
+    run_parity(W.config1(), 6, params=dict(cell_scale=cell_scale, cell_zdiv=cell_zdiv), flags=D.FLAG_PERSISTENT)
+
+
+@pytest.mark.parametrize("seed", [1, 5, 8, 13, 22, 27, 31, 38])
+def test_persistent_call_on_random_systems(seed):
+    D = dynbond()
+    rules = W.random_rules(seed)
+    s = W.random_small_system(seed, n_beads=60, box=3.0 + seed % 3, n_bonds=50, rules=rules,
+                              n_replicas=1 + seed % 3,
+                              params=dict(paircheck13=seed % 2, paircheck14=(seed // 2) % 2, max_rounds=seed % 3,
+                                          prob_mode=(seed // 3) % 2))
+    run_parity(s, 4, flags=D.FLAG_PERSISTENT)
+
+
+def test_persistent_call_on_batches_and_at_1m():
+    """Persistent launches on 48 uneven replicas against the oracle, and on
+    the 1M-bead system against the graph of one kernel per phase."""
+    D = dynbond()
+    full = W.config3(n_replicas=48)
+    run_parity(full, 3, snaps=full.snapshots(0, 3), flags=D.FLAG_PERSISTENT)
+    s = W.config2()
+    a = D.Context(s, params=dict(cell_scale=2))
+    b = D.Context(s, params=dict(cell_scale=2), flags=D.FLAG_PERSISTENT)
+    for k in range(3):
+        p = torch.from_numpy(s.snapshot(k)).cuda()
+        assert np.array_equal(a.step(p, k, stats=True), b.step(p, k, stats=True)), k
+    for x, y in zip(a.topology(), b.topology()):
+        assert np.array_equal(x, y)
+
+
+def test_persistent_call_bounded_barrier_gives_up_cleanly():
+    """With every wait limited to one poll the persistent call's first grid
+    barrier gives up: ETIMEOUT is reported and the CUDA context stays usable."""
+    D = dynbond()
+    s = W.config2()
+    pos = torch.from_numpy(s.snapshot(0)).cuda()
+    status = None
+    try:
+        ctx = D.Context(s, params=dict(spin_limit=1, cell_scale=2), flags=D.FLAG_PERSISTENT)
+        ctx.step(pos, 0, stats=True)
+    except D.DynbondError as e:
+        status = e.status
+    assert status == 5
+    assert torch.ones(1000, device="cuda").sum().item() == 1000.0
