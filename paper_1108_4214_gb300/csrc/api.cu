@@ -57,6 +57,7 @@ struct dynbond_ctx {
   long long max_cells = 0;      // cells allocated (geometry at scale 1)
   int* d_nc = nullptr;
   int* d_ncz = nullptr;
+  int4* d_geo = nullptr;
   long long* d_cb = nullptr;
   dynbond_tuning tuning{};
   unsigned long long* d_hash = nullptr;  // per-replica topology hashes
@@ -497,7 +498,19 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
   c->d.n_cells = c->n_cells;
   c->d.n_keys = c->n_cells * c->rt.n_cls;
   c->grid_scan = bounded_grid(c->d.n_keys, 256 * SCAN_PER_THREAD, c->nsm * 4);
+  std::vector<int4> geo(2 * R);
+  for (int r = 0; r < R; ++r) {
+    const long long L = c->h_box[r];
+    const float fxy = (float)nc[r] / (float)L, fz = (float)nz[r] / (float)L;
+    int bxy, bz;
+    std::memcpy(&bxy, &fxy, 4);
+    std::memcpy(&bz, &fz, 4);
+    const long long hz = (c->reach * nz[r] + L - 1) / L;
+    geo[2 * r] = make_int4((int)L, nc[r], nz[r], (int)hz);
+    geo[2 * r + 1] = make_int4(bxy, bz, (int)cb[r], 0);
+  }
   if (c->d_nc) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_geo, geo.data(), sizeof(int4) * 2 * R, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_nc, nc.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_ncz, nz.data(), 4 * R, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cb, cb.data(), 8 * (R + 1), cudaMemcpyHostToDevice, c->stream));
@@ -705,6 +718,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(p_cb, R + 1);
   ALLOC(p_nc, R);
   ALLOC(p_ncz, R);
+  ALLOC(c->d_geo, 2 * R);
   c->d_nc = p_nc;
   c->d_ncz = p_ncz;
   c->d_cb = p_cb;
@@ -813,6 +827,7 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   d.cell_base = p_cb;
   d.nc = p_nc;
   d.ncz = p_ncz;
+  d.geo = c->d_geo;
   d.reach = c->reach;
   d.rep = p_rep;
   d.type = p_type;

@@ -99,6 +99,9 @@ struct Dev {
   const long long* box;        // [R]
   const int* nc;               // [R] cells along x and y
   const int* ncz;              // [R] cells along z
+  // [2R] per replica: (L, nc, nz, hz) and (nc / L, nz / L as float bits, cell_base, 0); hz = ceil(reach nz / L),
+  // the z cells a reach interval can extend beyond its bead's cell on either side
+  const int4* geo;
   long long reach;              // smallest integer >= the largest creation distance (quantised units)
   const long long* cell_base;  // [R+1]
   long long n_cells;            // cells of one class (all replicas)

@@ -97,9 +97,11 @@ struct BondStage {
 };
 static_assert(sizeof(BondStage) == BF_SMEM_BYTES, "bond shared memory layout");
 
-__global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ff) {
+__global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ffp) {
   pdl_enter();
   if (aborted(d.err)) return;
+  __shared__ FF s_ff;
+  const FF& ff = ff_to_shared(ffp, s_ff);
   extern __shared__ __align__(16) unsigned char bf_smem[];
   BondStage& sm = *reinterpret_cast<BondStage*>(bf_smem);
   const int4* __restrict__ pos = d.args->pos;
@@ -310,9 +312,11 @@ struct AdStage {
 
 static_assert(sizeof(AdStage) == AD_SMEM_BYTES, "angle / dihedral shared memory layout");
 
-__global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF ff) {
+__global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF ffp) {
   pdl_enter();
   if (aborted(d.err)) return;
+  __shared__ FF s_ff;
+  const FF& ff = ff_to_shared(ffp, s_ff);
   extern __shared__ __align__(16) unsigned char ad_smem[];
   AdStage& sm = *reinterpret_cast<AdStage*>(ad_smem);
   const int4* __restrict__ pos = d.args->pos;

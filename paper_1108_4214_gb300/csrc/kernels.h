@@ -62,6 +62,26 @@ inline bool make_ff(const dynbond_forcefield& in, FF& out) {
   return true;
 }
 
+// The block's copy of a force field in shared memory.  Terms of different
+// types meet in one warp, and a per-type lookup with lane-dependent indices
+// replays in the constant bank once per distinct address; from shared memory
+// it is one access.  Every thread of the block must call it.
+__device__ __forceinline__ const FF& ff_to_shared(const FF& ff, FF& s) {
+  const int t = threadIdx.x;
+  if (t < 16) {
+    s.bond_k[t] = ff.bond_k[t];
+    s.bond_r0[t] = ff.bond_r0[t];
+    s.angle_k[t] = ff.angle_k[t];
+    s.dih_k[t] = ff.dih_k[t];
+    s.dih_d[t] = ff.dih_d[t];
+    s.bond_r0q2[t] = ff.bond_r0q2[t];
+    s.angle_pt0[t] = ff.angle_pt0[t];
+  }
+  if (t == 0) s.angle_harm = ff.angle_harm;
+  __syncthreads();
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // Per-term force arithmetic shared by the context's force kernels and the
 // allocation-free entry point.  Every term starts from exact integer
@@ -125,7 +145,7 @@ __device__ __forceinline__ BondHalf bond_half_force(const FF& ff, int t, int3 d)
   const long long q2 = doti(d, d);
   const float q2f = (float)q2, rs = rsqrtf(q2f);  // 1 / |d| in quantized units
   const float r = q2f * rs * s20;
-  const float dr = (float)(q2 - ff.bond_r0q2[t]) * (s20 * s20) * __frcp_rn(r + ff.bond_r0[t]);
+  const float dr = __fdividef((float)(q2 - ff.bond_r0q2[t]) * (s20 * s20), r + ff.bond_r0[t]);
   o.f = scale(-2.0f * ff.bond_k[t] * dr * (rs * 1048576.0f), o.rij);
   o.E = 0.5f * ff.bond_k[t] * dr * dr;
   return o;

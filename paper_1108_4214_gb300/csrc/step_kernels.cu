@@ -155,25 +155,43 @@ __device__ __forceinline__ void bead_body(const Dev& d, const RuleTab* __restric
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const int r = rep_of(d, i);
-    const int4 p = pos[i];
-    const bool elig = (d.bm_elig[i >> 5] >> (i & 31)) & 1u;
-    const int L = (int)d.box[r];
-    int cell = -1;
-    if (p.x < 0 || p.y < 0 || p.z < 0 || p.x >= L || p.y >= L || p.z >= L) {
-      atomicOr(d.err, ERR_POS);
-    } else if (elig) {
-      const int bt = d.type[i];
-      const int nc = d.nc[r], nz = d.ncz[r];
-      const float f = (float)nc / (float)L;
-      long long cx = cell_of(p.x, nc, L, f), cy = cell_of(p.y, nc, L, f);
-      long long cz = cell_of(p.z, nz, L, (float)nz / (float)L);
-      long long c = rt.cls_of[bt] * d.n_cells + d.cell_base[r] + (cx * nc + cy) * nz + cz;
-      atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
-      cell = (int)c;
+  constexpr int U = 4;  // beads per thread and pass, their loads issued together
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += U * stride) {
+    int4 p[U];
+    unsigned ew[U];
+    int rr[U], bt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * stride;
+      if (i < N) {
+        p[u] = pos[i];
+        ew[u] = d.bm_elig[i >> 5];
+        rr[u] = rep_of(d, i);
+        bt[u] = d.type[i];
+      }
     }
-    d.bead_cell[i] = cell;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * stride;
+      if (i >= N) break;
+      const int r = rr[u];
+      const int4 g0 = d.geo[2 * r];
+      const int L = g0.x;
+      int cell = -1;
+      if (p[u].x < 0 || p[u].y < 0 || p[u].z < 0 || p[u].x >= L || p[u].y >= L || p[u].z >= L) {
+        atomicOr(d.err, ERR_POS);
+      } else if ((ew[u] >> (i & 31)) & 1u) {
+        const int4 g1 = d.geo[2 * r + 1];
+        const int nc = g0.y, nz = g0.z;
+        const float f = __int_as_float(g1.x);
+        long long cx = cell_of(p[u].x, nc, L, f), cy = cell_of(p[u].y, nc, L, f);
+        long long cz = cell_of(p[u].z, nz, L, __int_as_float(g1.y));
+        long long c = rt.cls_of[bt[u]] * d.n_cells + g1.z + (cx * nc + cy) * nz + cz;
+        atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
+        cell = (int)c;
+      }
+      d.bead_cell[i] = cell;
+    }
   }
 }
 
@@ -439,73 +457,86 @@ __device__ __forceinline__ void cand_slow(const uint4* __restrict__ slots, const
   else ++ll->cnt;
 }
 
+// The cells eligible bead `me` (replica r) searches in each cell-list class:
+// NA x NA cell columns (xs x ys, nx distinct per axis; NA = 2 octant, else 3)
+// and along z a window of cells holding every cell that [z - reach, z + reach]
+// overlaps (periodic), as a main run [z0, z1] and, across the boundary, a
+// wrapped run [w0, w1] (empty if w1 < w0; the whole column when it covers it).  The cells of a column are
+// contiguous in cell order, so each run of each column is one contiguous
+// range of the sorted array.  GEO 1: every replica's columns are at least
+// twice the reach wide, and a bead's reach only touches the neighbouring
+// column on the side of the half it sits in (octant of columns); GEO 0: 3 x 3
+// columns, correct for any geometry with columns at least the reach wide.
+struct BeadGeo {
+  int L, nc, nz, cb, nx;
+  int xs[3], ys[3];
+  int z0, z1, w0, w1;
+};
+template <int GEO>
+__device__ __forceinline__ BeadGeo bead_geo(const Dev& d, const int4& me, int r) {
+  BeadGeo g;
+  const int4 g0 = d.geo[2 * r], g1 = d.geo[2 * r + 1];
+  const int L = g0.x, nc = g0.y, nz = g0.z, hz = g0.w;
+  g.L = L;
+  g.nc = nc;
+  g.nz = nz;
+  g.cb = g1.z;  // cell keys fit in 32 bits (n_cls * n_cells < 2^31 is checked on the host)
+  const float f = __int_as_float(g1.x), fz = __int_as_float(g1.y);
+  const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f);
+  g.nx = nc >= 3 ? 3 : nc;
+  g.xs[0] = cx;
+  g.xs[1] = cx + 1 == nc ? 0 : cx + 1;
+  g.xs[2] = cx == 0 ? nc - 1 : cx - 1;
+  g.ys[0] = cy;
+  g.ys[1] = cy + 1 == nc ? 0 : cy + 1;
+  g.ys[2] = cy == 0 ? nc - 1 : cy - 1;
+  // is coordinate x in the lower half of its cell c (exactly: 2 (x nc - c L) < L)?
+  auto lower = [&](int x, int c) { return 2 * ((long long)x * nc - (long long)c * L) < (long long)L; };
+  if (GEO == 1) {
+    g.nx = 2;
+    if (lower(me.x, cx)) g.xs[1] = g.xs[2];
+    if (lower(me.y, cy)) g.ys[1] = g.ys[2];
+  }
+  // z: the cells cz - hz .. cz + hz (periodic), which hold every cell the
+  // reach interval overlaps (floor(a - b) >= floor(a) - ceil(b) and
+  // floor(a + b) <= floor(a) + ceil(b)); the whole column when they cover it
+  const int cz = cell_of(me.z, nz, L, fz);
+  g.w0 = 0;
+  g.w1 = -1;
+  if (2 * hz + 1 >= nz) {
+    g.z0 = 0;
+    g.z1 = nz - 1;
+  } else {
+    const int lo = cz - hz, hi = cz + hz;
+    g.z0 = max(lo, 0);
+    g.z1 = min(hi, nz - 1);
+    if (lo < 0) {
+      g.w0 = lo + nz;
+      g.w1 = nz - 1;
+    } else if (hi >= nz) {
+      g.w0 = 0;
+      g.w1 = hi - nz;
+    }
+  }
+  return g;
+}
+
 // Visit every creation candidate of eligible bead i (sorted entry `me`):
 // for each cell-list class holding partner types of bead i, the entries
-// within the largest creation distance (the reach) among the neighbouring
-// cell columns (distinct columns when a replica has fewer than 3 per axis),
-// restricted along z to the cells overlapping [z - reach, z + reach], are
-// collected first; the rule and graph-distance tests then run on them after
-// the scan, so the lanes of a warp take the rare path together instead of
-// one after another.  GEO 1: every replica's columns are at least twice the
-// reach wide (octant of columns); GEO 0: 3 x 3 columns, correct for any
-// geometry with columns at least the reach wide.
+// within the largest creation distance (the reach) among the cells of
+// bead_geo are collected first; the rule and graph-distance tests then run on
+// them after the scan, so the lanes of a warp take the rare path together
+// instead of one after another.
 template <int GEO>
 __device__ __forceinline__ void scan_candidates(const Dev& d, const RuleTab* __restrict__ rtp, unsigned cmask,
                                                 long long r2max, const int4& me, int i, LocalList* ll, int mode,
                                                 int4** out, int* pj, long long* pd, int* np_out) {
   const int ti = me.w & 15;
   const int r = rep_of(d, i);
-  const int L = (int)d.box[r], nc = d.nc[r], nz = d.ncz[r];
-  // cell keys fit in 32 bits (n_cls * n_cells < 2^31 is checked on the host)
-  const int cb = (int)d.cell_base[r], ncl = (int)d.n_cells;
-  const float f = (float)nc / (float)L;
-  const int cx = cell_of(me.x, nc, L, f), cy = cell_of(me.y, nc, L, f);
-  // x and y: the distinct neighbouring columns.  Columns at least twice the
-  // reach wide: a bead's reach only touches the neighbour on the side of the
-  // half it sits in, so 2 x 2 columns (octant); else 3 x 3.  z: the cells of a
-  // column are contiguous in cell order, so the cells a column contributes
-  // are one or two contiguous runs of the sorted array.
-  const bool oct = GEO == 1;
-  int nx = nc >= 3 ? 3 : nc;
-  int xs[3] = {cx, cx + 1 == nc ? 0 : cx + 1, cx == 0 ? nc - 1 : cx - 1};
-  int ys[3] = {cy, cy + 1 == nc ? 0 : cy + 1, cy == 0 ? nc - 1 : cy - 1};
-  int z0, z1, w0 = 0, w1 = -1;  // main run [z0, z1], wrapped run [w0, w1]
-  // is coordinate x in the lower half of its cell c (exactly: 2 (x nc - c L) < L)?
-  auto lower = [&](int x, int c) { return 2 * ((long long)x * nc - (long long)c * L) < (long long)L; };
-  if (oct) {
-    nx = 2;
-    if (lower(me.x, cx)) xs[1] = xs[2];
-    if (lower(me.y, cy)) ys[1] = ys[2];
-  }
-  // z: the cells overlapping [z - reach, z + reach] (periodic), as a main run
-  // and, across the boundary, a wrapped run; the whole column if they meet
-  {
-    const float fz = (float)nz / (float)L;
-    const long long zlo = (long long)me.z - d.reach, zhi = (long long)me.z + d.reach;
-    if (zlo >= 0 && zhi < L) {
-      z0 = cell_of((int)zlo, nz, L, fz);
-      z1 = cell_of((int)zhi, nz, L, fz);
-    } else if (zlo < 0 && zhi < L) {
-      const int a = cell_of((int)(zlo + L), nz, L, fz), b = cell_of((int)zhi, nz, L, fz);
-      z0 = 0;
-      z1 = a > b ? b : nz - 1;
-      if (a > b) {
-        w0 = a;
-        w1 = nz - 1;
-      }
-    } else if (zlo >= 0 && zhi >= L) {
-      const int a = cell_of((int)zlo, nz, L, fz), b = cell_of((int)(zhi - L), nz, L, fz);
-      z0 = b < a ? a : 0;
-      z1 = nz - 1;
-      if (b < a) {
-        w0 = 0;
-        w1 = b;
-      }
-    } else {
-      z0 = 0;
-      z1 = nz - 1;
-    }
-  }
+  const BeadGeo g = bead_geo<GEO>(d, me, r);
+  const int L = g.L, nc = g.nc, nz = g.nz, cb = g.cb, ncl = (int)d.n_cells, nx = g.nx;
+  const int *xs = g.xs, *ys = g.ys;
+  const int z0 = g.z0, z1 = g.z1, w0 = g.w0, w1 = g.w1;
   int np = 0;
   bool more = false;
   // entries of the NA x NA column runs (NA = 2 octant, else 3), fetched
@@ -1145,6 +1176,8 @@ __device__ __forceinline__ void flag_round(const Dev& d, int round, int sys, int
 // block barrier inside a round) and one bounded grid barrier between rounds;
 // once few beads are left, block 0 finishes alone with block barriers.
 __device__ __forceinline__ void match_body(const Dev& d, const RuleTab* __restrict__ rtp, unsigned* bar) {
+  constexpr int MQ = 4;                              // round-0 jobs per lane and pass
+  __shared__ int s_mq[MATCH_THREADS / 32][32 * 32];  // round-0 job queue per warp (32 words x 32 beads)
   const RuleTab& rt = *rtp;
   const long long N = d.N;
   const int R = d.R;
@@ -1171,9 +1204,12 @@ __device__ __forceinline__ void match_body(const Dev& d, const RuleTab* __restri
     const int tthreads = nb * blockDim.x, tid = bi * blockDim.x + threadIdx.x;
     if (round == 0) {
       // nominations were written by the list producers; a mutual pair is a
-      // match, an unmatched nominator carries over.  Each lane walks one
-      // bitmap word at a time, bead by bead; the warp appends its carries
-      // with one atomic per pass.
+      // match, an unmatched nominator carries over.  Each lane reads one
+      // bitmap word; the warp queues the (bead, system) jobs of its 32 words
+      // in shared memory and takes them MQ per lane at a time, every load of
+      // a pass issued together, so a word with many active beads does not
+      // hold its warp for one dependent chain per bead.
+      int* q = s_mq[threadIdx.x >> 5];
       for (long long w0 = (long long)tid - lane; w0 < d.W; w0 += tthreads) {
         const long long w = w0 + lane;
         unsigned ca = 0, bn = 0;
@@ -1183,30 +1219,58 @@ __device__ __forceinline__ void match_body(const Dev& d, const RuleTab* __restri
           ca = d.bm_ca[w] & vmask;
           bn = d.bm_bn[w] & vmask;
         }
+        // job = bead | creation bit << 28 | breakage bit << 29 (beads < 2^28)
         unsigned todo = ca | bn;
-        while (__any_sync(FULL, todo != 0)) {
-          bool k0 = false, k1 = false;
-          int i = 0;
-          if (todo) {
-            const int bit = __ffs(todo) - 1;
-            todo &= todo - 1;
-            i = (int)(32 * w + bit);
+        const int nj = __popc(todo);
+        const int incl = warp_incl_scan(nj);
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int at = incl - nj; todo; todo &= todo - 1) {
+          const int bit = __ffs(todo) - 1;
+          q[at++] = (int)(32 * w + bit) | (int)(((ca >> bit) & 1u) << 28) | (int)(((bn >> bit) & 1u) << 29);
+        }
+        __syncwarp();
+        for (int t0 = 0; t0 < total; t0 += 32 * MQ) {
+          int job[MQ], j[MQ][2], back[MQ][2];
+#pragma unroll
+          for (int u = 0; u < MQ; ++u) {
+            const int t = t0 + u * 32 + lane;
+            job[u] = t < total ? q[t] : 0;
+          }
+#pragma unroll
+          for (int u = 0; u < MQ; ++u)
+#pragma unroll
+            for (int sys = 0; sys < 2; ++sys)
+              j[u][sys] = (job[u] >> (28 + sys)) & 1 ? d.nom[(sys ? N : 0) + (job[u] & 0x0FFFFFFF)] : -1;
+#pragma unroll
+          for (int u = 0; u < MQ; ++u)
+#pragma unroll
+            for (int sys = 0; sys < 2; ++sys)
+              back[u][sys] = j[u][sys] >= 0 ? ld_cg(d.nom + (sys ? N : 0) + j[u][sys]) : -1;
+          int want = 0;
+#pragma unroll
+          for (int u = 0; u < MQ; ++u) {
+            const int i = job[u] & 0x0FFFFFFF;
+#pragma unroll
             for (int sys = 0; sys < 2; ++sys) {
-              if (!(((sys ? bn : ca) >> bit) & 1u)) continue;
-              const long long o = sys ? N : 0;
-              const int j = d.nom[o + i];
-              if (j >= 0 && ld_cg(d.nom + o + j) == i) {
-                d.mate[o + i] = mate_pack(0, j);
-                if (i < j) count_hit(sys, i);
-              } else if (j >= 0) {
-                (sys ? k1 : k0) = true;
+              if (j[u][sys] < 0) continue;
+              if (back[u][sys] == i) {
+                d.mate[(sys ? N : 0) + i] = mate_pack(0, j[u][sys]);
+                if (i < j[u][sys]) count_hit(sys, i);
+                j[u][sys] = -1;  // matched: no carry
+              } else {
+                ++want;
               }
             }
           }
-          int at = warp_alloc(&d.cnt->round_live[0], (int)k0 + (int)k1);
-          if (k0) dst[at++] = i;
-          if (k1) dst[at] = (int)(1u << 31 | (unsigned)i);
+          int at = warp_alloc(&d.cnt->round_live[0], want);
+#pragma unroll
+          for (int u = 0; u < MQ; ++u) {
+            const int i = job[u] & 0x0FFFFFFF;
+            if (j[u][0] >= 0) dst[at++] = i;
+            if (j[u][1] >= 0) dst[at++] = (int)(1u << 31 | (unsigned)i);
+          }
         }
+        __syncwarp();
       }
     } else {
       // One phase per round: a live bead's nominee is its first list entry
@@ -1928,6 +1992,7 @@ __device__ __forceinline__ void step_persistent_body(const Dev& d, const RuleTab
   if (!aborted(d.err)) rebuild_body(d, rtp, 0);
 }
 
+static_assert(MATCH_THREADS == 256, "the persistent call runs the matching in its 256-thread blocks");
 __global__ void __launch_bounds__(256, 2) k_step_persistent(Dev d, const RuleTab* __restrict__ rtp) {
   step_persistent_body<0>(d, rtp);
 }

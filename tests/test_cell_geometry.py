@@ -6,12 +6,13 @@ as on the device):
    coordinate in the lower half of its column (2 (x nc - c L) < L) reaches
    only its own column and the one below it, and one in the upper half only
    its own and the one above (periodically).
-2. Along z, the cells overlapping the periodic interval [z - reach, z + reach]
-   are the main run and, across the boundary, a wrapped run as the search
-   forms them (or the whole column when those meet), without a cell listed
-   twice and without missing the cell of any coordinate within the reach.
+2. Along z, the window of cells the search forms -- cz - hz .. cz + hz with
+   hz = ceil(reach nz / L), as a main run and, across the boundary, a wrapped
+   run (or the whole column when it covers it) -- lists no cell twice and
+   misses the cell of no coordinate within the reach.
 """
 import numpy as np
+import pytest
 
 
 def cell(x, n, L):
@@ -39,7 +40,25 @@ def test_octant_columns_hold_every_partner_within_reach():
 
 
 def z_runs(z, reach, nz, L):
-    """Main run [z0, z1] and wrapped run [w0, w1] (empty if w1 < w0)."""
+    """Main run [z0, z1] and wrapped run [w0, w1] (empty if w1 < w0): the
+    cells cz - hz .. cz + hz, hz = ceil(reach nz / L), periodic, or the
+    whole column when they cover it."""
+    hz = -(-reach * nz // L)
+    cz = cell(z, nz, L)
+    if 2 * hz + 1 >= nz:
+        return 0, nz - 1, 0, -1
+    lo, hi = cz - hz, cz + hz
+    if lo < 0:
+        return 0, hi, lo + nz, nz - 1
+    if hi >= nz:
+        return lo, nz - 1, 0, hi - nz
+    return lo, hi, 0, -1
+
+
+def z_runs_exact(z, reach, nz, L):
+    """The staged search's runs of a whole staged column: the cells overlapping
+    [z - reach, z + reach] exactly, main run [z0, z1] and wrapped run
+    [w0, w1] (empty if w1 < w0)."""
     zlo, zhi = z - reach, z + reach
     w0, w1 = 0, -1
     if zlo >= 0 and zhi < L:
@@ -59,14 +78,15 @@ def z_runs(z, reach, nz, L):
     return z0, z1, w0, w1
 
 
-def test_z_runs_cover_the_reach_interval_once():
+@pytest.mark.parametrize("runs", [z_runs, z_runs_exact])
+def test_z_runs_cover_the_reach_interval_once(runs):
     rng = np.random.default_rng(6)
     for _ in range(3000):
         L = int(rng.integers(1, 300))
         reach = int(rng.integers(0, 160))
         nz = int(rng.integers(1, 50))
         z = int(rng.integers(0, L))
-        z0, z1, w0, w1 = z_runs(z, reach, nz, L)
+        z0, z1, w0, w1 = runs(z, reach, nz, L)
         cells = list(range(z0, z1 + 1)) + list(range(w0, w1 + 1))
         assert len(cells) == len(set(cells)) and all(0 <= c < nz for c in cells), (L, reach, nz, z)
         for y in range(L):
@@ -134,7 +154,7 @@ def test_staged_z_window_holds_the_bead_run():
             continue
         z = zs[int(rng.integers(0, len(zs)))]
         if whole:
-            a0, a1, b0, b1 = z_runs(z, reach, nz, L)
+            a0, a1, b0, b1 = z_runs_exact(z, reach, nz, L)
             local = list(range(a0, a1 + 1)) + list(range(b0, b1 + 1))
         else:
             cz = cell(z, nz, L)
