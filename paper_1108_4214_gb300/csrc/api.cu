@@ -19,6 +19,8 @@ struct dynbond_ctx {
   int device = 0;
   int nsm = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;                        // the breakage nomination's branch of a call
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // its fork from and join into `stream`
   dynbond_params prm{};
   RuleTab rt{};
   RuleTab* d_rt = nullptr;  // device copy read by the kernels
@@ -33,7 +35,7 @@ struct dynbond_ctx {
   bool use_graph = true;
   bool pdl = true;  // programmatic dependent launch between the kernels of a call
   int block = 256;
-  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_seg = 0, grid_edit = 0;
+  int grid_bead = 0, grid_scan = 0, grid_cand = 0, grid_match = 0, grid_seg = 0, grid_edit = 0, grid_purge = 0;
   int grid_adf = 0, grid_bf = 0;
   long long st_scan_n = 0;
   void* small = nullptr;
@@ -349,20 +351,28 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   }
   mark(c, c->ev_step, k++);
   E(launch(c, k_setup, c->nsm * 2, 1024, d));
+  // the breakage nomination needs only the zeroed per-call state: it runs on
+  // a branch beside the binning, cell list and candidate search, joined
+  // before the matching
+  E(cudaEventRecord(c->ev_fork, c->stream));
+  E(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  k_breakage<<<c->nsm * 4, 256, 0, c->side>>>(d, c->d_rt);
+  E(cudaEventRecord(c->ev_join, c->side));
   mark(c, c->ev_step, k++);
   E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   mark(c, c->ev_step, k++);
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
-  E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
+  E(launch(c, k_scatter, c->grid_bead, 256, d));
   mark(c, c->ev_step, k++);
   E(launch_candidates(c));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   mark(c, c->ev_step, k++);
+  E(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   E(launch_match(c));
   mark(c, c->ev_step, k++);
   E(launch(c, k_edit, c->grid_edit, 256, d, c->d_rt));
   mark(c, c->ev_step, k++);
-  E(launch(c, k_purge, c->nsm * 4, PURGE_TILE / PURGE_PER_THREAD, d));
+  E(launch(c, k_purge, c->grid_purge, PURGE_TILE / PURGE_PER_THREAD, d));
   E(launch(c, k_fill, c->nsm * 4, FILL_TILE, d));
   mark(c, c->ev_step, k++);
   E(launch(c, k_rebuild, c->grid_seg, 256, d, c->d_rt, 0));
@@ -563,7 +573,7 @@ cudaError_t enqueue_front(dynbond_ctx* c) {
   E(launch(c, k_setup, c->nsm * 2, 1024, d));
   E(launch(c, k_bead, c->grid_bead, 256, d, c->d_rt));
   E(launch(c, k_scan_cells, c->grid_scan, 256, d));
-  E(launch(c, k_scatter, c->grid_bead + c->nsm * 4, 256, d, c->d_rt, c->grid_bead));
+  E(launch(c, k_scatter, c->grid_bead, 256, d));
   E(launch_candidates(c));
   E(launch(c, k_cand_overflow, c->nsm, 128, d, c->d_rt));
   return cudaGetLastError();
@@ -605,6 +615,12 @@ void dynbond_destroy(dynbond_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->g_step) cudaGraphExecDestroy(c->g_step);
   if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (cudaEvent_t e : c->ev_step) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_forces) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
@@ -895,6 +911,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   c->grid_persist = std::min(occupancy_grid(c, (const void*)k_step_persistent, 256, 2),
                              occupancy_grid(c, (const void*)k_step_persistent_oct, 256, 2));
   c->grid_seg = c->nsm * 4;
+  // purge: every block resident, so every tile's records are in flight in one wave
+  c->grid_purge = occupancy_grid(c, (const void*)k_purge, PURGE_TILE / PURGE_PER_THREAD, 8);
   // matching: co-resident blocks (cooperative launch), at most two per SM so
   // the grid barriers between rounds stay short; round 0 gives each lane one
   // 32-bead bitmap word
@@ -913,7 +931,10 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   st = device_status(c);
   if (st) return (st);
 
-  // ---- profiling events and graphs
+  // ---- the side branch of a call, profiling events and graphs
+  CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   if (c->profile) {
     c->names_step = {"setup", "bead", "cells", "candidates", "match", "edit", "purge", "rebuild"};
     c->names_forces = {"bond_forces", "angle_dihedral_forces"};

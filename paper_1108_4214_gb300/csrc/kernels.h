@@ -250,7 +250,8 @@ __device__ __forceinline__ DihedralTerm dihedral_term_forces(const FF& ff, int t
 __global__ void k_bead(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_bead_flags(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_scan_cells(Dev d);
-__global__ void k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks);
+__global__ void k_scatter(Dev d);
+__global__ void k_breakage(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_candidates(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp);
 __global__ void k_candidates_tile(Dev d, const RuleTab* __restrict__ rtp);

@@ -302,50 +302,49 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
   scan_cells_body(d);
 }
 
-// The last scatter_blocks blocks: counting-sort scatter of the binned beads
-// into cell order.  The others: breakage nomination of the beads of the
-// breakage bitmap (independent work, run beside the scatter to share its
-// latency), with their edit / nomination bits OR-ed into the activity bitmaps.
-__device__ __forceinline__ void scatter_body(const Dev& d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
+// Counting-sort scatter of the binned beads into cell order, by blocks
+// b = 0 .. nb - 1 of the caller's.
+__device__ __forceinline__ void scatter_part(const Dev& d, int b, int nb) {
   const int4* __restrict__ pos = d.args->pos;
-  // the breakage blocks come first, so their longer dependent chains start
-  // with the first wave instead of trailing the scatter
-  const int nb = gridDim.x - scatter_blocks;
-  if ((int)blockIdx.x >= nb) {
-    const long long stride = (long long)scatter_blocks * blockDim.x;
-    constexpr int U = 4;  // beads per thread and pass, every load issued first
-    for (long long i0 = (long long)(blockIdx.x - nb) * blockDim.x + threadIdx.x; i0 < d.N; i0 += U * stride) {
-      int c[U], at[U];
-      int4 p[U];
+  const long long stride = (long long)nb * blockDim.x;
+  constexpr int U = 4;  // beads per thread and pass, every load issued first
+  for (long long i0 = (long long)b * blockDim.x + threadIdx.x; i0 < d.N; i0 += U * stride) {
+    int c[U], at[U];
+    int4 p[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long i = i0 + u * stride;
-        c[u] = i < d.N ? d.bead_cell[i] : -1;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const long long i = i0 + u * stride;
-        if (c[u] >= 0) {
-          p[u] = pos[i];
-          p[u].w = (int)((i << 4) | d.type[i]);
-        }
-      }
-      // after the scatter cell_start[c] holds the end of cell c, i.e. the start
-      // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (c[u] >= 0) at[u] = atomicAdd(&d.cell_start[c[u]], 1);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (c[u] >= 0) d.sorted[at[u]] = p[u];
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * stride;
+      c[u] = i < d.N ? d.bead_cell[i] : -1;
     }
-    return;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * stride;
+      if (c[u] >= 0) {
+        p[u] = pos[i];
+        p[u].w = (int)((i << 4) | d.type[i]);
+      }
+    }
+    // after the scatter cell_start[c] holds the end of cell c, i.e. the start
+    // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) at[u] = atomicAdd(&d.cell_start[c[u]], 1);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) d.sorted[at[u]] = p[u];
   }
+}
+
+// Breakage nomination of the beads of the breakage bitmap by blocks b = 0 ..
+// nb - 1 of the caller's, with their edit / nomination bits OR-ed into the
+// activity bitmaps.  It needs neither the positions' binning nor the cell
+// list, so it runs beside them.
+__device__ __forceinline__ void breakage_part(const Dev& d, const RuleTab* __restrict__ rtp, int b, int nb) {
+  const int4* __restrict__ pos = d.args->pos;
   const RuleTab& rt = *rtp;
   const CountTargets<2> tg{{d.stats + ST_BREAK_CANDIDATES, d.stats + ST_BREAK_MATCHED}, {NSTAT, NSTAT}};
   ReplicaCounts<2> cnt;
   int hit_r = -1;  // replica of the settled breakage pairs this thread counted
-  const int b = blockIdx.x;
   const long long nchunks = (d.W + CHUNK_WORDS - 1) / CHUNK_WORDS;
   const long long cpb = (nchunks + nb - 1) / nb;
   const long long c0 = (long long)b * cpb, c1 = min(nchunks, c0 + cpb);
@@ -360,10 +359,24 @@ __device__ __forceinline__ void scatter_body(const Dev& d, const RuleTab* __rest
   block_flag(d.round_hit + d.R, hit_r);
 }
 
-__global__ void __launch_bounds__(256) k_scatter(Dev d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
+// The persistent call's form: the first gridDim.x - scatter_blocks blocks
+// nominate (their longer dependent chains start with the first wave instead
+// of trailing the scatter), the last scatter_blocks scatter.
+__device__ __forceinline__ void scatter_body(const Dev& d, const RuleTab* __restrict__ rtp, int scatter_blocks) {
+  const int nb = gridDim.x - scatter_blocks;
+  if ((int)blockIdx.x >= nb) scatter_part(d, blockIdx.x - nb, scatter_blocks);
+  else breakage_part(d, rtp, blockIdx.x, nb);
+}
+
+__global__ void __launch_bounds__(256) k_scatter(Dev d) {
   pdl_enter();
   if (aborted(d.err)) return;
-  scatter_body(d, rtp, scatter_blocks);
+  scatter_part(d, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) k_breakage(Dev d, const RuleTab* __restrict__ rtp) {
+  if (aborted(d.err)) return;
+  breakage_part(d, rtp, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
