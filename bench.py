@@ -599,7 +599,7 @@ def main():
     step_gbs = alg / (res["ms"] * 1e-3) / 1e9
     rank, world, _ = dist_env()
     cpu = cpu_baseline(args.cpu_baseline_seconds) if world == 1 else None
-    kernels_per_step = 12 + 4  # step graph 11 + argument kernel; forces graph 3 + argument kernel
+    kernels_per_step = 13 + 4  # step graph 12 + argument kernel; forces graph 3 + argument kernel
     line = dict(
         metric=METRIC, value=res["value"], unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=res["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64+f32",

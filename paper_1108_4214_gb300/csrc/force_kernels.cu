@@ -85,6 +85,28 @@ __device__ __forceinline__ void flush_ev(const Dev& d, EV& acc, int r) {
   if (lane < 7 && mine != 0.0) atomicAdd(&d.ev_acc[((long long)r * EV_COPIES + copy) * 7 + lane], mine);
 }
 
+// The work items of block b of G under the chunked-strided order: chunk j
+// holds items (j G + b) 2^cs .. (j G + b) 2^cs + 2^cs - 1.  cs = 0 is the
+// plain strided order (at any time the grid works on neighbouring items);
+// with several replicas, cs > 0 keeps a block's consecutive items in one
+// replica, so its energy / virial partials are flushed about once per chunk
+// instead of at every item.
+struct ItemOrder {
+  int b, G, cs;
+  __device__ int item(int k) const { return (((k >> cs) * G + b) << cs) + (k & ((1 << cs) - 1)); }
+  __device__ int count(int nitems) const {
+    const int first = b << cs;
+    if (nitems <= first) return 0;
+    const int S = G << cs;
+    const int J = (nitems - first + S - 1) / S;  // chunks that start below nitems
+    const int last = (((J - 1) * G + b) << cs);
+    return ((J - 1) << cs) + min(1 << cs, nitems - last);
+  }
+};
+__device__ __forceinline__ ItemOrder item_order(const Dev& d) {
+  return ItemOrder{(int)blockIdx.x, (int)gridDim.x, d.R > 1 ? 3 : 0};
+}
+
 // Bonds: each bead sums, over its occupied slots, the harmonic force of the
 // type it stores for that bond (directional bonds, Sec. 2) and books half the
 // energy; no atomics.  Software-pipelined per thread like the angle /
@@ -109,10 +131,11 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ffp) {
   const int R = d.R, nitems = d.tb_beads[R];
   const unsigned N = (unsigned)d.N;
   const int tid = threadIdx.x;
-  // work items blockIdx.x, + gridDim.x, ...: at any time the grid works on
+  // work items in the chunked-strided order: at any time the grid works on
   // neighbouring tiles (shared partner positions stay in L2); each tile's
   // replica is looked up once, when its slots are issued
-  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const ItemOrder order = item_order(d);
+  const int ntiles = order.count(nitems);
   struct Tile {
     long long beg = 0, end = 0;
     int r = 0, L = 0;
@@ -122,7 +145,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ffp) {
   __shared__ int4 s_tiles[FORCE_TILE_TABLE];
   const int nlook = min(ntiles, FORCE_TILE_TABLE);
   for (int k = tid >> 5; k < nlook; k += BF_THREADS >> 5) {
-    const int it = (int)blockIdx.x + k * (int)gridDim.x;
+    const int it = order.item(k);
     const int r = find_seg_warp(d.tb_beads, R, it);
     if ((tid & 31) == 0) {
       const long long beg = d.off[r] + (long long)(it - d.tb_beads[r]) * BEAD_TILE;
@@ -141,7 +164,7 @@ __global__ void __launch_bounds__(BF_THREADS) k_bond_forces(Dev d, FF ffp) {
       t.L = e.w;
       return t;
     }
-    const int it = (int)blockIdx.x + k * (int)gridDim.x;
+    const int it = order.item(k);
     t.r = find_seg_warp(d.tb_beads, R, it);
     t.beg = d.off[t.r] + (long long)(it - d.tb_beads[t.r]) * BEAD_TILE;
     t.end = min(t.beg + BEAD_TILE, d.off[t.r + 1]);
@@ -324,20 +347,21 @@ __global__ void __launch_bounds__(AD_THREADS) k_angle_dihedral_forces(Dev d, FF 
   const int na_items = d.tb_fang[d.R], nitems = na_items + d.tb_fdih[d.R];
   const unsigned N = (unsigned)d.N;
   const int tid = threadIdx.x;
-  // work items blockIdx.x, + gridDim.x, ... (neighbouring records in flight
+  // work items in the chunked-strided order (neighbouring records in flight
   // together); each tile is looked up once, when its records are issued
-  const int ntiles = nitems > (int)blockIdx.x ? (nitems - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const ItemOrder order = item_order(d);
+  const int ntiles = order.count(nitems);
   // the block's tiles looked up first, a warp per tile (independent lookups)
   __shared__ AdTile s_tiles[FORCE_TILE_TABLE];
   const int nlook = min(ntiles, FORCE_TILE_TABLE);
   for (int k = tid >> 5; k < nlook; k += AD_THREADS >> 5) {
-    const AdTile t = ad_tile(d, (int)blockIdx.x + k * (int)gridDim.x, na_items, nitems);
+    const AdTile t = ad_tile(d, order.item(k), na_items, nitems);
     if ((tid & 31) == 0) s_tiles[k] = t;
   }
   __syncthreads();
   auto tile = [&](int k) {
     if (k < nlook) return s_tiles[k];
-    return ad_tile(d, k < ntiles ? (int)blockIdx.x + k * (int)gridDim.x : nitems, na_items, nitems);
+    return ad_tile(d, k < ntiles ? order.item(k) : nitems, na_items, nitems);
   };
   auto issue_rec = [&](const AdTile& t, int k) {
 #pragma unroll
