@@ -1379,14 +1379,30 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
   uint4 s = d.slots[i];
   unsigned removed = 0, changed = 0;
   int conv_partner = -1, form_partner = -1, form_type = 0;
+  // the per-bead words of both systems are read together, before any of them
+  // is needed (one round trip instead of a chain)
+  long long mb = -1, mc = -1;
+  int pb = 0, pc = 0, cs = 0;
+  unsigned km = 0, bl = 0;
   if (ba) {
-    removed = d.killmask[i];
+    km = d.killmask[i];
+    bl = d.brk_len[i];
+    mb = d.mate[N + i];
+    pb = d.ptr[N + i];
+  }
+  if (ca) {
+    mc = d.mate[i];
+    pc = d.ptr[i];
+    cs = d.cand_start[i];
+  }
+  if (ba) {
+    removed = km;
 #pragma unroll
     for (int q = 0; q < SLOTS; ++q)
       if ((removed >> q) & 1u) o.n_killed += s_partner(s_get(s, q)) > i;
-    int j = d.brk_len[i] ? mate_partner(d.mate[N + i]) : -1;
+    int j = bl ? mate_partner(mb) : -1;
     if (j >= 0) {
-      int4 ent = d.brk[4 * i + d.ptr[N + i]];
+      int4 ent = d.brk[4 * i + pb];
       int k = ent.y;
       int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
       if (trial(d, rt, a, b, r, TAG_BREAK, d.T_break[(long long)r * MAXR + k])) {
@@ -1408,9 +1424,9 @@ __device__ __forceinline__ void edit_bead(const Dev& d, const RuleTab& rt, long 
     }
   }
   if (ca) {
-    int j = mate_partner(d.mate[i]);
+    int j = mate_partner(mc);
     if (j >= 0) {
-      int4 ent = d.cand[d.cand_start[i] + d.ptr[i]];
+      int4 ent = d.cand[cs + pc];
       int k = ent.y & 0xFF;
       int a = (int)min((long long)j, i), b = (int)max((long long)j, i);
       if (trial(d, rt, a, b, r, TAG_FORM, d.T_form[(long long)r * MAXR + k])) {
@@ -1946,7 +1962,12 @@ __device__ __forceinline__ void setup_body(const Dev& d, bool keep_bar) {
                          (long long)sizeof(int);
   for (long long k = g; k < (long long)(sizeof(Counters) / sizeof(int)); k += stride)
     if (!keep_bar || k != bar1) cnt[k] = 0;
-  for (long long k = g; k <= d.n_keys; k += stride) d.cell_start[k] = 0;
+  {  // cell counts [0, n_keys]: 16-byte stores (the array is 256-byte aligned), then the last few words
+    const long long n4 = (d.n_keys + 1) / 4;
+    int4* c4 = reinterpret_cast<int4*>(d.cell_start);
+    for (long long k = g; k < n4; k += stride) c4[k] = make_int4(0, 0, 0, 0);
+    for (long long k = 4 * n4 + g; k <= d.n_keys; k += stride) d.cell_start[k] = 0;
+  }
   for (long long k = g; k < d.W; k += stride) {
     d.bm_ca[k] = 0;
     d.bm_ba[k] = 0;
