@@ -291,9 +291,25 @@ dynbond_status dynbond_step(dynbond_ctx* ctx, const int32_t* d_pos, uint64_t ste
 dynbond_status dynbond_forces(dynbond_ctx* ctx, const int32_t* d_pos, float* d_force, double* d_ev);
 
 /*
+ * dynbond_step followed by dynbond_forces at the same positions, in one call:
+ * the results (topology, statistics, d_force, d_ev) are those of the two calls
+ * in turn (forces within the same FP32 tolerance: only the order of the
+ * floating-point partial sums may differ).  The bond forces of the new
+ * topology depend only on the bonds (Appendix step 7) and the positions, so
+ * they run beside the removal and re-creation of angles and dihedrals
+ * (Appendix steps 6 and 9) instead of after them.  Arguments, alignment and
+ * errors as for dynbond_step and dynbond_forces; h_stats nullable (when given
+ * the call waits and fills it).  Contexts created with DYNBOND_FLAG_PROFILE or
+ * DYNBOND_FLAG_PERSISTENT run the two calls in turn.
+ */
+dynbond_status dynbond_step_forces(dynbond_ctx* ctx, const int32_t* d_pos, uint64_t step, float* d_force,
+                                   double* d_ev, dynbond_stats* h_stats);
+
+/*
  * dynbond_step + dynbond_forces from host buffers: copies h_pos (int4[N]) to
- * the device, runs both, and copies the forces (float4[N]) and energies /
- * virials (double[R*7]) back.  Waits for completion.  h_stats nullable.
+ * the device, runs both (as dynbond_step_forces), and copies the forces
+ * (float4[N]) and energies / virials (double[R*7]) back.  Waits for
+ * completion.  h_stats nullable.
  */
 dynbond_status dynbond_run_host(dynbond_ctx* ctx, const int32_t* h_pos, uint64_t step, float* h_force,
                                 double* h_ev, dynbond_stats* h_stats);

@@ -21,6 +21,7 @@ struct dynbond_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;                        // the breakage nomination's branch of a call
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // its fork from and join into `stream`
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;  // the bond forces' branch of a combined call
   dynbond_params prm{};
   RuleTab rt{};
   RuleTab* d_rt = nullptr;  // device copy read by the kernels
@@ -32,6 +33,7 @@ struct dynbond_ctx {
   Dev d{};
   std::vector<void*> allocs;
   cudaGraphExec_t g_step = nullptr, g_forces = nullptr;
+  cudaGraphExec_t g_both = nullptr;  // step + forces in one graph (dynbond_step_forces)
   bool use_graph = true;
   bool pdl = true;  // programmatic dependent launch between the kernels of a call
   int block = 256;
@@ -304,6 +306,16 @@ template <typename... KArgs, typename... Args>
 cudaError_t launch(dynbond_ctx* c, void (*kern)(KArgs...), int grid, int block, Args... args) {
   return launch_smem(c, kern, grid, block, 0, args...);
 }
+// a launch after an event wait (a graph branch or its join): plain stream order
+template <typename... KArgs, typename... Args>
+cudaError_t launch_plain(cudaStream_t st, void (*kern)(KArgs...), int grid, int block, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 cudaError_t launch_match(dynbond_ctx* c) {
   cudaLaunchConfig_t cfg{};
@@ -342,7 +354,11 @@ cudaError_t launch_persistent(dynbond_ctx* c) {
                             (const RuleTab*)c->d_rt);
 }
 
-cudaError_t enqueue_step(dynbond_ctx* c) {
+// The step's launch sequence; with bond_branch, the bond forces of the new
+// topology run on a branch forked after the edit (they read only the slots
+// and the positions, which nothing after the edit writes) beside the purge,
+// hole filling and rebuild, joined at the end.
+cudaError_t enqueue_step_seq(dynbond_ctx* c, bool bond_branch) {
   const Dev& d = c->d;
   size_t k = 0;
   if (c->persistent) {
@@ -371,12 +387,39 @@ cudaError_t enqueue_step(dynbond_ctx* c) {
   E(launch_match(c));
   mark(c, c->ev_step, k++);
   E(launch(c, k_edit, c->grid_edit, 256, d, c->d_rt));
+  if (bond_branch) {
+    E(cudaEventRecord(c->ev_fork2, c->stream));
+    E(cudaStreamWaitEvent(c->side, c->ev_fork2, 0));
+    E(launch_plain(c->side, k_bond_forces, c->grid_bf, BF_THREADS, (size_t)BF_SMEM_BYTES, d, c->ff));
+    E(cudaEventRecord(c->ev_join2, c->side));
+  }
   mark(c, c->ev_step, k++);
   E(launch(c, k_purge, c->grid_purge, PURGE_TILE / PURGE_PER_THREAD, d));
   E(launch(c, k_fill, c->nsm * 4, FILL_TILE, d));
   mark(c, c->ev_step, k++);
   E(launch(c, k_rebuild, c->grid_seg, 256, d, c->d_rt, 0));
   mark(c, c->ev_step, k++);
+  if (bond_branch) E(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
+  return cudaGetLastError();
+}
+cudaError_t enqueue_step(dynbond_ctx* c) { return enqueue_step_seq(c, false); }
+
+// The angle / dihedral forces (after the bonds') and the energy / virial output.
+cudaError_t enqueue_ad_forces(dynbond_ctx* c, bool after_join) {
+  const Dev& d = c->d;
+  if (after_join)
+    E(launch_plain(c->stream, k_angle_dihedral_forces, c->grid_adf, AD_THREADS, (size_t)AD_SMEM_BYTES, d, c->ff));
+  else
+    E(launch_smem(c, k_angle_dihedral_forces, c->grid_adf, AD_THREADS, (size_t)AD_SMEM_BYTES, d, c->ff));
+  return cudaSuccess;
+}
+
+// dynbond_step_forces: the step with the bond forces on a branch, then the
+// angle / dihedral forces and the energy / virial output
+cudaError_t enqueue_both(dynbond_ctx* c) {
+  E(enqueue_step_seq(c, true));
+  E(enqueue_ad_forces(c, true));
+  E(launch(c, k_ev_out, bounded_grid(7ll * c->R, 256, c->nsm), 256, c->d));
   return cudaGetLastError();
 }
 
@@ -550,10 +593,15 @@ dynbond_status set_geometry(dynbond_ctx* c, double scale, int zdiv) {
   return DYNBOND_OK;
 }
 
+// The combined call runs its own graph unless the context profiles phases or
+// runs each step as one persistent launch (then it is the two calls in turn).
+bool combined_graph(const dynbond_ctx* c) { return !c->profile && !c->persistent; }
+
 dynbond_status capture_graphs(dynbond_ctx* c) {
   if (c->g_step) cudaGraphExecDestroy(c->g_step);
   if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
-  c->g_step = c->g_forces = nullptr;
+  if (c->g_both) cudaGraphExecDestroy(c->g_both);
+  c->g_step = c->g_forces = c->g_both = nullptr;
   if (!c->use_graph) return DYNBOND_OK;
   if (capture(c, enqueue_step, &c->g_step) != cudaSuccess || capture(c, enqueue_forces, &c->g_forces) != cudaSuccess) {
     if (c->g_step) cudaGraphExecDestroy(c->g_step);
@@ -562,6 +610,11 @@ dynbond_status capture_graphs(dynbond_ctx* c) {
     c->use_graph = false;
     cudaGetLastError();
     c->last_error = "CUDA graph capture unavailable; launching kernels directly";
+    return DYNBOND_OK;
+  }
+  if (combined_graph(c) && capture(c, enqueue_both, &c->g_both) != cudaSuccess) {
+    c->g_both = nullptr;  // the combined call falls back to the two graphs
+    cudaGetLastError();
   }
   return DYNBOND_OK;
 }
@@ -615,12 +668,15 @@ void dynbond_destroy(dynbond_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->g_step) cudaGraphExecDestroy(c->g_step);
   if (c->g_forces) cudaGraphExecDestroy(c->g_forces);
+  if (c->g_both) cudaGraphExecDestroy(c->g_both);
   if (c->side) {
     cudaStreamSynchronize(c->side);
     cudaStreamDestroy(c->side);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
   for (cudaEvent_t e : c->ev_step) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_forces) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
@@ -935,6 +991,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming));
+  CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming));
   if (c->profile) {
     c->names_step = {"setup", "bead", "cells", "candidates", "match", "edit", "purge", "rebuild"};
     c->names_forces = {"bond_forces", "angle_dihedral_forces"};
@@ -1007,14 +1065,43 @@ dynbond_status dynbond_forces(dynbond_ctx* c, const int32_t* d_pos, float* d_for
   return DYNBOND_OK;
 }
 
+dynbond_status dynbond_step_forces(dynbond_ctx* c, const int32_t* d_pos, uint64_t step, float* d_force,
+                                   double* d_ev, dynbond_stats* h_stats) {
+  if (!c || !d_pos || !d_force || !d_ev) return DYNBOND_EINVAL;
+  if (!aligned16(d_pos) || !aligned16(d_force))
+    return fail(c, DYNBOND_EINVAL, "d_pos and d_force must be 16-byte aligned (4-vectors per bead)");
+  if (c->sticky) return c->sticky;
+  if (!c->tuned) {
+    dynbond_status st = dynbond_autotune(c, d_pos, nullptr);
+    if (st) return st;
+  }
+  if (!combined_graph(c) || (c->use_graph && !c->g_both)) {
+    dynbond_status st = dynbond_step(c, d_pos, step, nullptr);
+    if (!st) st = dynbond_forces(c, d_pos, d_force, d_ev);
+    if (st) return st;
+  } else {
+    k_set_args<<<1, 1, 0, c->stream>>>(c->d.args, (const int4*)d_pos, (float4*)d_force, d_ev, step, 1, 1, nullptr);
+    cudaError_t e = c->use_graph ? cudaGraphLaunch(c->g_both, c->stream) : enqueue_both(c);
+    if (e != cudaSuccess) {
+      c->sticky = DYNBOND_ECUDA;
+      return fail(c, DYNBOND_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+    }
+  }
+  if (h_stats) {
+    dynbond_status st = device_status(c);
+    if (st) return st;
+    CUDA_TRY(c, cudaMemcpy(h_stats, c->d.stats, sizeof(dynbond_stats) * c->R, cudaMemcpyDeviceToHost));
+  }
+  return DYNBOND_OK;
+}
+
 dynbond_status dynbond_run_host(dynbond_ctx* c, const int32_t* h_pos, uint64_t step, float* h_force, double* h_ev,
                                 dynbond_stats* h_stats) {
   if (!c || !h_pos || !h_force || !h_ev) return DYNBOND_EINVAL;
   if (c->sticky) return c->sticky;
   CUDA_TRY(c, cudaMemcpyAsync(c->h2d_pos, h_pos, 16 * c->N, cudaMemcpyHostToDevice, c->stream));
-  dynbond_status st = dynbond_step(c, (const int32_t*)c->h2d_pos, step, nullptr);
-  if (st) return st;
-  st = dynbond_forces(c, (const int32_t*)c->h2d_pos, (float*)c->d2h_force, c->d2h_ev);
+  dynbond_status st =
+      dynbond_step_forces(c, (const int32_t*)c->h2d_pos, step, (float*)c->d2h_force, c->d2h_ev, nullptr);
   if (st) return st;
   CUDA_TRY(c, cudaMemcpyAsync(h_force, c->d2h_force, 16 * c->N, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(h_ev, c->d2h_ev, 8 * 7 * c->R, cudaMemcpyDeviceToHost, c->stream));

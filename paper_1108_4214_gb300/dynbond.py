@@ -30,7 +30,8 @@ STAT_NAMES = [
 EXPORTS = ["dynbond_create", "dynbond_step", "dynbond_forces", "dynbond_run_host", "dynbond_get_topology",
            "dynbond_sync", "dynbond_phase_times", "dynbond_last_error", "dynbond_status_string", "dynbond_destroy",
            "dynbond_forces_noalloc", "dynbond_autotune", "dynbond_md_create", "dynbond_md_advance",
-           "dynbond_md_destroy", "dynbond_topology_hash", "dynbond_get_tuning", "dynbond_md_pair_forces"]
+           "dynbond_md_destroy", "dynbond_topology_hash", "dynbond_get_tuning", "dynbond_md_pair_forces",
+           "dynbond_step_forces"]
 NOALLOC_MAX_REPLICAS = 4096
 
 c_i32, c_u32, c_i64, c_u64, c_dbl, c_p = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
@@ -108,6 +109,8 @@ def load() -> ctypes.CDLL:
     L.dynbond_forces.argtypes = [c_p, c_p, c_p, c_p]
     L.dynbond_run_host.restype = c_i32
     L.dynbond_run_host.argtypes = [c_p, c_p, c_u64, c_p, c_p, c_p]
+    L.dynbond_step_forces.restype = c_i32
+    L.dynbond_step_forces.argtypes = [c_p, c_p, c_u64, c_p, c_p, c_p]
     L.dynbond_get_topology.restype = c_i32
     L.dynbond_get_topology.argtypes = [c_p, ctypes.POINTER(Topology)]
     L.dynbond_sync.restype = c_i32
@@ -277,6 +280,20 @@ class Context:
             ev = torch.empty((self.R, 7), dtype=torch.float64, device=pos.device)
         self._check(self.L.dynbond_forces(self.h, c_p(_ptr(pos)), c_p(_ptr(force)), c_p(_ptr(ev))))
         return force, ev
+
+    def step_forces(self, pos, step: int, force=None, ev=None, stats: bool = False):
+        """dynbond_step_forces: the step, then the forces at the same positions, in one call; returns
+        (force, ev, stats or None)."""
+        torch = self._torch
+        assert pos.is_cuda and pos.dtype == torch.int32 and pos.is_contiguous()
+        if force is None:
+            force = torch.empty((self.N, 4), dtype=torch.float32, device=pos.device)
+        if ev is None:
+            ev = torch.empty((self.R, 7), dtype=torch.float64, device=pos.device)
+        self._check(self.L.dynbond_step_forces(self.h, c_p(_ptr(pos)), int(step), c_p(_ptr(force)), c_p(_ptr(ev)),
+                                               ctypes.byref(self._stats) if stats else None))
+        st = (np.array([[getattr(s, n) for n in STAT_NAMES] for s in self._stats], np.int64) if stats else None)
+        return force, ev, st
 
     def run_host(self, pos_host, step: int, force_host=None, ev_host=None, stats: bool = False):
         """dynbond_run_host from host buffers (numpy arrays or CPU tensors, ideally pinned)."""

@@ -65,9 +65,13 @@ def ev_error(ev, evr, scale=None):
     return float((err / scale).max())
 
 
-def compare_forces(ctx, o, snap, where, ev_scale=None):
-    pos = torch().from_numpy(snap).cuda()
-    f, ev = ctx.forces(pos)
+def compare_forces(ctx, o, snap, where, ev_scale=None, given=None):
+    """Forces and energy / virial at snap against the oracle's: computed by
+    ctx.forces, or `given` as (force, ev) CUDA tensors from a combined call."""
+    if given is None:
+        f, ev = ctx.forces(torch().from_numpy(snap).cuda())
+    else:
+        f, ev = given
     f = f.cpu().numpy()
     ev = ev.cpu().numpy()
     fr, evr = o.forces(snap)
@@ -90,21 +94,29 @@ def compare_stats(st_g, st_o, where):
         raise AssertionError(f"{where}: statistics differ {diff}")
 
 
-def run_parity(system, n_calls, snaps=None, params=None, flags=0, forces=True, start=0):
+def run_parity(system, n_calls, snaps=None, params=None, flags=0, forces=True, start=0, combined=False):
     """n_calls calls on the GPU and on the oracle: statistics, topology and
-    (optionally) forces compared after every call.  Returns the oracle and
-    the per-call (force error, energy/virial error)."""
+    (optionally) forces compared after every call.  combined: each call is
+    dynbond_step_forces (step and forces in one call) instead of the two
+    calls.  Returns the oracle and the per-call (force error, energy/virial
+    error)."""
     o = O.Oracle(system, params=params)
     ctx = dynbond().Context(system, params=params, flags=flags)
     compare_topology(ctx, o, "initial")
     worst = []
     for k in range(n_calls):
         snap = snaps[k] if snaps is not None else system.snapshot(k)
-        st_g = ctx.step(torch().from_numpy(snap).cuda(), start + k, stats=True)
+        pos = torch().from_numpy(snap).cuda()
+        given = None
+        if combined:
+            f, ev, st_g = ctx.step_forces(pos, start + k, stats=True)
+            given = (f, ev)
+        else:
+            st_g = ctx.step(pos, start + k, stats=True)
         st_o = o.step(snap, start + k)
         compare_stats(st_g, st_o, f"call {k}")
         compare_topology(ctx, o, f"call {k}")
-        if forces:
-            worst.append(compare_forces(ctx, o, snap, f"call {k}"))
+        if forces or combined:
+            worst.append(compare_forces(ctx, o, snap, f"call {k}", given=given))
     ctx.close()
     return o, worst

@@ -254,6 +254,56 @@ def test_dependent_launch_overlap_changes_nothing_at_scale():
         assert np.array_equal(x, y)
 
 
+# dynbond_step_forces: the step with the bond forces on a graph branch beside
+# the angle / dihedral maintenance, then the angle / dihedral forces
+@pytest.mark.parametrize("cell_scale,cell_zdiv", [(0, 0), (2, 1), (1, 4)])
+def test_combined_call_plain_2048(cell_scale, cell_zdiv):
+    run_parity(W.config1(), 10, params=dict(cell_scale=cell_scale, cell_zdiv=cell_zdiv), combined=True)
+
+
+@pytest.mark.parametrize("seed", [2, 7, 11, 19, 26, 33])
+def test_combined_call_random_systems(seed):
+    rules = W.random_rules(seed)
+    s = W.random_small_system(seed, n_beads=60, box=3.0 + seed % 3, n_bonds=50, rules=rules,
+                              n_replicas=1 + seed % 3,
+                              params=dict(paircheck13=seed % 2, paircheck14=(seed // 2) % 2, max_rounds=seed % 3,
+                                          prob_mode=(seed // 3) % 2))
+    run_parity(s, 4, combined=True)
+
+
+def test_combined_call_batches_and_1m():
+    ladder = W.config3(n_replicas=48)
+    run_parity(ladder, 3, snaps=ladder.snapshots(0, 3), combined=True)
+    s = W.config2()
+    _, worst = run_parity(s, 3, snaps=s.snapshots(0, 3), combined=True)
+    print("1M combined: max force / ev error", worst)
+
+
+def test_combined_call_equals_the_two_calls():
+    """The combined call against dynbond_step then dynbond_forces on a second
+    context: identical statistics and topology, forces and energy / virial to
+    the rounding of the partial sums' order; the direct-launch form too."""
+    s = W.config2()
+    D = dynbond()
+    a = D.Context(s, params=dict(cell_scale=2, cell_zdiv=2))
+    b = D.Context(s, params=dict(cell_scale=2, cell_zdiv=2))
+    c = D.Context(s, params=dict(cell_scale=2, cell_zdiv=2), flags=D.FLAG_NO_GRAPH)
+    for k in range(3):
+        p = torch.from_numpy(s.snapshot(k)).cuda()
+        fa, eva, sta = a.step_forces(p, k, stats=True)
+        stb = b.step(p, k, stats=True)
+        fb, evb = b.forces(p)
+        fc, evc, stc = c.step_forces(p, k, stats=True)
+        assert np.array_equal(sta, stb) and np.array_equal(sta, stc)
+        for f in (fb, fc):
+            torch.testing.assert_close(fa, f, rtol=1e-5, atol=1e-4)
+        for ev in (evb, evc):
+            ea, eb = eva.cpu().numpy(), ev.cpu().numpy()
+            assert np.abs(ea - eb).max() <= 1e-9 * np.abs(ea).max()
+    for x, y, z in zip(a.topology(), b.topology(), c.topology()):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
 def test_host_buffer_entry_point_matches_device_path():
     s = W.config1()
     D = dynbond()
