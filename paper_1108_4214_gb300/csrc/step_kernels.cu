@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates(Dev d, const RuleTab* __r
   if (aborted(d.err)) return;
   candidates_body<0>(d, rtp);
 }
-__global__ void __launch_bounds__(256, 3) k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp) {
+__global__ void __launch_bounds__(256, 4) k_candidates_oct(Dev d, const RuleTab* __restrict__ rtp) {
   pdl_enter();
   if (aborted(d.err)) return;
   candidates_body<1>(d, rtp);
