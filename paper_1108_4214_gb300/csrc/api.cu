@@ -814,7 +814,8 @@ dynbond_status create_impl(dynbond_ctx* c, const dynbond_params* params, const d
   ALLOC(d.cell_start, c->n_cells * c->rt.n_cls + 5);
   CUDA_TRY(c, cudaMemsetAsync(d.cell_start, 0, 4 * (size_t)(c->n_cells * c->rt.n_cls + 5), c->stream));
   d.cell_start += 4;
-  ALLOC(d.bead_cell, N);
+  ALLOC(d.binned, N);
+  ALLOC(d.binned_n, (N + BIN_SEG - 1) / BIN_SEG);
   ALLOC(d.sorted, N);
   d.cand_fixed = N * CAND_FAST;
   d.cand_pool = 2 * N + 65536;

@@ -136,7 +136,8 @@ struct Dev {
   unsigned* err;               // sticky error word
   int* cell_start;             // [-1, n_keys], key = class * n_cells + cell: counts, then starts
                                // (exclusive scan), then ends after the scatter; cell_start[-1] = 0
-  int* bead_cell;              // [N]
+  int2* binned;                // [N] per segment of BIN_SEG beads, its binned beads (bead, cell key) first
+  int* binned_n;               // [N / BIN_SEG] binned beads per segment
   int4* sorted;                // [N] (x, y, z, gid << 4 | type)
   int4* cand;                  // (partner, rule | mytype << 8, d2 lo, d2 hi): CAND_FAST slots per
                                // sorted entry, then a pool of cand_pool entries for longer lists

@@ -12,6 +12,7 @@ constexpr int PURGE_TILE = 1024;   // 256 threads x 4 records (small tiles balan
 constexpr int PURGE_PER_THREAD = 4;
 constexpr int PURGE_COARSE_WORDS = 4096;  // coarse dirty bitmap of the purge, held in shared memory (16 KB)
 constexpr int FILL_TILE = 256;     // hole / tail items per k_fill work item, one per thread
+constexpr int BIN_SEG = 128;      // beads per binning segment (a warp, four loads per lane)
 constexpr int SCAN_PER_THREAD = 32;  // cell keys per thread in the histogram scan (a multiple of 4)
 constexpr int FORCE_TILE = 512;    // records per force work item (2 per thread)
 constexpr int AD_THREADS = 256;    // threads of the angle / dihedral force blocks

@@ -154,15 +154,21 @@ __device__ __forceinline__ void bead_body(const Dev& d, const RuleTab* __restric
   const RuleTab& rt = *rtp;
   const int4* __restrict__ pos = d.args->pos;
   const long long N = d.N;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  constexpr int U = 4;  // beads per thread and pass, their loads issued together
-  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += U * stride) {
+  const int lane = threadIdx.x & 31;
+  // a warp takes segments of BIN_SEG consecutive beads (32 per load, the
+  // segment's loads issued together) and writes its binned beads, (bead, cell
+  // key), to the front of the segment's own part of `binned` with their count
+  // in binned_n: no shared counter
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long sg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sg * BIN_SEG < N; sg += nwarps) {
+    const long long i0 = sg * BIN_SEG + lane;
+    constexpr int U = BIN_SEG / 32;
     int4 p[U];
     unsigned ew[U];
-    int rr[U], bt[U];
+    int rr[U], bt[U], cell[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const long long i = i0 + u * stride;
+      const long long i = i0 + 32 * u;
       if (i < N) {
         p[u] = pos[i];
         ew[u] = d.bm_elig[i >> 5];
@@ -170,14 +176,15 @@ __device__ __forceinline__ void bead_body(const Dev& d, const RuleTab* __restric
         bt[u] = d.type[i];
       }
     }
+    int nb = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const long long i = i0 + u * stride;
-      if (i >= N) break;
+      const long long i = i0 + 32 * u;
+      cell[u] = -1;
+      if (i >= N) continue;
       const int r = rr[u];
       const int4 g0 = d.geo[2 * r];
       const int L = g0.x;
-      int cell = -1;
       if (p[u].x < 0 || p[u].y < 0 || p[u].z < 0 || p[u].x >= L || p[u].y >= L || p[u].z >= L) {
         atomicOr(d.err, ERR_POS);
       } else if ((ew[u] >> (i & 31)) & 1u) {
@@ -188,10 +195,16 @@ __device__ __forceinline__ void bead_body(const Dev& d, const RuleTab* __restric
         long long cz = cell_of(p[u].z, nz, L, __int_as_float(g1.y));
         long long c = rt.cls_of[bt[u]] * d.n_cells + g1.z + (cx * nc + cy) * nz + cz;
         atomicAdd(&d.cell_start[c], 1);  // count only; the scatter assigns the slots
-        cell = (int)c;
+        cell[u] = (int)c;
+        ++nb;
       }
-      d.bead_cell[i] = cell;
     }
+    const int incl = warp_incl_scan(nb);
+    int at = (int)(sg * BIN_SEG) + incl - nb;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cell[u] >= 0) d.binned[at++] = make_int2((int)(i0 + 32 * u), cell[u]);
+    if (lane == 31) d.binned_n[sg] = incl;
   }
 }
 
@@ -303,35 +316,36 @@ __global__ void __launch_bounds__(256) k_scan_cells(Dev d) {
 }
 
 // Counting-sort scatter of the binned beads into cell order, by blocks
-// b = 0 .. nb - 1 of the caller's.
+// b = 0 .. nb - 1 of the caller's: a warp per segment of k_bead, only the
+// segment's binned beads.
 __device__ __forceinline__ void scatter_part(const Dev& d, int b, int nb) {
   const int4* __restrict__ pos = d.args->pos;
-  const long long stride = (long long)nb * blockDim.x;
-  constexpr int U = 4;  // beads per thread and pass, every load issued first
-  for (long long i0 = (long long)b * blockDim.x + threadIdx.x; i0 < d.N; i0 += U * stride) {
-    int c[U], at[U];
+  const int lane = threadIdx.x & 31;
+  const long long nseg = (d.N + BIN_SEG - 1) / BIN_SEG;
+  const long long nwarps = (long long)nb * (blockDim.x >> 5);
+  constexpr int U = BIN_SEG / 32;
+  for (long long sg = (long long)b * (blockDim.x >> 5) + (threadIdx.x >> 5); sg < nseg; sg += nwarps) {
+    const int cnt = d.binned_n[sg];
+    int2 e[U];
+    int at[U];
     int4 p[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const long long i = i0 + u * stride;
-      c[u] = i < d.N ? d.bead_cell[i] : -1;
-    }
+    for (int u = 0; u < U; ++u) e[u] = 32 * u + lane < cnt ? d.binned[sg * BIN_SEG + 32 * u + lane] : make_int2(-1, -1);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const long long i = i0 + u * stride;
-      if (c[u] >= 0) {
-        p[u] = pos[i];
-        p[u].w = (int)((i << 4) | d.type[i]);
+      if (e[u].x >= 0) {
+        p[u] = pos[e[u].x];
+        p[u].w = (int)(((long long)e[u].x << 4) | d.type[e[u].x]);
       }
     }
     // after the scatter cell_start[c] holds the end of cell c, i.e. the start
     // of cell c + 1 (the search reads cell c as [cell_start[c-1], cell_start[c]))
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (c[u] >= 0) at[u] = atomicAdd(&d.cell_start[c[u]], 1);
+      if (e[u].x >= 0) at[u] = atomicAdd(&d.cell_start[e[u].y], 1);
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (c[u] >= 0) d.sorted[at[u]] = p[u];
+      if (e[u].x >= 0) d.sorted[at[u]] = p[u];
   }
 }
 
