@@ -9,8 +9,9 @@ own independent system; there is no data-path collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the CPU oracle (the reference of this build) on the
-same workload, metric and unit, on the host cores.
+--impl reference times the CPU oracle (the paper ships no program, so the
+oracle is the reference arm) on the same workload, metric and unit, on the
+host cores.
 """
 
 from __future__ import annotations
