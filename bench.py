@@ -577,7 +577,9 @@ def reference_arm(args):
     v = s.n_beads * K / dt
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=K, warmup=Wm,
                 ms_per_step=1e3 * dt / K, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="int64+f64",
-                data="synthetic", config=dict(workload=s.name, beads=s.n_beads, replicas=1),
+                data="synthetic",
+                config=dict(workload=s.name, beads=s.n_beads, replicas=1, parallelism="replicas x1",
+                            step="dynbond_step + dynbond_forces (the oracle's step and forces)"),
                 cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle",
                                   sample=f"{K} timed calls (step + forces) of the workload, serial C++ oracle"),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
