@@ -279,6 +279,14 @@ def test_combined_call_batches_and_1m():
     print("1M combined: max force / ev error", worst)
 
 
+@pytest.mark.parametrize("flag", ["PERSISTENT", "PROFILE", "NO_PDL"])
+def test_combined_call_under_context_flags(flag):
+    """Contexts that run each step as one persistent launch or record phase
+    events take the two calls in turn inside dynbond_step_forces; without
+    dependent launch the combined graph is kept.  All match the oracle."""
+    run_parity(W.config1(), 4, flags=getattr(dynbond(), "FLAG_" + flag), combined=True)
+
+
 def test_combined_call_equals_the_two_calls():
     """The combined call against dynbond_step then dynbond_forces on a second
     context: identical statistics and topology, forces and energy / virial to
