@@ -129,50 +129,101 @@ __device__ __forceinline__ float md_gauss(const MdDev& m, int lo, int hi, unsign
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
+// The DPD force on bead i (sorted entry me, velocity vi, slots si) from
+// entry o within r_c: conservative, dissipative and random parts, zero for a
+// pair fewer than 3 bonds apart.
+__device__ __forceinline__ float3 md_pair_force(const MdDev& m, const int4& me, int i, const float4& vi, const uint4& si,
+                                                const int4& o, const float4* __restrict__ vel,
+                                                const uint4* __restrict__ slots, unsigned long long step) {
+  const int j = o.w;
+  if (md_excluded(slots, si, j)) return make_float3(0.f, 0.f, 0.f);
+  const float s20 = 1.0f / 1048576.0f;
+  float3 r = make_float3((float)wrap_dx(me.x - o.x, m.L) * s20, (float)wrap_dx(me.y - o.y, m.L) * s20,
+                         (float)wrap_dx(me.z - o.z, m.L) * s20);
+  float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
+  if (rr <= 0.f) return make_float3(0.f, 0.f, 0.f);
+  float w = 1.0f - rr * m.inv_rc;
+  float4 vj = vel[j];
+  float rv = (r.x * (vi.x - vj.x) + r.y * (vi.y - vj.y) + r.z * (vi.z - vj.z)) / rr;
+  float xi = md_gauss(m, min(i, j), max(i, j), step);
+  float fs = m.a * w - m.gamma * w * w * rv + m.sigma_over_sqrt_dt * w * xi;
+  return make_float3(fs * r.x / rr, fs * r.y / rr, fs * r.z / rr);
+}
+
 // DPD pair forces on every bead (both orders of a pair are evaluated, with the
-// same random number), written with plain stores
+// same random number), written with plain stores.  A bead first walks its
+// 27 neighbouring cells keeping the entries within r_c (a short loop); the
+// pair forces then run in lockstep across the warp, the k-th neighbour of
+// every lane together, so the random number and the weight are computed
+// with all lanes that have one instead of one lane at a time.  The pairs are
+// summed in cell order either way.
+constexpr int MD_NB = 32;  // neighbours within r_c a bead keeps for the lockstep loop
 __global__ void __launch_bounds__(256) md_dpd(MdDev m, const int4* __restrict__ pos, const float4* __restrict__ vel,
                                                const uint4* __restrict__ slots, unsigned long long step) {
   if (aborted(m.err)) return;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m.N; e += (long long)gridDim.x * blockDim.x) {
-    int4 me = m.sorted[e];
-    int i = me.w;
-    float4 vi = vel[i];
-    uint4 si = slots[i];
-    int nc = m.nc;
-    int cx = (int)((long long)me.x * nc / m.L), cy = (int)((long long)me.y * nc / m.L),
-        cz = (int)((long long)me.z * nc / m.L);
-    int noff = nc >= 3 ? 3 : nc;
-    int offs[3] = {0, 1, nc - 1};
-    float3 f = make_float3(0.f, 0.f, 0.f);
-    for (int a = 0; a < noff; ++a)
-      for (int b = 0; b < noff; ++b)
-        for (int c = 0; c < noff; ++c) {
-          long long cell = (((cx + offs[a]) % nc) * (long long)nc + (cy + offs[b]) % nc) * nc + (cz + offs[c]) % nc;
-          int q0 = m.cell_count[cell], q1 = m.cell_count[cell + 1];
-          for (int q = q0; q < q1; ++q) {
-            int4 o = m.sorted[q];
-            int j = o.w;
-            if (j == i) continue;
-            long long d2 = dist2(me, o, m.L);
-            if (d2 >= m.rc_q2) continue;
-            if (md_excluded(slots, si, j)) continue;
-            const float s20 = 1.0f / 1048576.0f;
-            float3 r = make_float3((float)wrap_dx(me.x - o.x, m.L) * s20, (float)wrap_dx(me.y - o.y, m.L) * s20,
-                                   (float)wrap_dx(me.z - o.z, m.L) * s20);
-            float rr = sqrtf(r.x * r.x + r.y * r.y + r.z * r.z);
-            if (rr <= 0.f) continue;
-            float w = 1.0f - rr * m.inv_rc;
-            float4 vj = vel[j];
-            float rv = (r.x * (vi.x - vj.x) + r.y * (vi.y - vj.y) + r.z * (vi.z - vj.z)) / rr;
-            float xi = md_gauss(m, min(i, j), max(i, j), step);
-            float fs = m.a * w - m.gamma * w * w * rv + m.sigma_over_sqrt_dt * w * xi;
-            f.x += fs * r.x / rr;
-            f.y += fs * r.y / rr;
-            f.z += fs * r.z / rr;
+  const int nc = m.nc, noff = nc >= 3 ? 3 : nc;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < m.N; base += stride) {  // warp-uniform
+    const long long e = base + threadIdx.x;
+    int4 me = make_int4(0, 0, 0, 0);
+    int i = 0, np = 0;
+    float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint4 si = make_uint4(0, 0, 0, 0);
+    int nb[MD_NB];
+    bool more = false;
+    int xs[3], ys[3], zs[3];
+    if (e < m.N) {
+      me = m.sorted[e];
+      i = me.w;
+      vi = vel[i];
+      si = slots[i];
+      const int cx = (int)((long long)me.x * nc / m.L), cy = (int)((long long)me.y * nc / m.L),
+                cz = (int)((long long)me.z * nc / m.L);
+      // the cells at offsets 0, +1, -1 (periodic) along each axis, distinct ones only
+      xs[0] = cx, xs[1] = cx + 1 == nc ? 0 : cx + 1, xs[2] = cx == 0 ? nc - 1 : cx - 1;
+      ys[0] = cy, ys[1] = cy + 1 == nc ? 0 : cy + 1, ys[2] = cy == 0 ? nc - 1 : cy - 1;
+      zs[0] = cz, zs[1] = cz + 1 == nc ? 0 : cz + 1, zs[2] = cz == 0 ? nc - 1 : cz - 1;
+      for (int a = 0; a < noff; ++a)
+        for (int b = 0; b < noff; ++b)
+          for (int c = 0; c < noff; ++c) {
+            const long long cell = ((long long)xs[a] * nc + ys[b]) * nc + zs[c];
+            const int q0 = m.cell_count[cell], q1 = m.cell_count[cell + 1];
+            for (int q = q0; q < q1; ++q) {
+              const int4 o = m.sorted[q];
+              if (o.w == i || dist2(me, o, m.L) >= m.rc_q2) continue;
+              if (np < MD_NB) nb[np++] = q;
+              else more = true;
+            }
           }
-        }
-    m.fdpd[i] = make_float4(f.x, f.y, f.z, 0.f);
+    }
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    const int kmax = __reduce_max_sync(FULL, (unsigned)np);
+    for (int k = 0; k < kmax; ++k) {
+      if (k >= np) continue;
+      const float3 df = md_pair_force(m, me, i, vi, si, m.sorted[nb[k]], vel, slots, step);
+      f.x += df.x;
+      f.y += df.y;
+      f.z += df.z;
+    }
+    if (more) {  // more than MD_NB neighbours (dense spot): the pairs after the kept ones, in the same order
+      int seen = 0;
+      for (int a = 0; a < noff; ++a)
+        for (int b = 0; b < noff; ++b)
+          for (int c = 0; c < noff; ++c) {
+            const long long cell = ((long long)xs[a] * nc + ys[b]) * nc + zs[c];
+            const int q0 = m.cell_count[cell], q1 = m.cell_count[cell + 1];
+            for (int q = q0; q < q1; ++q) {
+              const int4 o = m.sorted[q];
+              if (o.w == i || dist2(me, o, m.L) >= m.rc_q2) continue;
+              if (seen++ < MD_NB) continue;
+              const float3 df = md_pair_force(m, me, i, vi, si, o, vel, slots, step);
+              f.x += df.x;
+              f.y += df.y;
+              f.z += df.z;
+            }
+          }
+    }
+    if (e < m.N) m.fdpd[i] = make_float4(f.x, f.y, f.z, 0.f);
   }
 }
 
