@@ -366,7 +366,7 @@ cudaError_t enqueue_step_seq(dynbond_ctx* c, bool bond_branch) {
     return cudaGetLastError();
   }
   mark(c, c->ev_step, k++);
-  E(launch(c, k_setup, c->nsm * 2, 1024, d));
+  E(launch(c, k_setup, c->nsm * 4, 256, d));
   // the breakage nomination needs only the zeroed per-call state: it runs on
   // a branch beside the binning, cell list and candidate search, joined
   // before the matching

@@ -1109,6 +1109,7 @@ __global__ void __launch_bounds__(256, 3) k_candidates_tile_oct(Dev d, const Rul
 // Exact path for beads with more than MAXC candidates: count, allocate,
 // write, then sort the bead's list by (d2, partner) in place.
 __device__ __forceinline__ void cand_overflow_body(const Dev& d, const RuleTab* __restrict__ rtp) {
+  if (ld_cg(&d.cnt->n_ovf) == 0) return;  // the common case: nothing overflowed (every thread reads the same count)
   __shared__ unsigned s_mask[16];
   load_type_masks(*rtp, s_mask);
   const long long r2max = rtp->r2max;
